@@ -1,0 +1,217 @@
+"""Exact definitions in complex float64 (TEST INFRASTRUCTURE, see package doc).
+
+Everything here is the plain definition written out, on dense matrices,
+for systems small enough that O(N^3) work finishes in seconds.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------
+# ASED Hamiltonian (Section 2.2)
+# --------------------------------------------------------------------------
+def ased_hamiltonian(S: np.ndarray, eps: np.ndarray, K: float, orbital_atom: np.ndarray) -> np.ndarray:
+    """Dense ASED Hamiltonian.
+
+    Section 2.2: the diagonal element H_{i alpha, i alpha} is the atomic
+    level eps_{i alpha}; an element between orbitals of different atoms i != j
+    follows Eq. (Hap-1), H = K * (H_{i alpha,i alpha} + H_{j beta,j beta}) / 2
+    * S_{i alpha, j beta}, here with a constant K.  Two different orbitals on
+    the same atom are orthogonal (their overlap is zero), so their element is
+    zero as well.
+    """
+    N = len(eps)
+    H = np.zeros((N, N))
+    for a in range(N):
+        for b in range(N):
+            if a == b:
+                H[a, b] = eps[a]
+            elif orbital_atom[a] != orbital_atom[b]:
+                H[a, b] = K * 0.5 * (eps[a] + eps[b]) * S[a, b]
+    return H
+
+
+# --------------------------------------------------------------------------
+# Linear solves (Eq. base-2, Eq. GreensFunc)
+# --------------------------------------------------------------------------
+def gauss_solve(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Solve A X = B by Gaussian elimination with partial pivoting.
+
+    Forward elimination: at step k the row with the largest |A[p, k]|, p >= k,
+    becomes the pivot row; multiples of it are subtracted from the rows below.
+    Back substitution then runs from the last unknown to the first.
+    """
+    A = np.array(A, dtype=np.complex128)
+    X = np.array(B, dtype=np.complex128)
+    vec = X.ndim == 1
+    if vec:
+        X = X[:, None]
+    n = A.shape[0]
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(A[k:, k])))
+        if A[p, k] == 0:
+            raise np.linalg.LinAlgError("singular matrix")
+        if p != k:
+            A[[k, p]] = A[[p, k]]
+            X[[k, p]] = X[[p, k]]
+        f = A[k + 1:, k] / A[k, k]
+        A[k + 1:, k:] -= f[:, None] * A[k, k:][None, :]
+        X[k + 1:] -= f[:, None] * X[k][None, :]
+    for k in range(n - 1, -1, -1):
+        X[k] = (X[k] - A[k, k + 1:] @ X[k + 1:]) / A[k, k]
+    return X[:, 0] if vec else X
+
+
+def gauss_jordan_inverse(A: np.ndarray) -> np.ndarray:
+    """Inverse of A by Gauss-Jordan elimination on [A | I] with partial
+    pivoting: each pivot row is normalised and eliminated from every other
+    row.  A second, independent route to A^-1 for brute-force checks."""
+    A = np.array(A, dtype=np.complex128)
+    n = A.shape[0]
+    M = np.concatenate([A, np.eye(n, dtype=np.complex128)], axis=1)
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(M[k:, k])))
+        if M[p, k] == 0:
+            raise np.linalg.LinAlgError("singular matrix")
+        M[[k, p]] = M[[p, k]]
+        M[k] /= M[k, k]
+        for i in range(n):
+            if i != k and M[i, k] != 0:
+                M[i] -= M[i, k] * M[k]
+    return M[:, n:]
+
+
+def shifted_matrix(H: np.ndarray, S: np.ndarray, z: complex) -> np.ndarray:
+    """A(z) = z S - H: the matrix of Eq. (base-2) in a non-orthogonal basis
+    ((E - H) becomes (E S - H) when <i|j> = S_ij)."""
+    return z * S - H
+
+
+def green_columns(H, S, z, cols) -> np.ndarray:
+    """x_j(z_k) = (z_k S - H)^-1 e_j for every shift z_k and column j.
+
+    Eq. (base-2) with |j> = e_j and Eq. (GreensFunc): G_ij(z) = <i|x^(j)>.
+    Returns X with X[k, :, c] = x_{cols[c]}(z_k)  (shape K x N x len(cols)).
+    """
+    N = S.shape[0]
+    cols = np.asarray(cols)
+    B = np.zeros((N, len(cols)), dtype=np.complex128)
+    B[cols, np.arange(len(cols))] = 1.0
+    return np.stack([gauss_solve(shifted_matrix(H, S, zk), B) for zk in z])
+
+
+def green_matrix(H, S, zk) -> np.ndarray:
+    """Full G(z) = (z S - H)^-1 (all columns)."""
+    N = S.shape[0]
+    return gauss_solve(shifted_matrix(H, S, zk), np.eye(N, dtype=np.complex128))
+
+
+# --------------------------------------------------------------------------
+# Density matrix and Mulliken populations (Section 2.2)
+# --------------------------------------------------------------------------
+def density_matrix(H, S, z, w, g_s=2.0) -> np.ndarray:
+    """rho = -(g_s / pi) Im sum_k w_k G(z_k): the energy-integrated Green's
+    function (the paper integrates G into the charge density; the quadrature
+    z_k, w_k is an input)."""
+    rho = np.zeros(S.shape, dtype=np.complex128)
+    for zk, wk in zip(z, w):
+        rho += wk * green_matrix(H, S, zk)
+    return -(g_s / math.pi) * rho.imag
+
+
+def mulliken_orbital(H, S, z, w, g_s=2.0) -> np.ndarray:
+    """Gross Mulliken population of every orbital, q_{i alpha} =
+    (rho S)_{i alpha, i alpha} = sum_{j beta} rho_{i alpha, j beta} S_{j beta, i alpha}
+    (the Mulliken partition of the overlap charge density, Section 2.2)."""
+    rho = density_matrix(H, S, z, w, g_s)
+    N = S.shape[0]
+    return np.array([sum(rho[a, b] * S[b, a] for b in range(N)) for a in range(N)])
+
+
+def mulliken_atom(q_orb: np.ndarray, orbital_atom: np.ndarray, n_atoms: int) -> np.ndarray:
+    """Atomic gross population q_i = sum over the atom's orbitals."""
+    q = np.zeros(n_atoms)
+    for a, i in enumerate(orbital_atom):
+        q[i] += q_orb[a]
+    return q
+
+
+# --------------------------------------------------------------------------
+# Eigenvalues for the sum-rule closed form
+# --------------------------------------------------------------------------
+def cholesky(S: np.ndarray) -> np.ndarray:
+    """Lower-triangular L with S = L L^T; raises if S is not positive
+    definite (Section 3.3 relies on S being positive definite)."""
+    n = S.shape[0]
+    L = np.zeros_like(S, dtype=np.float64)
+    for j in range(n):
+        d = S[j, j] - L[j, :j] @ L[j, :j]
+        if d <= 0.0:
+            raise np.linalg.LinAlgError("overlap matrix is not positive definite")
+        L[j, j] = math.sqrt(d)
+        L[j + 1:, j] = (S[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return L
+
+
+def forward_substitution(L: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Solve L Y = B for lower-triangular L, row by row."""
+    Y = np.array(B, dtype=np.float64)
+    for i in range(L.shape[0]):
+        Y[i] = (Y[i] - L[i, :i] @ Y[:i]) / L[i, i]
+    return Y
+
+
+def jacobi_eigvals(A: np.ndarray, tol: float = 1e-14, max_sweeps: int = 60) -> np.ndarray:
+    """Eigenvalues of a real symmetric matrix by the cyclic Jacobi method:
+    plane rotations annihilate the off-diagonal entries one pair at a time
+    until the off-diagonal norm is below tol * ||A||_F."""
+    A = np.array(A, dtype=np.float64)
+    n = A.shape[0]
+    scale = np.linalg.norm(A)
+    for _ in range(max_sweeps):
+        off = math.sqrt(max(0.0, np.sum(A * A) - np.sum(np.diag(A) ** 2)))
+        if off <= tol * scale:
+            break
+        for p in range(n - 1):
+            for q in range(p + 1, n):
+                apq = A[p, q]
+                if abs(apq) < 1e-300:
+                    continue
+                theta = (A[q, q] - A[p, p]) / (2.0 * apq)
+                t = math.copysign(1.0, theta) / (abs(theta) + math.sqrt(theta * theta + 1.0))
+                c = 1.0 / math.sqrt(t * t + 1.0)
+                s = t * c
+                rp = A[p].copy()
+                rq = A[q].copy()
+                A[p] = c * rp - s * rq
+                A[q] = s * rp + c * rq
+                cp = A[:, p].copy()
+                cq = A[:, q].copy()
+                A[:, p] = c * cp - s * cq
+                A[:, q] = s * cp + c * cq
+    else:
+        raise RuntimeError("Jacobi eigensolver did not converge")
+    return np.sort(np.diag(A))
+
+
+def generalized_eigvals(H: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """Eigenvalues eps_m of H c = eps S c, via S = L L^T and the symmetric
+    matrix L^-1 H L^-T."""
+    L = cholesky(S)
+    Y = forward_substitution(L, H)            # L^-1 H
+    C = forward_substitution(L, Y.T)          # L^-1 (L^-1 H)^T = L^-1 H L^-T
+    return jacobi_eigvals(0.5 * (C + C.T))
+
+
+def electron_count_closed_form(eigs: np.ndarray, z, w, g_s=2.0) -> float:
+    """Sum rule: sum_{i alpha} q_{i alpha} = Tr(rho S)
+    = -(g_s/pi) Im sum_k w_k Tr[(z_k S - H)^-1 S]
+    = -(g_s/pi) Im sum_k w_k sum_m 1 / (z_k - eps_m),
+    exact for any quadrature nodes and weights."""
+    tot = 0.0 + 0.0j
+    for zk, wk in zip(z, w):
+        tot += wk * np.sum(1.0 / (zk - eigs))
+    return -(g_s / math.pi) * tot.imag

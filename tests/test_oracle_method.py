@@ -1,0 +1,144 @@
+"""Pins of the method oracle (oracle.method): convergence to the exact
+solve, the collinear-residual theorem (which fixes the sign of the pi
+recurrence), invariance under seed switching, reduction to plain
+preconditioned COCG for one shift, and the generalized Lanczos process
+against a directly orthogonalised Krylov basis."""
+import numpy as np
+import pytest
+
+from tbinputs import linspace_grid, choose_columns
+from oracle import dense, method
+
+
+def _true_res(H, S, z, x, j):
+    b = np.zeros(S.shape[0])
+    b[j] = 1.0
+    return np.array([np.linalg.norm(b - dense.shifted_matrix(H, S, zk) @ xk) for zk, xk in zip(z, x)])
+
+
+def test_converges_to_exact_solution(si64_dense):
+    H, S = si64_dense
+    z, _ = linspace_grid(32)
+    cols = choose_columns(256, 8, seed=2)[:2]
+    X = dense.green_columns(H, S, z, cols)
+    for c, j in enumerate(cols):
+        out = method.generalized_shifted_cocg(H, S, z, int(j), tol=1e-10)
+        assert out["converged"] and out["switches"] >= 1
+        tr = _true_res(H, S, z, out["x"], j)
+        assert tr.max() < 1e-9
+        # forward error bounded by cond(A) * residual; cond ~ 1/eta * ||A||
+        err = np.abs(out["x"] - X[:, :, c]).max(axis=1)
+        assert err.max() < 1e-4 * np.abs(X[:, :, c]).max()
+
+
+@pytest.mark.parametrize("sign,ok", [(1.0, True), (-1.0, False)])
+def test_collinear_residuals_fix_pi_sign(si64_dense, sign, ok):
+    """Eq. (collinear): b - A(z_k) x^k_n = r_n / pi^k_n.  The derived sign of
+    the pi recurrence satisfies it at every step; the printed sign does not
+    (planted mistake, sign=-1)."""
+    H, S = si64_dense
+    z, _ = linspace_grid(8)
+    j = 77
+    worst = 0.0
+    for n in (1, 2, 3, 5, 8, 13):
+        out = method.generalized_shifted_cocg(H, S, z, j, max_iter=n, switching=False, record=True,
+                                              pi_sign=sign)
+        rec = out["history"]["rnorm"][-1] / np.abs(out["history"]["pi"][-1])
+        tr = _true_res(H, S, z, out["x"], j)
+        worst = max(worst, np.max(np.abs(tr - rec) / rec))
+    if ok:
+        assert worst < 1e-9
+    else:
+        assert worst > 1e-2
+
+
+def test_seed_switch_invariance(si64_dense):
+    """Switching the seed rescales collinear residuals only, so the shifted
+    iterates after n steps do not depend on the switches."""
+    H, S = si64_dense
+    z, _ = linspace_grid(16)
+    a = method.generalized_shifted_cocg(H, S, z, 5, max_iter=40, switching=False)
+    b = method.generalized_shifted_cocg(H, S, z, 5, max_iter=40, force_switch_every=7)
+    assert b["switches"] >= 4
+    assert np.abs(a["x"] - b["x"]).max() < 1e-7 * np.abs(a["x"]).max()
+
+
+def test_single_shift_is_preconditioned_cocg(si64_dense):
+    """K = 1: the seed recurrence in residual form equals textbook
+    preconditioned COCG (explicit search direction, M = S)."""
+    H, S = si64_dense
+    zk = -3.0 + 0.01j
+    A = dense.shifted_matrix(H, S, zk)
+    b = np.zeros(256, dtype=complex)
+    b[11] = 1.0
+    x = np.zeros(256, dtype=complex)
+    r = b.copy()
+    zz = np.linalg.solve(S, r)
+    p = zz.copy()
+    rho = r @ zz
+    for _ in range(30):
+        q = A @ p
+        al = rho / (p @ q)
+        x = x + al * p
+        r = r - al * q
+        zz = np.linalg.solve(S, r)
+        rho_new = r @ zz
+        p = zz + (rho_new / rho) * p
+        rho = rho_new
+    out = method.generalized_shifted_cocg(H, S, [zk], 11, max_iter=30)
+    assert np.abs(out["x"][0] - x).max() < 1e-10 * np.abs(x).max()
+
+
+def test_functional_tracking_matches_full(si64_dense):
+    H, S = si64_dense
+    z, _ = linspace_grid(8)
+    j = 40
+    F = np.stack([S[j], np.eye(256)[3], np.eye(256)[j]])
+    out = method.generalized_shifted_cocg(H, S, z, j, max_iter=60, functionals=F)
+    assert np.abs(out["t"] - out["x"] @ F.T).max() < 1e-11 * np.abs(out["t"]).max()
+
+
+def test_inner_cg_vs_solve(si64_dense):
+    _, S = si64_dense
+    rng = np.random.default_rng(5)
+    r = rng.normal(size=256) + 1j * rng.normal(size=256)
+    x, it = method.apply_S_inverse(S, r, 1e-13, 500)
+    assert np.abs(x - np.linalg.solve(S, r)).max() < 1e-11 and 10 < it < 100
+
+
+def test_generalized_lanczos_vs_krylov_basis(si64_dense):
+    """a_n, b_n equal the entries of U^T H U for the S-orthonormal basis U of
+    the Krylov space K_m(S^-1 H, S^-1 e_j) (Eqs. 1.13, 1.18, Krylov),
+    built here by explicit Gram-Schmidt."""
+    H, S = si64_dense
+    j, m = 9, 8
+    a, b, nrm2 = method.generalized_lanczos(H, S, j, m)
+    e = np.eye(256)[j]
+    v = np.linalg.solve(S, e)
+    assert abs(nrm2 - e @ v) < 1e-12
+    Op = np.linalg.solve(S, H)
+    Kry = [v]
+    for _ in range(m - 1):
+        Kry.append(Op @ Kry[-1])
+    U = []
+    for k in Kry:
+        w = k / np.sqrt(k @ S @ k)
+        for _ in range(2):
+            for u in U:
+                w = w - (u @ S @ w) * u
+        U.append(w / np.sqrt(w @ S @ w))
+    U = np.array(U).T
+    T = U.T @ H @ U
+    assert np.abs(np.diag(T) - a).max() < 1e-8
+    assert np.abs(np.abs(np.diag(T, 1)) - b[1:m]).max() < 1e-8
+    assert np.all(b[1:] > 0)
+
+
+def test_lanczos_continued_fraction_vs_exact(si64_dense):
+    H, S = si64_dense
+    j = 9
+    z = np.array([-5.0 + 2.0j, 2.0 + 2.0j])
+    a, b, nrm2 = method.generalized_lanczos(H, S, j, 100)
+    g = method.lanczos_green(a, b, nrm2, z)
+    ref = dense.green_columns(H, S, z, [j])[:, j, 0]
+    assert np.abs(g - ref).max() < 1e-8 * np.abs(ref).max()
