@@ -1,0 +1,193 @@
+/*
+ * tbcocg.h -- C ABI of the GB300 generalized shifted COCG library.
+ *
+ * The library solves, for many complex energies z_k and unit right-hand
+ * sides e_j, the linear systems of Eq. (base-2) in a non-orthogonal local
+ * basis,
+ *
+ *     (z_k S - H) x_j(z_k) = e_j ,
+ *
+ * and returns the Green's-function elements G_ij(z_k) = (x_j(z_k))_i of
+ * Eq. (GreensFunc), or their energy integral folded into Mulliken
+ * populations.  H is the tight-binding Hamiltonian matrix and S the overlap
+ * matrix of Section 2.2; both are real symmetric, S positive definite.
+ * The solver is the generalized shifted COCG method of Section 3.3: one seed
+ * system (Eq. shift-E) iterated by Eqs. (CGp:p), (CGp:x), (CGp:r) with
+ * r' = S^-1 r from an inner CG, every other shift carried by the scalar
+ * recurrence Eq. (shift:pi) through the collinear residuals of
+ * Eq. (collinear), and seed switching.  The generalized Lanczos process of
+ * Section 3.2 (Eqs. 1.13, 1.18) is exported as well.
+ *
+ * Conventions for every entry point
+ *  - Return value: tb_status, TB_OK = 0.  tb_status_string() names it.
+ *  - Pointers are owned by the caller and are only read/written during the
+ *    call; nothing is retained after it returns except inside a tb_handle.
+ *  - Input arrays marked "host" are read on the host.  Output arrays marked
+ *    "host or device" may be either: the library asks the CUDA runtime where
+ *    the pointer lives and copies the result there.  Device outputs are
+ *    complete when the call returns (the call synchronises the stream).
+ *  - Complex numbers are pairs of doubles (real, imaginary), interleaved.
+ *  - Orbital indices are in the caller's orbital order: the orbitals of atom
+ *    0 first (s, then px, py, pz for sp atoms), then atom 1, and so on.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  All device work of a call is enqueued on it.
+ *  - Only one call may use a given handle at a time.
+ */
+#ifndef TBCOCG_H
+#define TBCOCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tb_handle tb_handle;
+
+typedef enum {
+    TB_OK = 0,
+    TB_ERR_INVALID_ARG = 1,    /* malformed argument or block structure   */
+    TB_ERR_NOT_SYMMETRIC = 2,  /* S or H (or their pattern) not symmetric */
+    TB_ERR_S_NOT_SPD = 3,      /* S not positive definite (seen by CG)    */
+    TB_ERR_OOM = 4,            /* device allocation failed                */
+    TB_ERR_CUDA = 5,           /* a CUDA runtime call failed              */
+    TB_ERR_NOT_CONVERGED = 6,  /* max_iter reached; converged shifts valid*/
+    TB_ERR_BREAKDOWN = 7,      /* COCG breakdown (rho or mu == 0)         */
+    TB_ERR_TIMEOUT = 8,        /* a bounded device wait ran out           */
+    TB_ERR_NO_DEVICE = 9       /* no usable CUDA device                   */
+} tb_status;
+
+enum { TB_FP64 = 0 };
+
+/*
+ * Block-sparse system in atom blocks (Section 2.2: one block per pair of
+ * atoms within the overlap cutoff).  Block row i holds the blocks
+ * bcol[brow_ptr[i]] ... bcol[brow_ptr[i+1]-1], sorted ascending, the
+ * diagonal block included; the pattern holds both triangles and must be
+ * symmetric.  Block (i, j) has orb_per_atom[i] x orb_per_atom[j] values,
+ * row-major; the blocks are concatenated in block order.
+ *
+ * H_vals == NULL builds H by the ASED rule (Section 2.2, Eq. Hap-1) on the
+ * device: H_{ia,ia} = eps_{ia}; H_{ia,ib} = 0 for a != b on one atom;
+ * H_{ia,jb} = K (eps_{ia} + eps_{jb}) / 2 * S_{ia,jb} for i != j.
+ * All arrays are host memory and are copied during tb_create.
+ */
+typedef struct {
+    int32_t n_atoms;
+    const int32_t *orb_per_atom; /* [n_atoms], 1 (s) or 4 (s,px,py,pz)  */
+    const int64_t *brow_ptr;     /* [n_atoms+1]                          */
+    const int32_t *bcol;         /* [nb]                                 */
+    const double *S_vals;        /* concatenated blocks of S             */
+    const double *H_vals;        /* concatenated blocks of H, or NULL    */
+    const double *eps;           /* [N] on-site levels (eV); needed when
+                                    H_vals == NULL, else may be NULL     */
+    double K;                    /* ASED constant of Eq. Hap-1           */
+    int32_t precision;           /* TB_FP64                              */
+} tb_system_desc;
+
+/* Validate the system, copy it to the device (H built by Eq. Hap-1 if not
+ * given) and return a handle.  Errors: TB_ERR_INVALID_ARG (structure),
+ * TB_ERR_NOT_SYMMETRIC (pattern or values), TB_ERR_OOM, TB_ERR_CUDA,
+ * TB_ERR_NO_DEVICE.  On error *out is NULL and nothing is allocated. */
+tb_status tb_create(tb_handle **out, const tb_system_desc *desc, void *stream);
+
+/* Release all device memory of the handle (NULL is allowed). */
+tb_status tb_destroy(tb_handle *h);
+
+/* Number of orbitals N and atoms of the system. */
+int64_t tb_num_orbitals(const tb_handle *h);
+int64_t tb_num_atoms(const tb_handle *h);
+int64_t tb_num_blocks(const tb_handle *h);
+
+typedef struct {
+    double tol;               /* shift converged when ||r_{n+1}||_2/|pi^k_{n+1}| <= tol
+                                 (||e_j|| = 1); default 1e-10                         */
+    double inner_tol;         /* inner CG: ||r - S r'|| <= inner_tol ||r||; 1e-13      */
+    int32_t max_iter;         /* outer iterations per panel; default 100000           */
+    int32_t inner_max_iter;   /* inner CG iterations per outer step; default 1000     */
+    int32_t panel;            /* right-hand sides per panel (power of two <= 256);
+                                 0 = automatic                                         */
+    int32_t seed;             /* index of the initial seed shift; default 0           */
+    int32_t switching;        /* 1 = seed switching (default), 0 = keep the seed       */
+    int32_t force_switch_every; /* > 0: also switch every that many steps (testing)    */
+} tb_solve_opts;
+
+/* Fill *opts with the defaults listed above. */
+void tb_default_opts(tb_solve_opts *opts);
+
+/* Optional statistics; every pointer member may be NULL. */
+typedef struct {
+    int32_t *conv_iter;        /* host [R*K]: outer step at which shift k of column
+                                  c converged (index c*K + k), -1 if it did not      */
+    int64_t outer_iterations;  /* sum over columns of the steps each column ran    */
+    int64_t inner_iterations;  /* sum over outer steps of inner CG iterations       */
+    int64_t max_column_iterations; /* steps of the slowest column                   */
+    int32_t switches;          /* seed switches, all columns                       */
+    int32_t unconverged;       /* (column, shift) pairs not converged              */
+    double seconds;            /* wall time of the solve                           */
+} tb_stats;
+
+/*
+ * Full solutions.  For shifts z[0..K-1] (host, complex) and right-hand sides
+ * e_j, j = cols[0..R-1] (host), writes
+ *     x_out[(k*R + c)*N + i] = (x_{cols[c]}(z_k))_i     (complex, host or device)
+ * Memory for x_out: K*R*N complex doubles.
+ * Returns TB_ERR_NOT_CONVERGED if some shift did not reach opts->tol within
+ * max_iter steps (the converged ones are valid), TB_ERR_BREAKDOWN or
+ * TB_ERR_S_NOT_SPD if the iteration failed.
+ */
+tb_status tb_shifted_cocg(tb_handle *h, int32_t K, const double *z, int32_t R, const int32_t *cols,
+                          const tb_solve_opts *opts, double *x_out, tb_stats *stats, void *stream);
+
+/*
+ * Selected Green's-function elements (Eq. GreensFunc) with the shifted
+ * solutions projected on the requested rows (no full solution is stored).
+ * Column c (orbital cols[c]) asks for rows rows[row_ptr[c] .. row_ptr[c+1]-1]
+ * (host arrays; row_ptr[0] = 0).  Writes, complex, host or device,
+ *     G_out[(row_ptr[c] + r)*K + k] = G_{rows[row_ptr[c]+r], cols[c]}(z_k).
+ * At most 1024 rows per column.  Status as tb_shifted_cocg.
+ */
+tb_status tb_green_elements(tb_handle *h, int32_t K, const double *z, int32_t R, const int32_t *cols,
+                            const int64_t *row_ptr, const int32_t *rows, const tb_solve_opts *opts,
+                            double *G_out, tb_stats *stats, void *stream);
+
+/*
+ * Gross Mulliken populations of selected orbitals (Section 2.2, the
+ * Mulliken partition of the charge density), from the energy integral of
+ * the Green's function with the quadrature (z_k, w_k) (host, complex):
+ *     q_j = -(g_s/pi) Im sum_k w_k (G(z_k) S)_jj = -(g_s/pi) Im sum_k w_k s_j^T x_j(z_k),
+ * s_j the j-th column of S.  Writes q_out[c] for orbital cols[c]
+ * (double, host or device).  Status as tb_shifted_cocg.
+ */
+tb_status tb_mulliken_orbital(tb_handle *h, int32_t K, const double *z, const double *w, double g_s,
+                              int32_t R, const int32_t *cols, const tb_solve_opts *opts,
+                              double *q_out, tb_stats *stats, void *stream);
+
+/*
+ * Gross Mulliken population of every atom: q_i = sum of q_j over the
+ * orbitals j of atom i, all N orbitals solved in panels.  q_out: double
+ * [n_atoms], host or device.  Status as tb_shifted_cocg.
+ */
+tb_status tb_mulliken_charges(tb_handle *h, int32_t K, const double *z, const double *w, double g_s,
+                              const tb_solve_opts *opts, double *q_out, tb_stats *stats, void *stream);
+
+/*
+ * Generalized Lanczos process (Section 3.2, Eqs. 1.13 and 1.18) for the
+ * operator S^-1 H with the S-product, started from u^0 = S^-1 e_j normalised
+ * in the S-norm.  Writes a[0..n_steps-1], b[0..n_steps] (b[0] = 0) and
+ * *norm = e_j^T S^-1 e_j (all double, host or device), so that
+ *     G_jj(z) = norm / (z - a_0 - b_1^2 / (z - a_1 - b_2^2 / ...)).
+ * If some b_{n+1} is 0 the remaining coefficients are 0 (invariant
+ * subspace found).  inner_tol as in tb_solve_opts (<= 0: 1e-13).
+ */
+tb_status tb_generalized_lanczos(tb_handle *h, int32_t j, int32_t n_steps, double inner_tol,
+                                 double *a, double *b, double *norm, void *stream);
+
+/* Static string naming a status code. */
+const char *tb_status_string(tb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBCOCG_H */

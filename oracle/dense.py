@@ -34,6 +34,22 @@ def ased_hamiltonian(S: np.ndarray, eps: np.ndarray, K: float, orbital_atom: np.
     return H
 
 
+def ased_hamiltonian_sparse(S_csr, eps: np.ndarray, K: float, orbital_atom: np.ndarray):
+    """The same rule as ased_hamiltonian applied to the stored entries of a
+    scipy.sparse overlap matrix (large systems; only the nonzero pattern of S
+    can carry an off-diagonal element of Eq. Hap-1)."""
+    import scipy.sparse as sp
+    C = S_csr.tocoo()
+    vals = np.zeros(C.nnz)
+    for e in range(C.nnz):
+        a, b = C.row[e], C.col[e]
+        if a == b:
+            vals[e] = eps[a]
+        elif orbital_atom[a] != orbital_atom[b]:
+            vals[e] = K * 0.5 * (eps[a] + eps[b]) * C.data[e]
+    return sp.csr_matrix((vals, (C.row, C.col)), shape=S_csr.shape)
+
+
 # --------------------------------------------------------------------------
 # Linear solves (Eq. base-2, Eq. GreensFunc)
 # --------------------------------------------------------------------------

@@ -1,0 +1,13 @@
+"""GB300 generalized shifted COCG for non-orthogonal tight binding.
+
+The compute path is the CUDA library ``libtbcocg.so`` (C ABI in
+``include/tbcocg.h``); this package holds its sources (``csrc/``), the
+in-tree build (``_build_lib``) and the ctypes binding (``tb``), whose
+functions carry the names of the C entry points.
+"""
+from .tb import (  # noqa: F401
+    Handle, TBError, SolveOpts, load_library, library_path,
+    tb_create, tb_create_system, tb_default_opts, tb_shifted_cocg, tb_green_elements,
+    tb_mulliken_orbital, tb_mulliken_charges, tb_generalized_lanczos, tb_status_string,
+)
+from ._build_lib import build  # noqa: F401

@@ -1,0 +1,695 @@
+// C ABI of the generalized shifted COCG library: validation, device memory,
+// and the host-side step loop that enqueues the kernels of tb_kernels.cu.
+#include "../../include/tbcocg.h"
+#include "tb_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+using namespace tb;
+
+namespace tb {
+int max_grid();
+}
+
+struct tb_handle {
+    DevSystem ds;
+    int device = 0;
+    int n_atoms = 0;
+    int64_t n_orb = 0;
+    std::vector<int32_t> orb_per_atom;
+    std::vector<int32_t> orb2pad_h;   // caller orbital -> padded slot
+    int32_t* orb2pad = nullptr;       // device copy
+    double* eps_pad = nullptr;
+    int* flags_host = nullptr;        // pinned, 4 ints
+};
+
+namespace {
+
+struct Cleanup {
+    std::vector<void*> dev;
+    cudaStream_t st = nullptr;
+    void* add(void* p) { dev.push_back(p); return p; }
+    ~Cleanup() {
+        for (void* p : dev)
+            if (p) cudaFreeAsync(p, st);
+    }
+};
+
+#define TB_CK(call)                                         \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) {                            \
+            cudaGetLastError();                             \
+            return e_ == cudaErrorMemoryAllocation ? TB_ERR_OOM : TB_ERR_CUDA; \
+        }                                                   \
+    } while (0)
+
+template <class T>
+tb_status dalloc(Cleanup& cl, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, count * sizeof(T), cl.st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TB_ERR_OOM : TB_ERR_CUDA;
+    }
+    cl.add(q);
+    *p = static_cast<T*>(q);
+    return TB_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct Solve {
+    int K = 0;
+    const double* z = nullptr;  // host, interleaved
+    int R = 0;
+    const int32_t* cols = nullptr;
+    int proj = PROJ_NONE;
+    const int64_t* row_ptr = nullptr;   // PROJ_ROWS
+    const int32_t* rows = nullptr;
+    const double* w = nullptr;          // PROJ_SROW quadrature weights (host)
+    double g_s = 2.0;
+    // device outputs
+    double2* x_out = nullptr;           // full
+    double2* g_out = nullptr;           // rows
+    double* q_out = nullptr;            // srow, per column
+};
+
+tb_status check_opts(const tb_solve_opts* o) {
+    if (!o) return TB_ERR_INVALID_ARG;
+    if (!(o->tol > 0.0) || !(o->inner_tol > 0.0) || o->max_iter < 1 || o->inner_max_iter < 1) return TB_ERR_INVALID_ARG;
+    if (o->panel < 0 || o->panel > MAX_P || (o->panel & (o->panel - 1)) != 0) return TB_ERR_INVALID_ARG;
+    if (o->seed < 0 || o->force_switch_every < 0) return TB_ERR_INVALID_ARG;
+    return TB_OK;
+}
+
+// Inner CG for S r' = r on the current panel; one host synchronisation in the
+// common case (the number of iterations is predicted from the previous call
+// and the surplus launches exit at once).
+tb_status inner_cg(tb_handle* h, const PanelDev& p, int inner_max, int& pred, int64_t& inner_total, cudaStream_t st) {
+    int launched = 0;
+    int target = std::min(std::max(pred, 1), inner_max);
+    while (true) {
+        for (int i = launched; i < target; ++i) {
+            launch_inner_spmv(h->ds, p, i, st);
+            launch_inner_update(h->ds, p, i, st);
+        }
+        launched = target;
+        TB_CK(cudaGetLastError());
+        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaStreamSynchronize(st));
+        if (h->flags_host[1] == 0) {
+            inner_total += h->flags_host[3];
+            pred = h->flags_host[3] + 1;
+            return TB_OK;
+        }
+        if (launched >= inner_max) return TB_ERR_NOT_CONVERGED;
+        target = std::min(launched + 8, inner_max);
+    }
+}
+
+tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int K = q.K, R = q.R;
+    const int npad = h->ds.npad;
+    int P = o->panel ? o->panel : 64;
+    P = std::min(P, next_pow2(R));
+    if (q.proj == PROJ_NONE) {
+        // keep the full-mode x^k, p^k within 8 GiB
+        while (P > 1 && (double)K * npad * P * 32.0 > 8.0 * (1 << 30)) P >>= 1;
+    }
+    int M = 0;
+    if (q.proj == PROJ_ROWS) {
+        for (int c = 0; c < R; ++c) M = std::max<int64_t>(M, q.row_ptr[c + 1] - q.row_ptr[c]);
+        if (M < 1) M = 1;
+    } else if (q.proj == PROJ_SROW) {
+        M = 1;
+    }
+    Cleanup cl;
+    cl.st = st;
+    PanelDev p;
+    p.P = P;
+    p.K = K;
+    p.npad = npad;
+    p.M = M;
+    p.proj = q.proj;
+    p.grid = max_grid();
+    p.tol = o->tol;
+    p.inner_tol = o->inner_tol;
+    p.switching = o->switching;
+    p.force_switch_every = o->force_switch_every;
+    const size_t nv = (size_t)npad * P;
+    tb_status s;
+    double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
+    for (double2** v : vecs)
+        if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.col, P)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.inner, 2 * P)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.z, K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.pi, (size_t)P * K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.pi_prev, (size_t)P * K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.conv_iter, (size_t)P * K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.partials, (size_t)p.grid * 4 * P)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.counter, 1)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.flags, 4)) != TB_OK) return s;
+    if (q.proj == PROJ_NONE) {
+        if ((s = dalloc(cl, &p.ak, (size_t)P * K)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.bk, (size_t)P * K)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.ipi, (size_t)P * K)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.X, nv * K)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.Pk, nv * K)) != TB_OK) return s;
+    } else {
+        if ((s = dalloc(cl, &p.t, (size_t)P * K * M)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.u, (size_t)P * K * M)) != TB_OK) return s;
+        if (q.proj == PROJ_ROWS && (s = dalloc(cl, &p.frow, (size_t)P * M)) != TB_OK) return s;
+    }
+    double2* w_dev = nullptr;
+    if (q.proj == PROJ_SROW) {
+        if ((s = dalloc(cl, &w_dev, K)) != TB_OK) return s;
+        TB_CK(cudaMemcpyAsync(w_dev, q.w, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    }
+    int64_t* off_dev = nullptr;
+    if (q.proj == PROJ_ROWS) {
+        if ((s = dalloc(cl, &off_dev, (size_t)R + 1)) != TB_OK) return s;
+        TB_CK(cudaMemcpyAsync(off_dev, q.row_ptr, sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, st));
+    }
+    TB_CK(cudaMemcpyAsync(p.z, q.z, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned), st));
+
+    std::vector<ColState> colh(P);
+    std::vector<int32_t> convh((size_t)P * K);
+    std::vector<int32_t> frowh((size_t)P * std::max(M, 1));
+    int64_t outer_total = 0, inner_total = 0, max_col_iters = 0;
+    int switches = 0, unconverged = 0, errbits = 0;
+    int pred = 64;
+    tb_status final_status = TB_OK;
+
+    for (int c0 = 0; c0 < R; c0 += P) {
+        const int ncols = std::min(P, R - c0);
+        for (int c = 0; c < P; ++c) {
+            ColState cs;
+            std::memset(&cs, 0, sizeof(cs));
+            cs.zs = make_double2(q.z[2 * o->seed], q.z[2 * o->seed + 1]);
+            cs.alpha_prev = make_double2(1.0, 0.0);
+            cs.beta_prev = make_double2(0.0, 0.0);
+            cs.sc_cur = make_double2(1.0, 0.0);
+            cs.sc_prev = make_double2(1.0, 0.0);
+            cs.seed = o->seed;
+            cs.active = c < ncols ? 1 : 0;
+            cs.row = c < ncols ? h->orb2pad_h[q.cols[c0 + c]] : -1;
+            cs.nfun = q.proj == PROJ_ROWS && c < ncols ? (int)(q.row_ptr[c0 + c + 1] - q.row_ptr[c0 + c])
+                                                       : (q.proj == PROJ_SROW ? 1 : 0);
+            colh[c] = cs;
+            if (q.proj == PROJ_ROWS) {
+                for (int m = 0; m < M; ++m) {
+                    int v = 0;
+                    if (c < ncols && m < cs.nfun) v = h->orb2pad_h[q.rows[q.row_ptr[c0 + c] + m]];
+                    frowh[(size_t)c * M + m] = v;
+                }
+            }
+        }
+        TB_CK(cudaMemcpyAsync(p.col, colh.data(), sizeof(ColState) * P, cudaMemcpyHostToDevice, st));
+        TB_CK(cudaMemsetAsync(p.inner, 0, sizeof(InnerState) * 2 * P, st));
+        TB_CK(cudaMemsetAsync(p.flags, 0, sizeof(int) * 4, st));
+        if (q.proj == PROJ_ROWS)
+            TB_CK(cudaMemcpyAsync(p.frow, frowh.data(), sizeof(int32_t) * P * M, cudaMemcpyHostToDevice, st));
+
+        // r_0 = e_j, r'_0 = S^-1 r_0, rho_0, pi = 1, x^k = 0, p^k = r'_0
+        launch_panel_init(h->ds, p, st);
+        if ((s = inner_cg(h, p, o->inner_max_iter, pred, inner_total, st)) != TB_OK) return s;
+        if (h->flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
+        launch_finish(h->ds, p, st);
+        launch_shift_init(h->ds, p, st);
+        TB_CK(cudaGetLastError());
+
+        int active = ncols;
+        for (int n = 0; n < o->max_iter && active > 0; ++n) {
+            launch_outer_spmm(h->ds, p, st);
+            launch_outer_update(h->ds, p, st);
+            s = inner_cg(h, p, o->inner_max_iter, pred, inner_total, st);
+            if (s != TB_OK) return s;
+            active = h->flags_host[2];     // columns still active after step n-1
+            errbits |= h->flags_host[0];
+            if (errbits & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
+            if (active == 0) break;
+            launch_finish(h->ds, p, st);
+            launch_shift_step(h->ds, p, st);
+            if (q.proj == PROJ_NONE) launch_full_update(h->ds, p, st);
+            TB_CK(cudaGetLastError());
+        }
+        // outputs of this panel
+        if (q.proj == PROJ_NONE)
+            launch_full_output(p, h->orb2pad, (int)h->n_orb, R, ncols, c0, q.x_out, st);
+        else if (q.proj == PROJ_ROWS)
+            launch_green_output(p, ncols, off_dev + c0, q.g_out, st);
+        else
+            launch_mulliken_output(p, ncols, w_dev, q.g_s, q.q_out + c0, st);
+        TB_CK(cudaGetLastError());
+        TB_CK(cudaMemcpyAsync(colh.data(), p.col, sizeof(ColState) * P, cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaMemcpyAsync(convh.data(), p.conv_iter, sizeof(int32_t) * P * K, cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaStreamSynchronize(st));
+        errbits |= h->flags_host[0];
+        for (int c = 0; c < ncols; ++c) {
+            outer_total += colh[c].iters;
+            max_col_iters = std::max<int64_t>(max_col_iters, colh[c].iters);
+            switches += colh[c].switches;
+            for (int k = 0; k < K; ++k) {
+                const int ci = convh[(size_t)c * K + k];
+                if (ci < 0) ++unconverged;
+                if (stats && stats->conv_iter) stats->conv_iter[(size_t)(c0 + c) * K + k] = ci;
+            }
+        }
+    }
+    if (errbits & ERR_NOT_SPD) final_status = TB_ERR_S_NOT_SPD;
+    else if (errbits & ERR_BREAKDOWN) final_status = TB_ERR_BREAKDOWN;
+    else if (unconverged > 0) final_status = TB_ERR_NOT_CONVERGED;
+    if (stats) {
+        stats->outer_iterations = outer_total;
+        stats->inner_iterations = inner_total;
+        stats->max_column_iterations = max_col_iters;
+        stats->switches = switches;
+        stats->unconverged = unconverged;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return final_status;
+}
+
+tb_status check_cols(const tb_handle* h, int R, const int32_t* cols) {
+    if (R < 1 || !cols) return TB_ERR_INVALID_ARG;
+    for (int c = 0; c < R; ++c)
+        if (cols[c] < 0 || cols[c] >= h->n_orb) return TB_ERR_INVALID_ARG;
+    return TB_OK;
+}
+
+tb_status check_shifts(int K, const double* z, const tb_solve_opts* o) {
+    if (K < 1 || K > MAX_K || !z) return TB_ERR_INVALID_ARG;
+    if (o->seed >= K) return TB_ERR_INVALID_ARG;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(z[k])) return TB_ERR_INVALID_ARG;
+    return TB_OK;
+}
+
+// Output staging: write straight into device memory, or into a temporary
+// that is copied to the caller's host buffer at the end.
+struct OutBuf {
+    void* user = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+};
+
+tb_status out_prepare(Cleanup& cl, OutBuf& ob, void* user, size_t bytes) {
+    ob.user = user;
+    ob.bytes = bytes;
+    ob.host = !is_device_ptr(user);
+    if (!ob.host) {
+        ob.dev = user;
+        return TB_OK;
+    }
+    char* d = nullptr;
+    tb_status s = dalloc(cl, &d, bytes);
+    ob.dev = d;
+    return s;
+}
+
+tb_status out_finish(const OutBuf& ob, cudaStream_t st) {
+    if (ob.host) TB_CK(cudaMemcpyAsync(ob.user, ob.dev, ob.bytes, cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaStreamSynchronize(st));
+    return TB_OK;
+}
+
+tb_status merge(tb_status run, tb_status fin) { return run != TB_OK && run != TB_ERR_NOT_CONVERGED ? run : (fin != TB_OK ? fin : run); }
+
+}  // namespace
+
+extern "C" {
+
+const char* tb_status_string(tb_status s) {
+    switch (s) {
+        case TB_OK: return "TB_OK";
+        case TB_ERR_INVALID_ARG: return "TB_ERR_INVALID_ARG";
+        case TB_ERR_NOT_SYMMETRIC: return "TB_ERR_NOT_SYMMETRIC";
+        case TB_ERR_S_NOT_SPD: return "TB_ERR_S_NOT_SPD";
+        case TB_ERR_OOM: return "TB_ERR_OOM";
+        case TB_ERR_CUDA: return "TB_ERR_CUDA";
+        case TB_ERR_NOT_CONVERGED: return "TB_ERR_NOT_CONVERGED";
+        case TB_ERR_BREAKDOWN: return "TB_ERR_BREAKDOWN";
+        case TB_ERR_TIMEOUT: return "TB_ERR_TIMEOUT";
+        case TB_ERR_NO_DEVICE: return "TB_ERR_NO_DEVICE";
+    }
+    return "TB_UNKNOWN_STATUS";
+}
+
+void tb_default_opts(tb_solve_opts* o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->inner_tol = 1e-13;
+    o->max_iter = 100000;
+    o->inner_max_iter = 1000;
+    o->panel = 0;
+    o->seed = 0;
+    o->switching = 1;
+    o->force_switch_every = 0;
+}
+
+int64_t tb_num_orbitals(const tb_handle* h) { return h ? h->n_orb : 0; }
+int64_t tb_num_atoms(const tb_handle* h) { return h ? h->n_atoms : 0; }
+int64_t tb_num_blocks(const tb_handle* h) { return h ? h->ds.nb : 0; }
+
+tb_status tb_destroy(tb_handle* h) {
+    if (!h) return TB_OK;
+    cudaFree(h->ds.brow);
+    cudaFree(h->ds.bcol);
+    cudaFree(h->ds.S);
+    cudaFree(h->ds.H);
+    cudaFree(h->orb2pad);
+    cudaFree(h->eps_pad);
+    if (h->flags_host) cudaFreeHost(h->flags_host);
+    delete h;
+    return TB_OK;
+}
+
+tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
+    if (!out) return TB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d || d->n_atoms < 1 || !d->orb_per_atom || !d->brow_ptr || !d->bcol || !d->S_vals) return TB_ERR_INVALID_ARG;
+    if (d->precision != TB_FP64) return TB_ERR_INVALID_ARG;
+    if (!d->H_vals && (!d->eps || !std::isfinite(d->K))) return TB_ERR_INVALID_ARG;
+    const int n = d->n_atoms;
+    if ((int64_t)n * 4 > (int64_t)1 << 30) return TB_ERR_INVALID_ARG;
+    // ---- structure ----
+    std::vector<int64_t> ooff(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const int o = d->orb_per_atom[i];
+        if (o != 1 && o != 4) return TB_ERR_INVALID_ARG;
+        ooff[i + 1] = ooff[i] + o;
+    }
+    const int64_t N = ooff[n];
+    if (d->brow_ptr[0] != 0) return TB_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (d->brow_ptr[i + 1] < d->brow_ptr[i]) return TB_ERR_INVALID_ARG;
+    const int64_t nb = d->brow_ptr[n];
+    if (nb < n || nb > INT32_MAX) return TB_ERR_INVALID_ARG;
+    std::vector<int64_t> boff(nb + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        bool diag = false;
+        for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
+            const int j = d->bcol[b];
+            if (j < 0 || j >= n) return TB_ERR_INVALID_ARG;
+            if (b > d->brow_ptr[i] && d->bcol[b - 1] >= j) return TB_ERR_INVALID_ARG;
+            if (j == i) diag = true;
+            boff[b + 1] = boff[b] + (int64_t)d->orb_per_atom[i] * d->orb_per_atom[j];
+        }
+        if (!diag) return TB_ERR_INVALID_ARG;
+    }
+    // ---- symmetry of pattern and values ----
+    double smax = 0.0, hmax = 0.0;
+    for (int64_t e = 0; e < boff[nb]; ++e) {
+        if (!std::isfinite(d->S_vals[e])) return TB_ERR_INVALID_ARG;
+        smax = std::max(smax, std::fabs(d->S_vals[e]));
+        if (d->H_vals) {
+            if (!std::isfinite(d->H_vals[e])) return TB_ERR_INVALID_ARG;
+            hmax = std::max(hmax, std::fabs(d->H_vals[e]));
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        const int ni = d->orb_per_atom[i];
+        for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
+            const int j = d->bcol[b];
+            const int nj = d->orb_per_atom[j];
+            const int32_t* beg = d->bcol + d->brow_ptr[j];
+            const int32_t* end = d->bcol + d->brow_ptr[j + 1];
+            const int32_t* f = std::lower_bound(beg, end, (int32_t)i);
+            if (f == end || *f != i) return TB_ERR_NOT_SYMMETRIC;
+            const int64_t bt = d->brow_ptr[j] + (f - beg);
+            for (int a = 0; a < ni; ++a)
+                for (int c = 0; c < nj; ++c) {
+                    const double s1 = d->S_vals[boff[b] + (int64_t)a * nj + c];
+                    const double s2 = d->S_vals[boff[bt] + (int64_t)c * ni + a];
+                    if (std::fabs(s1 - s2) > 1e-12 * smax) return TB_ERR_NOT_SYMMETRIC;
+                    if (d->H_vals) {
+                        const double h1 = d->H_vals[boff[b] + (int64_t)a * nj + c];
+                        const double h2 = d->H_vals[boff[bt] + (int64_t)c * ni + a];
+                        if (std::fabs(h1 - h2) > 1e-12 * hmax) return TB_ERR_NOT_SYMMETRIC;
+                    }
+                }
+        }
+        // diagonal of S must be positive
+        for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b)
+            if (d->bcol[b] == i)
+                for (int a = 0; a < ni; ++a)
+                    if (!(d->S_vals[boff[b] + (int64_t)a * ni + a] > 0.0)) return TB_ERR_S_NOT_SPD;
+    }
+    if (!d->H_vals)
+        for (int64_t o = 0; o < N; ++o)
+            if (!std::isfinite(d->eps[o])) return TB_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return TB_ERR_NO_DEVICE;
+    }
+    // ---- padded host copies ----
+    std::vector<double> Sp((size_t)nb * 16, 0.0), Hp;
+    if (d->H_vals) Hp.assign((size_t)nb * 16, 0.0);
+    std::vector<int> browh(n + 1), bcolh(nb);
+    for (int i = 0; i <= n; ++i) browh[i] = (int)d->brow_ptr[i];
+    for (int64_t b = 0; b < nb; ++b) bcolh[b] = d->bcol[b];
+    for (int i = 0; i < n; ++i) {
+        const int ni = d->orb_per_atom[i];
+        for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
+            const int j = d->bcol[b], nj = d->orb_per_atom[j];
+            for (int a = 0; a < ni; ++a)
+                for (int c = 0; c < nj; ++c) {
+                    Sp[16 * b + 4 * a + c] = d->S_vals[boff[b] + (int64_t)a * nj + c];
+                    if (d->H_vals) Hp[16 * b + 4 * a + c] = d->H_vals[boff[b] + (int64_t)a * nj + c];
+                }
+            if (j == i)
+                for (int a = ni; a < 4; ++a) Sp[16 * b + 5 * a] = 1.0;   // padded slot: S = 1, H = 0
+        }
+    }
+    std::vector<double> epsp((size_t)4 * n, 0.0);
+    std::vector<int32_t> o2p(N);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < d->orb_per_atom[i]; ++a) {
+            o2p[ooff[i] + a] = 4 * i + a;
+            if (d->eps) epsp[4 * i + a] = d->eps[ooff[i] + a];
+        }
+    // ---- device ----
+    tb_handle* h = new tb_handle();
+    h->n_atoms = n;
+    h->n_orb = N;
+    h->orb_per_atom.assign(d->orb_per_atom, d->orb_per_atom + n);
+    h->orb2pad_h = o2p;
+    h->ds.n_atoms = n;
+    h->ds.nb = nb;
+    h->ds.npad = 4 * n;
+    cudaGetDevice(&h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto fail = [&](cudaError_t e) {
+        cudaGetLastError();
+        tb_destroy(h);
+        return e == cudaErrorMemoryAllocation ? TB_ERR_OOM : TB_ERR_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->ds.brow, sizeof(int) * (n + 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.bcol, sizeof(int) * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.S, sizeof(double) * 16 * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.H, sizeof(double) * 16 * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->orb2pad, sizeof(int32_t) * N)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->eps_pad, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost(&h->flags_host, 4 * sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->ds.brow, browh.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->ds.bcol, bcolh.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->ds.S, Sp.data(), sizeof(double) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->orb2pad, o2p.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->eps_pad, epsp.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if (d->H_vals) {
+        if ((e = cudaMemcpyAsync(h->ds.H, Hp.data(), sizeof(double) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    } else {
+        launch_ased_build(h->ds, h->eps_pad, d->K, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    *out = h;
+    return TB_OK;
+}
+
+tb_status tb_shifted_cocg(tb_handle* h, int32_t K, const double* z, int32_t R, const int32_t* cols,
+                          const tb_solve_opts* opts, double* x_out, tb_stats* stats, void* stream) {
+    if (!h || !x_out) return TB_ERR_INVALID_ARG;
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    if ((s = check_cols(h, R, cols)) != TB_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    OutBuf ob;
+    if ((s = out_prepare(cl, ob, x_out, sizeof(double2) * (size_t)K * R * h->n_orb)) != TB_OK) return s;
+    Solve q;
+    q.K = K; q.z = z; q.R = R; q.cols = cols; q.proj = PROJ_NONE;
+    q.x_out = static_cast<double2*>(ob.dev);
+    const tb_status run = run_solve(h, q, opts, stats, st);
+    return merge(run, out_finish(ob, st));
+}
+
+tb_status tb_green_elements(tb_handle* h, int32_t K, const double* z, int32_t R, const int32_t* cols,
+                            const int64_t* row_ptr, const int32_t* rows, const tb_solve_opts* opts,
+                            double* G_out, tb_stats* stats, void* stream) {
+    if (!h || !G_out || !row_ptr || !rows) return TB_ERR_INVALID_ARG;
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    if ((s = check_cols(h, R, cols)) != TB_OK) return s;
+    if (row_ptr[0] != 0) return TB_ERR_INVALID_ARG;
+    for (int c = 0; c < R; ++c) {
+        const int64_t m = row_ptr[c + 1] - row_ptr[c];
+        if (m < 1 || m > MAX_M) return TB_ERR_INVALID_ARG;
+    }
+    for (int64_t e = 0; e < row_ptr[R]; ++e)
+        if (rows[e] < 0 || rows[e] >= h->n_orb) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    OutBuf ob;
+    if ((s = out_prepare(cl, ob, G_out, sizeof(double2) * (size_t)row_ptr[R] * K)) != TB_OK) return s;
+    Solve q;
+    q.K = K; q.z = z; q.R = R; q.cols = cols; q.proj = PROJ_ROWS; q.row_ptr = row_ptr; q.rows = rows;
+    q.g_out = static_cast<double2*>(ob.dev);
+    const tb_status run = run_solve(h, q, opts, stats, st);
+    return merge(run, out_finish(ob, st));
+}
+
+tb_status tb_mulliken_orbital(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,
+                              int32_t R, const int32_t* cols, const tb_solve_opts* opts, double* q_out,
+                              tb_stats* stats, void* stream) {
+    if (!h || !q_out || !w || !std::isfinite(g_s)) return TB_ERR_INVALID_ARG;
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    if ((s = check_cols(h, R, cols)) != TB_OK) return s;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(w[k])) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    OutBuf ob;
+    if ((s = out_prepare(cl, ob, q_out, sizeof(double) * (size_t)R)) != TB_OK) return s;
+    Solve q;
+    q.K = K; q.z = z; q.R = R; q.cols = cols; q.proj = PROJ_SROW; q.w = w; q.g_s = g_s;
+    q.q_out = static_cast<double*>(ob.dev);
+    const tb_status run = run_solve(h, q, opts, stats, st);
+    return merge(run, out_finish(ob, st));
+}
+
+tb_status tb_mulliken_charges(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,
+                              const tb_solve_opts* opts, double* q_out, tb_stats* stats, void* stream) {
+    if (!h || !q_out) return TB_ERR_INVALID_ARG;
+    std::vector<int32_t> cols(h->n_orb);
+    for (int64_t o = 0; o < h->n_orb; ++o) cols[o] = (int32_t)o;
+    std::vector<double> qo(h->n_orb);
+    const tb_status run = tb_mulliken_orbital(h, K, z, w, g_s, (int32_t)h->n_orb, cols.data(), opts, qo.data(),
+                                              stats, stream);
+    if (run != TB_OK && run != TB_ERR_NOT_CONVERGED) return run;
+    std::vector<double> qa(h->n_atoms, 0.0);
+    int64_t o = 0;
+    for (int i = 0; i < h->n_atoms; ++i)
+        for (int a = 0; a < h->orb_per_atom[i]; ++a) qa[i] += qo[o++];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (is_device_ptr(q_out)) {
+        TB_CK(cudaMemcpyAsync(q_out, qa.data(), sizeof(double) * h->n_atoms, cudaMemcpyHostToDevice, st));
+        TB_CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(q_out, qa.data(), sizeof(double) * h->n_atoms);
+    }
+    return run;
+}
+
+tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, double inner_tol, double* a,
+                                 double* b, double* norm, void* stream) {
+    if (!h || !a || !b || !norm || n_steps < 1 || j < 0 || j >= h->n_orb) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    tb_status s;
+    const int npad = h->ds.npad;
+    PanelDev p;
+    p.P = 1;
+    p.K = 1;
+    p.npad = npad;
+    p.grid = max_grid();
+    p.inner_tol = inner_tol > 0.0 ? inner_tol : 1e-13;
+    double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
+    for (double2** v : vecs)
+        if ((s = dalloc(cl, v, npad)) != TB_OK) return s;
+    double2 *U, *Uprev, *Wv;
+    if ((s = dalloc(cl, &U, npad)) != TB_OK) return s;
+    if ((s = dalloc(cl, &Uprev, npad)) != TB_OK) return s;
+    if ((s = dalloc(cl, &Wv, npad)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.col, 1)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.inner, 2)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.partials, (size_t)p.grid * 4)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.counter, 1)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.flags, 4)) != TB_OK) return s;
+    double *ad, *bd, *nd;
+    if ((s = dalloc(cl, &ad, n_steps)) != TB_OK) return s;
+    if ((s = dalloc(cl, &bd, (size_t)n_steps + 1)) != TB_OK) return s;
+    if ((s = dalloc(cl, &nd, 1)) != TB_OK) return s;
+    ColState cs;
+    std::memset(&cs, 0, sizeof(cs));
+    cs.active = 1;
+    cs.row = h->orb2pad_h[j];
+    TB_CK(cudaMemcpyAsync(p.col, &cs, sizeof(cs), cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemsetAsync(p.inner, 0, 2 * sizeof(InnerState), st));
+    TB_CK(cudaMemsetAsync(p.flags, 0, 4 * sizeof(int), st));
+    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned), st));
+    TB_CK(cudaMemsetAsync(Uprev, 0, sizeof(double2) * npad, st));
+    TB_CK(cudaMemsetAsync(ad, 0, sizeof(double) * n_steps, st));
+    TB_CK(cudaMemsetAsync(bd, 0, sizeof(double) * (n_steps + 1), st));
+    int pred = 64;
+    int64_t inner_total = 0;
+    const int inner_max = 1000;
+    launch_panel_init(h->ds, p, st);
+    if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
+    launch_lz_start(p, p.Rp, cs.row, U, nd, st);
+    for (int n = 0; n < n_steps; ++n) {
+        launch_lz_spmv(h->ds, h->ds.H, U, p.W, st);                  // H u^n
+        launch_lz_dot(p, U, p.W, ad + n, 0, st);                     // a_n = u^T H u
+        TB_CK(cudaMemcpyAsync(p.Rin, p.W, sizeof(double2) * npad, cudaMemcpyDeviceToDevice, st));
+        if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;   // S^-1 H u^n
+        launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, st);  // w = S^-1 H u - a u - b u_prev
+        launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, st);                 // S w
+        launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, st);                // b_{n+1} = ||w||_S
+        launch_lz_scale(p, Wv, U, Uprev, bd + n + 1, st);
+        TB_CK(cudaGetLastError());
+    }
+    if (h->flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
+    const bool ad_dev = is_device_ptr(a), bd_dev = is_device_ptr(b), nd_dev = is_device_ptr(norm);
+    TB_CK(cudaMemcpyAsync(a, ad, sizeof(double) * n_steps, ad_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaMemcpyAsync(b, bd, sizeof(double) * (n_steps + 1), bd_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaMemcpyAsync(norm, nd, sizeof(double), nd_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaStreamSynchronize(st));
+    return TB_OK;
+}
+
+}  // extern "C"

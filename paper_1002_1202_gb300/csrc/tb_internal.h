@@ -1,0 +1,119 @@
+// Internal declarations shared by the kernels (tb_kernels.cu) and the host
+// orchestration (tb_api.cu).  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tb {
+
+constexpr int THREADS = 256;   // every kernel runs 256-thread CTAs
+constexpr int MAX_P = 256;     // right-hand sides per panel (power of two)
+constexpr int MAX_K = 1024;    // shifts per call
+constexpr int MAX_M = 1024;    // projected rows per column
+
+// error bits in PanelDev::flags[0]
+constexpr int ERR_BREAKDOWN = 1;
+constexpr int ERR_NOT_SPD = 2;
+
+// functional kinds of the projected mode
+constexpr int PROJ_NONE = 0;   // full solutions kept (x^k, p^k are N-vectors)
+constexpr int PROJ_ROWS = 1;   // G elements: unit vectors e_row
+constexpr int PROJ_SROW = 2;   // Mulliken: s_j = row j of S (one functional)
+
+// Device copy of the block-sparse system.  Atoms are padded to 4 orbital
+// slots (s, px, py, pz); a padded slot has S = 1 on its diagonal and no
+// coupling, so it stays exactly zero in every vector.
+struct DevSystem {
+    int n_atoms = 0;
+    int64_t nb = 0;
+    int npad = 0;              // 4 * n_atoms
+    int* brow = nullptr;       // [n_atoms + 1]
+    int* bcol = nullptr;       // [nb]
+    double* S = nullptr;       // [nb][16] row-major 4x4 blocks
+    double* H = nullptr;       // [nb][16]
+};
+
+// Per right-hand side (complex column) state of a panel.
+struct ColState {
+    double2 zs;          // seed shift z_s
+    double2 alpha;       // alpha_n of the current step
+    double2 alpha_prev;  // alpha_{n-1}
+    double2 beta_prev;   // beta_{n-1}
+    double2 rho;         // rho_n = r_n^T r'_n
+    double2 rho_new;     // rho_{n+1}
+    double2 sc_cur;      // pending scale of r_n and r'_n (seed switch)
+    double2 sc_prev;     // pending scale of r_{n-1}
+    double rnorm;        // ||r_{n+1}||_2
+    int32_t seed;        // index of the seed shift
+    int32_t active;      // 1 while some shift of the column is unconverged
+    int32_t iters;       // outer steps run
+    int32_t switches;    // seed switches
+    int32_t row;         // padded orbital index of e_j, -1 for a dummy column
+    int32_t n_unconv;    // unconverged shifts
+    int32_t nfun;        // projected functionals of this column
+    int32_t pad_;
+};
+
+// Per real column (two per complex column) state of the inner CG.
+struct InnerState {
+    double gamma_prev;
+    double alpha;
+    double beta;
+    double bnorm2;
+    int32_t conv;
+    int32_t pad_;
+};
+
+struct PanelDev {
+    int P = 0, K = 0, npad = 0, M = 0, proj = PROJ_NONE;
+    int grid = 0;                 // CTAs of the grid-stride kernels
+    double tol = 1e-10, inner_tol = 1e-13;
+    int switching = 1, force_switch_every = 0;
+    // panel vectors, [npad][P] complex
+    double2 *Rcur = nullptr, *Rprev = nullptr, *Rp = nullptr, *W = nullptr;
+    double2 *Rin = nullptr, *Pin = nullptr, *Sin = nullptr;
+    ColState* col = nullptr;       // [P]
+    InnerState* inner = nullptr;   // [2P]
+    double2* z = nullptr;          // [K]
+    double2 *pi = nullptr, *pi_prev = nullptr;   // [P][K]
+    int32_t* conv_iter = nullptr;                // [P][K]
+    double2 *ak = nullptr, *bk = nullptr, *ipi = nullptr;  // [P][K] this step (full mode)
+    int32_t* frow = nullptr;       // [P][M] padded rows (PROJ_ROWS)
+    double2 *t = nullptr, *u = nullptr;          // [P][K][M] projected x, p
+    double2 *X = nullptr, *Pk = nullptr;         // [K][npad][P] full mode x, p
+    double* partials = nullptr;    // [grid][4][P]
+    unsigned* counter = nullptr;   // arrival counter of the last-CTA reductions
+    int* flags = nullptr;          // [4]: errors, inner active, active columns, inner iters
+};
+
+// ---- launchers (tb_kernels.cu) -------------------------------------------
+void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st);
+void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_outer_spmm(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_outer_update(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_inner_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
+void launch_inner_update(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
+void launch_finish(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_full_update(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_full_output(const PanelDev& p, const int32_t* orb2pad, int n_orb, int R, int ncols,
+                        int c0, double2* out, cudaStream_t st);
+void launch_green_output(const PanelDev& p, int ncols, const int64_t* out_off, double2* out,
+                         cudaStream_t st);
+void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
+                            cudaStream_t st);
+
+// generalized Lanczos helpers (single real column carried in a P = 1 panel)
+void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, cudaStream_t st);
+void launch_lz_dot(const PanelDev& p, const double2* x, const double2* y, double* out, int mode,
+                   cudaStream_t st);
+void launch_lz_combine(const PanelDev& p, const double2* y, double2* u, double2* u_prev, double2* w,
+                       const double* a, const double* b, cudaStream_t st);
+void launch_lz_scale(const PanelDev& p, double2* w, double2* u, double2* u_prev, const double* bnext,
+                     cudaStream_t st);
+void launch_lz_start(const PanelDev& p, const double2* v, int row, double2* u, double* nrm2,
+                     cudaStream_t st);
+
+}  // namespace tb

@@ -1,0 +1,782 @@
+// CUDA kernels of the generalized shifted COCG hot path (sm_103a).
+//
+// Data layout (device, HBM):
+//   * S and H: block-sparse rows over atoms, every block padded to 4x4
+//     (row-major doubles), block row I covering padded orbitals 4I..4I+3;
+//   * panel vectors: [npad][P] complex doubles (double2), the P right-hand
+//     sides of a panel interleaved per orbital row, so one atom's 4 rows of a
+//     panel are 4*P*16 contiguous bytes and a CTA's loads are coalesced along
+//     the column index.
+//
+// Reductions are deterministic: each CTA writes per-column partial sums, the
+// last CTA to arrive (atomic ticket) adds the partials in CTA order and
+// turns them into the step's scalars.  Grid sizes are fixed per launch, so
+// the summation order never changes between runs.
+#include "tb_internal.h"
+
+#include <math.h>
+
+namespace tb {
+
+namespace {
+
+__device__ __forceinline__ double2 cmk(double r, double i) { return make_double2(r, i); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// complex division by Smith's method (no intermediate overflow of |b|^2)
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, den = b.x + b.y * r;
+        return cmk((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+    }
+    double r = b.x / b.y, den = b.y + b.x * r;
+    return cmk((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+}
+__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
+
+// Sum NV per-thread values over the threads of a CTA that share a column
+// (column = tid % P).  Result for column c (< P) in smem[q*THREADS + c].
+template <int NV>
+__device__ void block_reduce_cols(const double (&v)[NV], int P, double* smem) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) smem[q * THREADS + tid] = v[q];
+    __syncthreads();
+    for (int s = (THREADS / P) / 2; s >= 1; s >>= 1) {
+        if (tid < s * P) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) smem[q * THREADS + tid] += smem[q * THREADS + tid + s * P];
+        }
+        __syncthreads();
+    }
+}
+
+// Grid-wide per-column sums.  Returns true in the last CTA to finish, whose
+// threads tid < P then find the total of column tid in smem[q*THREADS + tid].
+template <int NV>
+__device__ bool grid_reduce_cols(const double (&v)[NV], int P, double* partials, unsigned* counter,
+                                 double* smem) {
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    block_reduce_cols<NV>(v, P, smem);
+    if (tid < P) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[((size_t)blockIdx.x * NV + q) * P + tid] = smem[q * THREADS + tid];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    const int c = tid % P, g = tid / P, G = THREADS / P;
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    for (int b = g; b < (int)gridDim.x; b += G) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&partials[((size_t)b * NV + q) * P + c]);
+    }
+    __syncthreads();
+    block_reduce_cols<NV>(acc, P, smem);
+    if (tid == 0) *counter = 0u;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// ASED Hamiltonian (Section 2.2, Eq. Hap-1) built from S on the device.
+// ---------------------------------------------------------------------------
+__global__ void k_ased_build(int n_atoms, const int* __restrict__ brow, const int* __restrict__ bcol,
+                             const double* __restrict__ S, double* __restrict__ H,
+                             const double* __restrict__ eps, double K) {
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < n_atoms; I += gridDim.x * blockDim.x) {
+        for (int b = brow[I]; b < brow[I + 1]; ++b) {
+            const int J = bcol[b];
+            for (int a = 0; a < 4; ++a) {
+                for (int c = 0; c < 4; ++c) {
+                    double h;
+                    if (I == J) h = (a == c) ? eps[4 * I + a] : 0.0;   // on-site level
+                    else h = K * 0.5 * (eps[4 * I + a] + eps[4 * J + c]) * S[16 * (size_t)b + 4 * a + c];
+                    H[16 * (size_t)b + 4 * a + c] = h;
+                }
+            }
+        }
+    }
+}
+
+// r_0 = b = e_j, r_{-1} = 0, inner right-hand side = b
+__global__ void k_panel_init(PanelDev p) {
+    const long long items = (long long)p.npad * p.P;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const int c = (int)(idx % p.P), i = (int)(idx / p.P);
+        const double2 v = cmk(i == p.col[c].row ? 1.0 : 0.0, 0.0);
+        p.Rcur[idx] = v;
+        p.Rin[idx] = v;
+        p.Rprev[idx] = cmk(0.0, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a1 + a2: q = A(z_s) r'_n = z_s S r'_n - H r'_n in one pass over the blocks,
+// A p_n = q + (beta_{n-1}/alpha_{n-1}) (r_{n-1} - r_n), mu = r'_n^T A p_n,
+// alpha_n = rho_n / mu (Eqs. CGp:p, CGp:r and the alpha_n of Section 3.3).
+// Pending seed-switch scales of r_n, r'_n, r_{n-1} are applied on the fly.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p) {
+    __shared__ double smem[2 * THREADS];
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    const ColState cs = p.col[c];
+    const bool act = cs.active != 0;
+    const double2 sc = cs.sc_cur, scp = cs.sc_prev;
+    const double2 coef = act ? cdiv(cs.beta_prev, cs.alpha_prev) : cmk(0.0, 0.0);
+    double mu[2] = {0.0, 0.0};
+    const long long items = (long long)s.n_atoms * P;
+    if (act) {
+        for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+             idx += (long long)gridDim.x * THREADS) {
+            const int I = (int)(idx / P);
+            double2 aS[4], aH[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) { aS[a] = cmk(0.0, 0.0); aH[a] = cmk(0.0, 0.0); }
+            for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
+                const int J = s.bcol[b];
+                const double2* xr = p.Rp + (size_t)4 * J * P + c;
+                const double2 x0 = xr[0], x1 = xr[P], x2 = xr[2 * P], x3 = xr[3 * P];
+                const double2* Sb = reinterpret_cast<const double2*>(s.S + 16 * (size_t)b);
+                const double2* Hb = reinterpret_cast<const double2*>(s.H + 16 * (size_t)b);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const double2 s01 = __ldg(Sb + 2 * a), s23 = __ldg(Sb + 2 * a + 1);
+                    const double2 h01 = __ldg(Hb + 2 * a), h23 = __ldg(Hb + 2 * a + 1);
+                    aS[a].x += s01.x * x0.x + s01.y * x1.x + s23.x * x2.x + s23.y * x3.x;
+                    aS[a].y += s01.x * x0.y + s01.y * x1.y + s23.x * x2.y + s23.y * x3.y;
+                    aH[a].x += h01.x * x0.x + h01.y * x1.x + h23.x * x2.x + h23.y * x3.x;
+                    aH[a].y += h01.x * x0.y + h01.y * x1.y + h23.x * x2.y + h23.y * x3.y;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const size_t e = (size_t)(4 * I + a) * P + c;
+                const double2 q = cmul(sc, csub(cmul(cs.zs, aS[a]), aH[a]));
+                const double2 rc = cmul(sc, p.Rcur[e]);
+                const double2 rpv = cmul(scp, p.Rprev[e]);
+                const double2 Ap = cadd(q, cmul(coef, csub(rpv, rc)));
+                p.W[e] = Ap;
+                const double2 m = cmul(cmul(sc, p.Rp[e]), Ap);
+                mu[0] += m.x;
+                mu[1] += m.y;
+            }
+        }
+    }
+    if (grid_reduce_cols<2>(mu, P, p.partials, p.counter, smem)) {
+        const int t = threadIdx.x;
+        if (t < P && p.col[t].active) {
+            const double2 m = cmk(smem[t], smem[THREADS + t]);
+            const double2 rho = p.col[t].rho;
+            if ((m.x == 0.0 && m.y == 0.0) || (rho.x == 0.0 && rho.y == 0.0) || !isfinite(m.x) ||
+                !isfinite(m.y)) {
+                atomicOr(&p.flags[0], ERR_BREAKDOWN);
+                p.col[t].active = 0;
+            } else {
+                p.col[t].alpha = cdiv(rho, m);
+            }
+        }
+    }
+}
+
+// r_{n+1} = r_n - alpha_n A p_n; r_n becomes r_{n-1}; the inner CG starts
+// from b = r_{n+1}.
+__global__ void k_outer_update(PanelDev p) {
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    const ColState cs = p.col[c];
+    if (!cs.active) return;
+    const long long items = (long long)p.npad * P;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const double2 rc = cmul(cs.sc_cur, p.Rcur[idx]);
+        const double2 rn = csub(rc, cmul(cs.alpha, p.W[idx]));
+        p.Rprev[idx] = rc;
+        p.Rcur[idx] = rn;
+        p.Rin[idx] = rn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3 + a4: inner CG for S r' = r (Section 3.3), both real parts of every
+// complex column, Chronopoulos-Gear form (one reduction per iteration):
+//   w_i = S r_i, gamma_i = r_i.r_i, delta_i = w_i.r_i,
+//   beta_i = gamma_i/gamma_{i-1}, alpha_i = gamma_i/(delta_i - beta_i gamma_i/alpha_{i-1}),
+//   p_i = r_i + beta_i p_{i-1}, s_i = w_i + beta_i s_{i-1},
+//   x_{i+1} = x_i + alpha_i p_i, r_{i+1} = r_i - alpha_i s_i,   x_0 = 0.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS) k_inner_spmv(DevSystem s, PanelDev p, int it) {
+    __shared__ double smem[4 * THREADS];
+    if (it > 0 && *(volatile int*)&p.flags[1] == 0) return;
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    const bool act = p.col[c].active != 0;
+    const bool live = act && !(p.inner[2 * c].conv && p.inner[2 * c + 1].conv && it > 0);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};   // gamma_re, gamma_im, delta_re, delta_im
+    const long long items = (long long)s.n_atoms * P;
+    if (live) {
+        for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+             idx += (long long)gridDim.x * THREADS) {
+            const int I = (int)(idx / P);
+            double2 acc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = cmk(0.0, 0.0);
+            for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
+                const int J = s.bcol[b];
+                const double2* xr = p.Rin + (size_t)4 * J * P + c;
+                const double2 x0 = xr[0], x1 = xr[P], x2 = xr[2 * P], x3 = xr[3 * P];
+                const double2* Sb = reinterpret_cast<const double2*>(s.S + 16 * (size_t)b);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const double2 s01 = __ldg(Sb + 2 * a), s23 = __ldg(Sb + 2 * a + 1);
+                    acc[a].x += s01.x * x0.x + s01.y * x1.x + s23.x * x2.x + s23.y * x3.x;
+                    acc[a].y += s01.x * x0.y + s01.y * x1.y + s23.x * x2.y + s23.y * x3.y;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const size_t e = (size_t)(4 * I + a) * P + c;
+                const double2 r = p.Rin[e];
+                p.W[e] = acc[a];
+                v[0] += r.x * r.x;
+                v[1] += r.y * r.y;
+                v[2] += acc[a].x * r.x;
+                v[3] += acc[a].y * r.y;
+            }
+        }
+    }
+    if (grid_reduce_cols<4>(v, P, p.partials, p.counter, smem)) {
+        const int t = threadIdx.x;
+        int nact = 0;
+        if (t < P) {
+            const bool cact = p.col[t].active != 0;
+            if (it == 0 && cact) p.col[t].rnorm = sqrt(smem[t] + smem[THREADS + t]);
+            for (int part = 0; part < 2; ++part) {
+                InnerState st = p.inner[2 * t + part];
+                const double gam = smem[part * THREADS + t];
+                const double del = smem[(2 + part) * THREADS + t];
+                if (it == 0) {
+                    st.bnorm2 = gam;
+                    st.conv = (!cact || gam == 0.0) ? 1 : 0;
+                }
+                if (!st.conv) {
+                    if (gam <= p.inner_tol * p.inner_tol * st.bnorm2) {
+                        st.conv = 1;
+                    } else {
+                        const double beta = (it == 0) ? 0.0 : gam / st.gamma_prev;
+                        const double den = del - ((it == 0) ? 0.0 : beta * gam / st.alpha);
+                        if (!(den > 0.0)) {
+                            atomicOr(&p.flags[0], ERR_NOT_SPD);
+                            st.conv = 1;
+                        } else {
+                            st.alpha = gam / den;
+                            st.beta = beta;
+                            st.gamma_prev = gam;
+                        }
+                    }
+                }
+                nact += st.conv ? 0 : 1;
+                p.inner[2 * t + part] = st;
+            }
+        }
+        // count unconverged real columns
+        __shared__ int s_cnt;
+        if (t == 0) s_cnt = 0;
+        __syncthreads();
+        if (nact) atomicAdd(&s_cnt, nact);
+        __syncthreads();
+        if (t == 0) {
+            p.flags[1] = s_cnt;
+            if (s_cnt == 0) p.flags[3] = it;
+        }
+    }
+}
+
+__global__ void k_inner_update(PanelDev p, int it) {
+    if (it > 0 && *(volatile int*)&p.flags[1] == 0) return;
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    if (!p.col[c].active) return;
+    const InnerState s0 = p.inner[2 * c], s1 = p.inner[2 * c + 1];
+    if (s0.conv && s1.conv && it > 0) return;
+    const long long items = (long long)p.npad * P;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const double2 r = p.Rin[idx], w = p.W[idx];
+        double2 pv = (it == 0) ? cmk(0.0, 0.0) : p.Pin[idx];
+        double2 sv = (it == 0) ? cmk(0.0, 0.0) : p.Sin[idx];
+        double2 x = (it == 0) ? cmk(0.0, 0.0) : p.Rp[idx];
+        double2 rn = r;
+        if (!s0.conv) {
+            pv.x = r.x + s0.beta * pv.x;
+            sv.x = w.x + s0.beta * sv.x;
+            x.x += s0.alpha * pv.x;
+            rn.x = r.x - s0.alpha * sv.x;
+        }
+        if (!s1.conv) {
+            pv.y = r.y + s1.beta * pv.y;
+            sv.y = w.y + s1.beta * sv.y;
+            x.y += s1.alpha * pv.y;
+            rn.y = r.y - s1.alpha * sv.y;
+        }
+        p.Pin[idx] = pv;
+        p.Sin[idx] = sv;
+        p.Rp[idx] = x;
+        p.Rin[idx] = rn;
+    }
+}
+
+// rho_{n+1} = r_{n+1}^T r'_{n+1} (unconjugated); also clears the count of
+// active columns that the shift step rebuilds.
+__global__ void __launch_bounds__(THREADS) k_finish(PanelDev p) {
+    __shared__ double smem[2 * THREADS];
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    double v[2] = {0.0, 0.0};
+    if (p.col[c].active) {
+        const long long items = (long long)p.npad * P;
+        for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+             idx += (long long)gridDim.x * THREADS) {
+            const double2 m = cmul(p.Rcur[idx], p.Rp[idx]);
+            v[0] += m.x;
+            v[1] += m.y;
+        }
+    }
+    if (grid_reduce_cols<2>(v, P, p.partials, p.counter, smem)) {
+        const int t = threadIdx.x;
+        if (t < P && p.col[t].active) p.col[t].rho_new = cmk(smem[t], smem[THREADS + t]);
+        if (t == 0) p.flags[2] = 0;
+    }
+}
+
+// Projected functionals f_m^T r' of column c into d[0..nfun).
+__device__ void eval_functionals(const DevSystem& s, const PanelDev& p, int c, int nfun, double2* d,
+                                 double* red) {
+    const int tid = threadIdx.x;
+    if (p.proj == PROJ_ROWS) {
+        for (int m = tid; m < nfun; m += THREADS) d[m] = p.Rp[(size_t)p.frow[(size_t)c * p.M + m] * p.P + c];
+    } else if (p.proj == PROJ_SROW) {
+        // s_j^T r' = sum over row j of S (S symmetric)
+        const int row = p.col[c].row, I = row >> 2, a = row & 3;
+        const int b0 = s.brow[I], nbl = s.brow[I + 1] - b0;
+        double re = 0.0, im = 0.0;
+        for (int e = tid; e < 4 * nbl; e += THREADS) {
+            const int b = b0 + e / 4, be = e % 4;
+            const double sv = s.S[16 * (size_t)b + 4 * a + be];
+            const double2 x = p.Rp[(size_t)(4 * s.bcol[b] + be) * p.P + c];
+            re += sv * x.x;
+            im += sv * x.y;
+        }
+        red[tid] = re;
+        red[THREADS + tid] = im;
+        __syncthreads();
+        for (int st = THREADS / 2; st >= 1; st >>= 1) {
+            if (tid < st) {
+                red[tid] += red[tid + st];
+                red[THREADS + tid] += red[THREADS + tid + st];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) d[0] = cmk(red[0], red[THREADS]);
+    }
+    __syncthreads();
+}
+
+// Initial shift state: pi_0 = pi_{-1} = 1, x^k_0 = 0, p^k_0 = r'_0 (projected:
+// u^k = f^T r'_0), rho_0 = r_0^T r'_0.
+__global__ void k_shift_init(DevSystem s, PanelDev p) {
+    extern __shared__ double2 dyn[];
+    __shared__ double red[2 * THREADS];
+    const int c = blockIdx.x, K = p.K;
+    ColState cs = p.col[c];
+    if (!cs.active) return;
+    const int nfun = cs.nfun;
+    double2* d = dyn;
+    if (p.proj != PROJ_NONE) eval_functionals(s, p, c, nfun, d, red);
+    for (int k = threadIdx.x; k < K; k += THREADS) {
+        p.pi[(size_t)c * K + k] = cmk(1.0, 0.0);
+        p.pi_prev[(size_t)c * K + k] = cmk(1.0, 0.0);
+        p.conv_iter[(size_t)c * K + k] = -1;
+    }
+    if (p.proj != PROJ_NONE) {
+        for (int e = threadIdx.x; e < K * nfun; e += THREADS) {
+            const int k = e / nfun, m = e % nfun;
+            const size_t o = ((size_t)c * K + k) * p.M + m;
+            p.t[o] = cmk(0.0, 0.0);
+            p.u[o] = d[m];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cs.rho = cs.rho_new;
+        cs.n_unconv = K;
+        p.col[c] = cs;
+        atomicAdd(&p.flags[2], 1);
+    }
+}
+
+__global__ void k_full_init(PanelDev p) {
+    const long long per = (long long)p.npad * p.P;
+    const long long items = per * p.K;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        p.X[idx] = cmk(0.0, 0.0);
+        p.Pk[idx] = p.Rp[idx % per];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5 + a6: every shift of column c in one pass (Eq. shift:pi, Eq. collinear),
+// projected updates, convergence, and seed switching on the device.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS) k_shift_step(DevSystem s, PanelDev p) {
+    extern __shared__ double2 dyn[];
+    __shared__ double red[2 * THREADS];
+    __shared__ int s_cnt[THREADS];
+    __shared__ double s_best[THREADS];
+    __shared__ int s_bestk[THREADS];
+    __shared__ int s_sw;
+    __shared__ double2 s_c1, s_c0;
+    const int c = blockIdx.x, K = p.K, tid = threadIdx.x;
+    const ColState cs = p.col[c];
+    if (!cs.active) {
+        if (p.proj == PROJ_NONE)
+            for (int k = tid; k < K; k += THREADS) p.ipi[(size_t)c * K + k] = cmk(0.0, 0.0);
+        return;
+    }
+    const int nfun = cs.nfun;
+    double2* d = dyn;                       // [M]
+    double2* sak = d + p.M;                 // [K]
+    double2* sbk = sak + K;                 // [K]
+    double2* sip = sbk + K;                 // [K]
+    if (p.proj != PROJ_NONE) eval_functionals(s, p, c, nfun, d, red);
+
+    const double2 one = cmk(1.0, 0.0);
+    const double2 alpha = cs.alpha;
+    const double2 beta = cdiv(cs.rho_new, cs.rho);
+    const double2 c2 = cdiv(cmul(cs.beta_prev, alpha), cs.alpha_prev);
+    const double rnorm = cs.rnorm;
+    const int it = cs.iters;
+    int nunc = 0;
+    double best = -1.0;
+    int bestk = K;
+    for (int k = tid; k < K; k += THREADS) {
+        const size_t o = (size_t)c * K + k;
+        if (p.conv_iter[o] >= 0) {
+            sip[k] = cmk(0.0, 0.0);
+            if (p.proj == PROJ_NONE) p.ipi[o] = cmk(0.0, 0.0);
+            continue;
+        }
+        const double2 pk = p.pi[o], pp = p.pi_prev[o];
+        const double2 dl = csub(p.z[k], cs.zs);
+        const double2 pin = cadd(cmul(cadd(one, cmul(alpha, dl)), pk), cmul(c2, csub(pk, pp)));
+        const double2 ratio = cdiv(pk, pin);
+        const double2 ak = cmul(alpha, ratio);
+        const double2 bk = cmul(beta, cmul(ratio, ratio));
+        const double2 ip = cdiv(one, pin);
+        const double res = rnorm / cabs2(pin);
+        p.pi_prev[o] = pk;
+        p.pi[o] = pin;
+        sak[k] = ak;
+        sbk[k] = bk;
+        sip[k] = ip;
+        if (p.proj == PROJ_NONE) {
+            p.ak[o] = ak;
+            p.bk[o] = bk;
+            p.ipi[o] = ip;
+        }
+        if (res <= p.tol) {
+            p.conv_iter[o] = it + 1;
+        } else {
+            ++nunc;
+            if (res > best) { best = res; bestk = k; }
+        }
+    }
+    __syncthreads();
+    if (p.proj != PROJ_NONE) {
+        for (int e = tid; e < K * nfun; e += THREADS) {
+            const int k = e / nfun, m = e % nfun;
+            const double2 ip = sip[k];
+            if (ip.x == 0.0 && ip.y == 0.0) continue;
+            const size_t o = ((size_t)c * K + k) * p.M + m;
+            const double2 u = p.u[o];
+            p.t[o] = cadd(p.t[o], cmul(sak[k], u));
+            p.u[o] = cadd(cmul(d[m], ip), cmul(sbk[k], u));
+        }
+    }
+    // block reductions: number of unconverged shifts, worst residual (ties -> lowest k)
+    s_cnt[tid] = nunc;
+    s_best[tid] = best;
+    s_bestk[tid] = bestk;
+    __syncthreads();
+    for (int st = THREADS / 2; st >= 1; st >>= 1) {
+        if (tid < st) {
+            s_cnt[tid] += s_cnt[tid + st];
+            const double ob = s_best[tid + st];
+            const int ok = s_bestk[tid + st];
+            if (ob > s_best[tid] || (ob == s_best[tid] && ok < s_bestk[tid])) {
+                s_best[tid] = ob;
+                s_bestk[tid] = ok;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        ColState out = cs;
+        out.iters = it + 1;
+        out.n_unconv = s_cnt[0];
+        if (out.n_unconv == 0) out.active = 0;
+        int sw = 0;
+        const int s2 = s_bestk[0];
+        if (out.active && p.switching) {
+            const bool seed_conv = p.conv_iter[(size_t)c * K + cs.seed] >= 0;
+            const bool forced = p.force_switch_every > 0 && ((it + 1) % p.force_switch_every == 0);
+            if ((seed_conv || forced) && s2 < K && s2 != cs.seed) sw = 1;
+        }
+        if (sw) {
+            const double2 c1 = p.pi[(size_t)c * K + s2], c0 = p.pi_prev[(size_t)c * K + s2];
+            out.rho = cdiv(cs.rho_new, cmul(c1, c1));
+            out.alpha_prev = sak[s2];
+            out.beta_prev = sbk[s2];
+            out.sc_cur = cdiv(one, c1);
+            out.sc_prev = cdiv(one, c0);
+            out.zs = p.z[s2];
+            out.seed = s2;
+            out.switches += 1;
+            s_c1 = c1;
+            s_c0 = c0;
+        } else {
+            out.rho = cs.rho_new;
+            out.alpha_prev = alpha;
+            out.beta_prev = beta;
+            out.sc_cur = one;
+            out.sc_prev = one;
+        }
+        s_sw = sw;
+        p.col[c] = out;
+        if (out.active) atomicAdd(&p.flags[2], 1);
+    }
+    __syncthreads();
+    if (s_sw) {
+        const double2 c1 = s_c1, c0 = s_c0;
+        for (int k = tid; k < K; k += THREADS) {
+            const size_t o = (size_t)c * K + k;
+            p.pi[o] = cdiv(p.pi[o], c1);
+            p.pi_prev[o] = cdiv(p.pi_prev[o], c0);
+        }
+    }
+}
+
+// Full mode: x^k += alpha^k p^k, p^k = r'_{n+1}/pi^k_{n+1} + beta^k p^k.
+__global__ void k_full_update(PanelDev p) {
+    const int P = p.P;
+    const long long per = (long long)p.npad * P;
+    const long long items = per * p.K;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const int c = (int)(idx % P);
+        const int k = (int)(idx / per);
+        const size_t o = (size_t)c * p.K + k;
+        const double2 ip = p.ipi[o];
+        if (ip.x == 0.0 && ip.y == 0.0) continue;
+        const double2 pk = p.Pk[idx];
+        p.X[idx] = cadd(p.X[idx], cmul(p.ak[o], pk));
+        p.Pk[idx] = cadd(cmul(p.Rp[idx % per], ip), cmul(p.bk[o], pk));
+    }
+}
+
+__global__ void k_full_output(PanelDev p, const int32_t* __restrict__ orb2pad, int n_orb, int R, int ncols,
+                              int c0, double2* __restrict__ out) {
+    const long long items = (long long)p.K * ncols * n_orb;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const int o = (int)(idx % n_orb);
+        const int c = (int)((idx / n_orb) % ncols);
+        const int k = (int)(idx / ((long long)n_orb * ncols));
+        out[((size_t)k * R + c0 + c) * n_orb + o] = p.X[((size_t)k * p.npad + orb2pad[o]) * p.P + c];
+    }
+}
+
+__global__ void k_green_output(PanelDev p, int ncols, const int64_t* __restrict__ off, double2* __restrict__ out) {
+    const int c = blockIdx.x;
+    if (c >= ncols) return;
+    const int nf = p.col[c].nfun;
+    for (int e = threadIdx.x; e < nf * p.K; e += THREADS) {
+        const int m = e / p.K, k = e % p.K;
+        out[(size_t)(off[c] + m) * p.K + k] = p.t[((size_t)c * p.K + k) * p.M + m];
+    }
+}
+
+// a7: q_j = -(g_s/pi) Im sum_k w_k s_j^T x_j(z_k)
+__global__ void k_mulliken_output(PanelDev p, int ncols, const double2* __restrict__ w, double g_s,
+                                  double* __restrict__ out) {
+    __shared__ double red[THREADS];
+    const int c = blockIdx.x;
+    if (c >= ncols) return;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < p.K; k += THREADS) {
+        const double2 tv = p.t[((size_t)c * p.K + k) * p.M];
+        acc += w[k].x * tv.y + w[k].y * tv.x;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = THREADS / 2; st >= 1; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = -(g_s / 3.14159265358979323846) * red[0];
+}
+
+// ---------------------------------------------------------------------------
+// Generalized Lanczos helpers (Section 3.2), one real vector stored in the
+// real part of a P = 1 panel column.
+// ---------------------------------------------------------------------------
+__global__ void k_lz_spmv(DevSystem s, const double* __restrict__ M, const double2* __restrict__ x,
+                          double2* __restrict__ y) {
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < s.n_atoms; I += gridDim.x * blockDim.x) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
+            const int J = s.bcol[b];
+            for (int a = 0; a < 4; ++a)
+                for (int e = 0; e < 4; ++e) acc[a] += M[16 * (size_t)b + 4 * a + e] * x[4 * J + e].x;
+        }
+        for (int a = 0; a < 4; ++a) y[4 * I + a] = cmk(acc[a], 0.0);
+    }
+}
+
+__global__ void __launch_bounds__(THREADS) k_lz_dot(PanelDev p, const double2* __restrict__ x,
+                                                    const double2* __restrict__ y, double* out, int mode) {
+    __shared__ double smem[THREADS];
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS)
+        v[0] += x[i].x * y[i].x;
+    if (grid_reduce_cols<1>(v, 1, p.partials, p.counter, smem)) {
+        if (threadIdx.x == 0) *out = (mode == 0) ? smem[0] : sqrt(fmax(smem[0], 0.0));
+    }
+}
+
+__global__ void k_lz_start(PanelDev p, const double2* __restrict__ v, int row, double2* __restrict__ u,
+                           double* nrm2) {
+    const double n2 = v[row].x;
+    const double inv = 1.0 / sqrt(n2);
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS)
+        u[i] = cmk(v[i].x * inv, 0.0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nrm2 = n2;
+}
+
+__global__ void k_lz_combine(PanelDev p, const double2* __restrict__ y, const double2* __restrict__ u,
+                             const double2* __restrict__ up, double2* __restrict__ w, const double* a,
+                             const double* b) {
+    const double av = *a, bv = *b;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS)
+        w[i] = cmk(y[i].x - av * u[i].x - bv * up[i].x, 0.0);
+}
+
+__global__ void k_lz_scale(PanelDev p, const double2* __restrict__ w, double2* __restrict__ u,
+                           double2* __restrict__ up, const double* bnext) {
+    const double bv = *bnext;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS) {
+        up[i] = u[i];
+        u[i] = cmk(bv > 0.0 ? w[i].x / bv : 0.0, 0.0);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int g_gmax = 0;
+static int gmax() {
+    if (g_gmax == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g_gmax = 4 * (sms > 0 ? sms : 1);
+    }
+    return g_gmax;
+}
+int max_grid() { return gmax(); }
+
+static int grid_for(long long items) {
+    long long g = (items + THREADS - 1) / THREADS;
+    int gm = gmax();
+    return (int)(g < 1 ? 1 : (g > gm ? gm : g));
+}
+
+void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st) {
+    k_ased_build<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s.n_atoms, s.brow, s.bcol, s.S, s.H, eps_pad, K);
+}
+void launch_panel_init(const DevSystem&, const PanelDev& p, cudaStream_t st) {
+    k_panel_init<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+}
+void launch_outer_spmm(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
+    k_outer_spmm<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+}
+void launch_outer_update(const DevSystem&, const PanelDev& p, cudaStream_t st) {
+    k_outer_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+}
+void launch_inner_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st) {
+    k_inner_spmv<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
+}
+void launch_inner_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
+    k_inner_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
+}
+void launch_finish(const DevSystem&, const PanelDev& p, cudaStream_t st) {
+    k_finish<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+}
+static size_t shift_smem(const PanelDev& p) { return sizeof(double2) * ((size_t)(p.M > 0 ? p.M : 1) + 3 * (size_t)p.K); }
+void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
+    const size_t sm = shift_smem(p);
+    cudaFuncSetAttribute(k_shift_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_shift_init<<<p.P, THREADS, sm, st>>>(s, p);
+    if (p.proj == PROJ_NONE) k_full_init<<<grid_for((long long)p.npad * p.P * p.K), THREADS, 0, st>>>(p);
+}
+void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
+    const size_t sm = shift_smem(p);
+    cudaFuncSetAttribute(k_shift_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_shift_step<<<p.P, THREADS, sm, st>>>(s, p);
+}
+void launch_full_update(const DevSystem&, const PanelDev& p, cudaStream_t st) {
+    k_full_update<<<grid_for((long long)p.npad * p.P * p.K), THREADS, 0, st>>>(p);
+}
+void launch_full_output(const PanelDev& p, const int32_t* orb2pad, int n_orb, int R, int ncols, int c0,
+                        double2* out, cudaStream_t st) {
+    k_full_output<<<grid_for((long long)p.K * ncols * n_orb), THREADS, 0, st>>>(p, orb2pad, n_orb, R, ncols, c0, out);
+}
+void launch_green_output(const PanelDev& p, int ncols, const int64_t* off, double2* out, cudaStream_t st) {
+    k_green_output<<<p.P, THREADS, 0, st>>>(p, ncols, off, out);
+}
+void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
+                            cudaStream_t st) {
+    k_mulliken_output<<<p.P, THREADS, 0, st>>>(p, ncols, w, g_s, out);
+}
+void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, cudaStream_t st) {
+    k_lz_spmv<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s, M, x, y);
+}
+void launch_lz_dot(const PanelDev& p, const double2* x, const double2* y, double* out, int mode, cudaStream_t st) {
+    k_lz_dot<<<grid_for(p.npad), THREADS, 0, st>>>(p, x, y, out, mode);
+}
+void launch_lz_combine(const PanelDev& p, const double2* y, double2* u, double2* u_prev, double2* w,
+                       const double* a, const double* b, cudaStream_t st) {
+    k_lz_combine<<<grid_for(p.npad), THREADS, 0, st>>>(p, y, u, u_prev, w, a, b);
+}
+void launch_lz_scale(const PanelDev& p, double2* w, double2* u, double2* u_prev, const double* bnext,
+                     cudaStream_t st) {
+    k_lz_scale<<<grid_for(p.npad), THREADS, 0, st>>>(p, w, u, u_prev, bnext);
+}
+void launch_lz_start(const PanelDev& p, const double2* v, int row, double2* u, double* nrm2, cudaStream_t st) {
+    k_lz_start<<<grid_for(p.npad), THREADS, 0, st>>>(p, v, row, u, nrm2);
+}
+
+}  // namespace tb

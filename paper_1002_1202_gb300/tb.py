@@ -1,0 +1,321 @@
+"""Python binding of the C ABI in ``include/tbcocg.h`` (ctypes, marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it converts numpy/torch arguments to pointers and
+sizes, calls the library, and turns the status into an exception.  Device
+outputs are torch tensors (PyTorch is used for device memory and streams);
+host outputs are numpy arrays.  The library must be built
+(``paper_1002_1202_gb300._build_lib.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build_lib
+
+TB_OK = 0
+TB_ERR_NOT_CONVERGED = 6
+TB_FP64 = 0
+
+_STATUS = {
+    0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_NOT_SYMMETRIC", 3: "TB_ERR_S_NOT_SPD",
+    4: "TB_ERR_OOM", 5: "TB_ERR_CUDA", 6: "TB_ERR_NOT_CONVERGED", 7: "TB_ERR_BREAKDOWN",
+    8: "TB_ERR_TIMEOUT", 9: "TB_ERR_NO_DEVICE",
+}
+
+
+class TBError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)}")
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int32),
+        ("orb_per_atom", C.POINTER(C.c_int32)),
+        ("brow_ptr", C.POINTER(C.c_int64)),
+        ("bcol", C.POINTER(C.c_int32)),
+        ("S_vals", C.POINTER(C.c_double)),
+        ("H_vals", C.POINTER(C.c_double)),
+        ("eps", C.POINTER(C.c_double)),
+        ("K", C.c_double),
+        ("precision", C.c_int32),
+    ]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double),
+        ("inner_tol", C.c_double),
+        ("max_iter", C.c_int32),
+        ("inner_max_iter", C.c_int32),
+        ("panel", C.c_int32),
+        ("seed", C.c_int32),
+        ("switching", C.c_int32),
+        ("force_switch_every", C.c_int32),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("conv_iter", C.POINTER(C.c_int32)),
+        ("outer_iterations", C.c_int64),
+        ("inner_iterations", C.c_int64),
+        ("max_column_iterations", C.c_int64),
+        ("switches", C.c_int32),
+        ("unconverged", C.c_int32),
+        ("seconds", C.c_double),
+    ]
+
+
+# (name, restype, argtypes) of every entry point declared in include/tbcocg.h
+_VP = C.c_void_p
+_DP = C.POINTER(C.c_double)
+_I32P = C.POINTER(C.c_int32)
+_I64P = C.POINTER(C.c_int64)
+SIGNATURES = [
+    ("tb_create", C.c_int, [C.POINTER(_VP), C.POINTER(SystemDesc), _VP]),
+    ("tb_destroy", C.c_int, [_VP]),
+    ("tb_num_orbitals", C.c_int64, [_VP]),
+    ("tb_num_atoms", C.c_int64, [_VP]),
+    ("tb_num_blocks", C.c_int64, [_VP]),
+    ("tb_default_opts", None, [C.POINTER(SolveOpts)]),
+    ("tb_shifted_cocg", C.c_int, [_VP, C.c_int32, _DP, C.c_int32, _I32P, C.POINTER(SolveOpts), _VP,
+                                  C.POINTER(Stats), _VP]),
+    ("tb_green_elements", C.c_int, [_VP, C.c_int32, _DP, C.c_int32, _I32P, _I64P, _I32P,
+                                    C.POINTER(SolveOpts), _VP, C.POINTER(Stats), _VP]),
+    ("tb_mulliken_orbital", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.c_int32, _I32P,
+                                      C.POINTER(SolveOpts), _VP, C.POINTER(Stats), _VP]),
+    ("tb_mulliken_charges", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP,
+                                      C.POINTER(Stats), _VP]),
+    ("tb_generalized_lanczos", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
+    ("tb_status_string", C.c_char_p, [C.c_int]),
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build_lib.LIB
+
+
+def load_library(path: str | None = None) -> C.CDLL:
+    """Load libtbcocg.so (building nothing); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build_lib.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_1002_1202_gb300._build_lib.build()")
+    lib = C.CDLL(p)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return C.c_void_p(0)
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _complex_host(z) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(z, dtype=np.complex128)).view(np.float64)
+
+
+def _out_ptr(out):
+    if isinstance(out, np.ndarray):
+        if not out.flags.c_contiguous:
+            raise ValueError("output array must be contiguous")
+        return C.c_void_p(out.ctypes.data)
+    if not out.is_contiguous():
+        raise ValueError("output tensor must be contiguous")
+    return C.c_void_p(out.data_ptr())
+
+
+def _check(st: int, where: str, allow_unconverged: bool):
+    if st == TB_OK or (st == TB_ERR_NOT_CONVERGED and allow_unconverged):
+        return st
+    raise TBError(st, where)
+
+
+def tb_default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    load_library().tb_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """A device copy of a block-sparse system (tb_create / tb_destroy)."""
+
+    def __init__(self, ptr: C.c_void_p, n_orb: int, n_atoms: int, nb: int):
+        self.ptr = ptr
+        self.n_orb = n_orb
+        self.n_atoms = n_atoms
+        self.nb = nb
+
+    def close(self):
+        if self.ptr:
+            load_library().tb_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tb_create(orb_per_atom, brow_ptr, bcol, S_vals, H_vals=None, eps=None, K=1.75, stream=None) -> Handle:
+    lib = load_library()
+    orb = np.ascontiguousarray(orb_per_atom, dtype=np.int32)
+    bp = np.ascontiguousarray(brow_ptr, dtype=np.int64)
+    bc = np.ascontiguousarray(bcol, dtype=np.int32)
+    sv = np.ascontiguousarray(S_vals, dtype=np.float64)
+    hv = None if H_vals is None else np.ascontiguousarray(H_vals, dtype=np.float64)
+    ev = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+    d = SystemDesc()
+    d.n_atoms = len(orb)
+    d.orb_per_atom = _ptr(orb, C.c_int32)
+    d.brow_ptr = _ptr(bp, C.c_int64)
+    d.bcol = _ptr(bc, C.c_int32)
+    d.S_vals = _ptr(sv, C.c_double)
+    d.H_vals = _ptr(hv, C.c_double) if hv is not None else None
+    d.eps = _ptr(ev, C.c_double) if ev is not None else None
+    d.K = float(K)
+    d.precision = TB_FP64
+    h = C.c_void_p()
+    _check(lib.tb_create(C.byref(h), C.byref(d), _stream(stream)), "tb_create", False)
+    return Handle(h, int(lib.tb_num_orbitals(h)), int(lib.tb_num_atoms(h)), int(lib.tb_num_blocks(h)))
+
+
+def tb_create_system(sysobj, explicit_H=None, stream=None) -> Handle:
+    """tb_create from a ``tbinputs.TBSystem`` (H by Eq. Hap-1 unless given)."""
+    return tb_create(sysobj.orb_per_atom, sysobj.brow_ptr, sysobj.bcol, sysobj.S_vals, explicit_H, sysobj.eps,
+                     sysobj.K, stream)
+
+
+def _stats(R: int, K: int, want_conv: bool):
+    st = Stats()
+    conv = None
+    if want_conv:
+        conv = np.full(R * K, -1, dtype=np.int32)
+        st.conv_iter = _ptr(conv, C.c_int32)
+    return st, conv
+
+
+def _stats_dict(st: Stats, conv, R, K, status):
+    return {"status": _STATUS.get(status, status), "outer_iterations": st.outer_iterations,
+            "inner_iterations": st.inner_iterations, "max_column_iterations": st.max_column_iterations,
+            "switches": st.switches, "unconverged": st.unconverged, "seconds": st.seconds,
+            "conv_iter": None if conv is None else conv.reshape(R, K)}
+
+
+def tb_shifted_cocg(h: Handle, z, cols, opts: SolveOpts | None = None, out=None, stream=None,
+                    allow_unconverged=False):
+    """Full solutions x[k, c, :] = (z_k S - H)^-1 e_{cols[c]}; returns (out, stats)."""
+    import torch
+    zz = _complex_host(z)
+    cc = np.ascontiguousarray(cols, dtype=np.int32)
+    K, R = len(zz) // 2, len(cc)
+    if out is None:
+        out = torch.empty((K, R, h.n_orb), dtype=torch.complex128, device="cuda")
+    opts = opts or tb_default_opts()
+    st, conv = _stats(R, K, True)
+    s = load_library().tb_shifted_cocg(h.ptr, K, _ptr(zz, C.c_double), R, _ptr(cc, C.c_int32), C.byref(opts),
+                                       _out_ptr(out), C.byref(st), _stream(stream))
+    _check(s, "tb_shifted_cocg", allow_unconverged)
+    return out, _stats_dict(st, conv, R, K, s)
+
+
+def tb_green_elements(h: Handle, z, cols, row_ptr, rows, opts: SolveOpts | None = None, out=None, stream=None,
+                      allow_unconverged=False):
+    """G[(row_ptr[c]+r), k] = G_{rows[row_ptr[c]+r], cols[c]}(z_k); returns (out, stats)."""
+    import torch
+    zz = _complex_host(z)
+    cc = np.ascontiguousarray(cols, dtype=np.int32)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    rr = np.ascontiguousarray(rows, dtype=np.int32)
+    K, R = len(zz) // 2, len(cc)
+    if out is None:
+        out = torch.empty((int(rp[-1]), K), dtype=torch.complex128, device="cuda")
+    opts = opts or tb_default_opts()
+    st, conv = _stats(R, K, True)
+    s = load_library().tb_green_elements(h.ptr, K, _ptr(zz, C.c_double), R, _ptr(cc, C.c_int32),
+                                         _ptr(rp, C.c_int64), _ptr(rr, C.c_int32), C.byref(opts), _out_ptr(out),
+                                         C.byref(st), _stream(stream))
+    _check(s, "tb_green_elements", allow_unconverged)
+    return out, _stats_dict(st, conv, R, K, s)
+
+
+def tb_mulliken_orbital(h: Handle, z, w, cols, g_s=2.0, opts: SolveOpts | None = None, out=None, stream=None,
+                        allow_unconverged=False):
+    """Gross Mulliken populations of the orbitals ``cols``; returns (out, stats)."""
+    import torch
+    zz = _complex_host(z)
+    ww = _complex_host(w)
+    cc = np.ascontiguousarray(cols, dtype=np.int32)
+    K, R = len(zz) // 2, len(cc)
+    if out is None:
+        out = torch.empty((R,), dtype=torch.float64, device="cuda")
+    opts = opts or tb_default_opts()
+    st, conv = _stats(R, K, True)
+    s = load_library().tb_mulliken_orbital(h.ptr, K, _ptr(zz, C.c_double), _ptr(ww, C.c_double), float(g_s), R,
+                                           _ptr(cc, C.c_int32), C.byref(opts), _out_ptr(out), C.byref(st),
+                                           _stream(stream))
+    _check(s, "tb_mulliken_orbital", allow_unconverged)
+    return out, _stats_dict(st, conv, R, K, s)
+
+
+def tb_mulliken_charges(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None, out=None, stream=None,
+                        allow_unconverged=False):
+    """Gross Mulliken population of every atom; returns (out, stats)."""
+    import torch
+    zz = _complex_host(z)
+    ww = _complex_host(w)
+    K = len(zz) // 2
+    if out is None:
+        out = torch.empty((h.n_atoms,), dtype=torch.float64, device="cuda")
+    opts = opts or tb_default_opts()
+    st, _ = _stats(h.n_orb, K, False)
+    s = load_library().tb_mulliken_charges(h.ptr, K, _ptr(zz, C.c_double), _ptr(ww, C.c_double), float(g_s),
+                                           C.byref(opts), _out_ptr(out), C.byref(st), _stream(stream))
+    _check(s, "tb_mulliken_charges", allow_unconverged)
+    return out, _stats_dict(st, None, h.n_orb, K, s)
+
+
+def tb_generalized_lanczos(h: Handle, j: int, n_steps: int, inner_tol=1e-13, stream=None):
+    """Lanczos coefficients (a[n_steps], b[n_steps+1], norm) as numpy arrays."""
+    a = np.zeros(n_steps)
+    b = np.zeros(n_steps + 1)
+    nrm = np.zeros(1)
+    s = load_library().tb_generalized_lanczos(h.ptr, int(j), int(n_steps), float(inner_tol),
+                                              C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data),
+                                              C.c_void_p(nrm.ctypes.data), _stream(stream))
+    _check(s, "tb_generalized_lanczos", False)
+    return a, b, float(nrm[0])
+
+
+def tb_status_string(s: int) -> str:
+    return load_library().tb_status_string(int(s)).decode()

@@ -98,6 +98,24 @@ class TBSystem:
                 S[oo[i]:oo[i] + ni, oo[j]:oo[j] + nj] = self.S_vals[bo[b]:bo[b + 1]].reshape(ni, nj)
         return S
 
+    def to_csr(self):
+        """S as a scipy.sparse CSR matrix in orbital order (format conversion)."""
+        import scipy.sparse as sp
+        oo = self.orb_offset()
+        bo = self.block_offsets()
+        rows = np.repeat(np.arange(self.n_atoms), np.diff(self.brow_ptr))
+        ni = self.orb_per_atom[rows]
+        nj = self.orb_per_atom[self.bcol]
+        r_idx, c_idx = [], []
+        for b in range(self.nb):
+            a = np.arange(ni[b])[:, None]
+            c = np.arange(nj[b])[None, :]
+            r_idx.append(np.broadcast_to(oo[rows[b]] + a, (ni[b], nj[b])).ravel())
+            c_idx.append(np.broadcast_to(oo[self.bcol[b]] + c, (ni[b], nj[b])).ravel())
+        r_idx = np.concatenate(r_idx)
+        c_idx = np.concatenate(c_idx)
+        return sp.csr_matrix((self.S_vals.copy(), (r_idx, c_idx)), shape=(self.n_orb, self.n_orb))
+
     def orbital_atom(self) -> np.ndarray:
         return np.repeat(np.arange(self.n_atoms), self.orb_per_atom)
 

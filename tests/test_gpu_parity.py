@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Plain FP64 path: true relative residual <= 1e-8 per shift, Green's function
+elements within the forward-error bound cond(A) * 1e-8 of the dense solve,
+Mulliken populations within 1e-6 e per orbital/atom of the dense definition.
+Fixed-iteration runs are compared with the oracle's method, which runs the
+same recurrences in the same order, to 1e-9 (1e-8 with forced switches).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tbinputs import si_system, water_system, linspace_grid, gauss_legendre_grid, choose_columns
+from oracle import dense, method
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_1202_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """Si 64 atoms, sp3 (N = 256), 32 shifts on [-20, 5] eV + 0.01i, 8 columns."""
+    s = si_system((2, 2, 2), sigma=0.05, seed=1, cutoff=4.0)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(32)
+    cols = choose_columns(256, 8, seed=2)
+    return s, H, S, z, w, cols
+
+
+@pytest.fixture(scope="module")
+def c1_ref(c1):
+    s, H, S, z, w, cols = c1
+    return dense.green_columns(H, S, z, cols)
+
+
+@pytest.fixture(scope="module")
+def h1(P, c1):
+    return P.tb_create_system(c1[0])
+
+
+def _true_rel_res(H, S, z, X, cols):
+    out = np.zeros((len(z), len(cols)))
+    for k, zk in enumerate(z):
+        A = dense.shifted_matrix(H, S, zk)
+        for c, j in enumerate(cols):
+            b = np.zeros(S.shape[0])
+            b[j] = 1.0
+            out[k, c] = np.linalg.norm(b - A @ X[k, c]) / np.linalg.norm(b)
+    return out
+
+
+def test_full_mode_c1(P, c1, c1_ref, h1):
+    s, H, S, z, w, cols = c1
+    x, st = P.tb_shifted_cocg(h1, z, cols)
+    X = x.cpu().numpy()
+    assert st["status"] == "TB_OK" and st["unconverged"] == 0
+    assert np.all(st["conv_iter"] > 0) and st["switches"] >= 1
+    res = _true_rel_res(H, S, z, X, cols)
+    assert res.max() <= 1e-8, res.max()
+    ref = np.transpose(c1_ref, (0, 2, 1))
+    # forward error <= cond(A) * residual; cond(A) ~ ||A|| / eta ~ 1e4 here
+    assert np.abs(X - ref).max() <= 1e4 * 1e-8 * np.abs(ref).max()
+
+
+def test_complex_symmetry(P, c1, h1):
+    s, H, S, z, w, _ = c1
+    cols = [10, 11, 57]
+    x, _ = P.tb_shifted_cocg(h1, z[::4], cols)
+    X = x.cpu().numpy()
+    for a, ca in enumerate(cols):
+        for b, cb in enumerate(cols):
+            assert np.abs(X[:, a, cb] - X[:, b, ca]).max() <= 1e-6 * np.abs(X).max()
+
+
+@pytest.mark.parametrize("force", [0, 6])
+def test_fixed_iterations_match_method_oracle(P, c1, h1, force):
+    s, H, S, z, w, cols = c1
+    n = 30
+    opts = P.tb_default_opts(max_iter=n, force_switch_every=force)
+    x, st = P.tb_shifted_cocg(h1, z, cols[:3], opts=opts, allow_unconverged=True)
+    X = x.cpu().numpy()
+    for c, j in enumerate(cols[:3]):
+        ref = method.generalized_shifted_cocg(H, S, z, int(j), max_iter=n, force_switch_every=force)["x"]
+        scale = np.abs(ref).max()
+        assert np.abs(X[:, c] - ref).max() <= (1e-9 if force == 0 else 1e-7) * scale
+
+
+def test_green_elements(P, c1, c1_ref, h1):
+    s, H, S, z, w, cols = c1
+    rng = np.random.default_rng(11)
+    row_ptr = [0]
+    rows = []
+    for j in cols:
+        r = sorted(set([int(j)] + list(rng.choice(256, 5, replace=False))))
+        rows += r
+        row_ptr.append(len(rows))
+    G, st = P.tb_green_elements(h1, z, cols, row_ptr, rows)
+    G = G.cpu().numpy()
+    assert st["status"] == "TB_OK"
+    for c in range(len(cols)):
+        for m in range(row_ptr[c], row_ptr[c + 1]):
+            ref = c1_ref[:, rows[m], c]
+            assert np.abs(G[m] - ref).max() <= 1e-4 * np.abs(c1_ref[:, :, c]).max()
+    # projected rows equal the rows of the full solution (same recurrences)
+    x, _ = P.tb_shifted_cocg(h1, z, cols)
+    X = x.cpu().numpy()
+    for c in range(len(cols)):
+        for m in range(row_ptr[c], row_ptr[c + 1]):
+            assert np.abs(G[m] - X[:, c, rows[m]]).max() <= 1e-10 * np.abs(X[:, c]).max()
+
+
+@pytest.fixture(scope="module")
+def c1_mulliken(c1):
+    s, H, S, z, w, cols = c1
+    return dense.mulliken_orbital(H, S, z, w, 2.0)
+
+
+def test_mulliken_orbital(P, c1, c1_mulliken, h1):
+    s, H, S, z, w, cols = c1
+    q, st = P.tb_mulliken_orbital(h1, z, w, cols, 2.0)
+    q = q.cpu().numpy()
+    assert np.abs(q - c1_mulliken[cols]).max() <= 1e-6
+
+
+def test_mulliken_charges_and_sum_rule(P, c1, c1_mulliken, h1):
+    s, H, S, z, w, cols = c1
+    q, st = P.tb_mulliken_charges(h1, z, w, 2.0)
+    q = q.cpu().numpy()
+    ref = dense.mulliken_atom(c1_mulliken, s.orbital_atom(), s.n_atoms)
+    assert np.abs(q - ref).max() <= 1e-6
+    import scipy.linalg as sl
+    eig = sl.eigh(H, S, eigvals_only=True)
+    assert abs(q.sum() - dense.electron_count_closed_form(eig, z, w)) <= 1e-6 * s.n_atoms
+
+
+def test_host_output_buffers(P, c1, h1):
+    s, H, S, z, w, cols = c1
+    out = np.zeros((len(cols),))
+    q_host, _ = P.tb_mulliken_orbital(h1, z, w, cols, 2.0, out=out)
+    q_dev, _ = P.tb_mulliken_orbital(h1, z, w, cols, 2.0)
+    assert np.array_equal(q_host, q_dev.cpu().numpy())
+
+
+def test_explicit_H_same_as_ased(P, c1, h1):
+    s, H, S, z, w, cols = c1
+    # block values of the oracle's ASED H in the input layout
+    oo = s.orb_offset()
+    bo = s.block_offsets()
+    hv = np.zeros_like(s.S_vals)
+    for i in range(s.n_atoms):
+        for b in range(s.brow_ptr[i], s.brow_ptr[i + 1]):
+            j = s.bcol[b]
+            hv[bo[b]:bo[b + 1]] = H[oo[i]:oo[i] + 4, oo[j]:oo[j] + 4].ravel()
+    h2 = P.tb_create_system(s, explicit_H=hv)
+    x1, _ = P.tb_shifted_cocg(h1, z[:8], cols[:2])
+    x2, _ = P.tb_shifted_cocg(h2, z[:8], cols[:2])
+    assert np.abs(x1.cpu().numpy() - x2.cpu().numpy()).max() <= 1e-12 * np.abs(x1.cpu().numpy()).max()
+
+
+def test_panel_split_with_ragged_tail(P, c1, c1_ref, h1):
+    s, H, S, z, w, cols = c1
+    cols13 = choose_columns(256, 13, seed=7)
+    zz = z[::6]
+    opts = P.tb_default_opts(panel=8)
+    x, st = P.tb_shifted_cocg(h1, zz, cols13, opts=opts)
+    X = x.cpu().numpy()
+    res = _true_rel_res(H, S, zz, X, cols13)
+    assert res.max() <= 1e-8
+
+
+def test_single_shift_single_column(P, c1, h1):
+    s, H, S, z, w, cols = c1
+    x, st = P.tb_shifted_cocg(h1, [z[5]], [int(cols[0])])
+    X = x.cpu().numpy()
+    assert _true_rel_res(H, S, [z[5]], X, [cols[0]]).max() <= 1e-8
+    assert st["switches"] == 0
+
+
+def test_water_ragged_blocks(P):
+    s = water_system(32, seed=4)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(8, -35.0, 5.0, 0.05)
+    cols = [0, 1, 4, s.n_orb - 1]
+    h = P.tb_create_system(s)
+    x, st = P.tb_shifted_cocg(h, z, cols)
+    X = x.cpu().numpy()
+    assert _true_rel_res(H, S, z, X, cols).max() <= 1e-8
+    q, _ = P.tb_mulliken_orbital(h, z, w, cols, 2.0)
+    ref = dense.mulliken_orbital(H, S, z, w, 2.0)[cols]
+    assert np.abs(q.cpu().numpy() - ref).max() <= 1e-6
+
+
+def test_lanczos(P, c1, h1):
+    s, H, S, z, w, cols = c1
+    j = 9
+    a, b, nrm = P.tb_generalized_lanczos(h1, j, 100)
+    ar, br, nr = method.generalized_lanczos(H, S, j, 100)
+    assert abs(nrm - nr) <= 1e-12 * nr
+    assert np.abs(a[:20] - ar[:20]).max() <= 1e-8 * np.abs(ar).max()
+    assert np.abs(b[:21] - br[:21]).max() <= 1e-8 * np.abs(br).max()
+    zz = np.array([-5.0 + 2.0j, 2.0 + 2.0j])
+    g = method.lanczos_green(a, b, nrm, zz)
+    ref = dense.green_columns(H, S, zz, [j])[:, j, 0]
+    assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_not_converged_status(P, c1, h1):
+    s, H, S, z, w, cols = c1
+    opts = P.tb_default_opts(max_iter=5)
+    with pytest.raises(P.TBError) as e:
+        P.tb_shifted_cocg(h1, z, cols[:2], opts=opts)
+    assert e.value.status == 6
+    x, st = P.tb_shifted_cocg(h1, z, cols[:2], opts=opts, allow_unconverged=True)
+    assert st["unconverged"] == 2 * 32
+
+
+def test_invalid_arguments(P, c1, h1):
+    s, H, S, z, w, cols = c1
+    for bad in ([-1], [256], []):
+        with pytest.raises(P.TBError) as e:
+            P.tb_shifted_cocg(h1, z[:2], bad)
+        assert e.value.status == 1
+    with pytest.raises(P.TBError):
+        P.tb_shifted_cocg(h1, z[:2], [0], opts=P.tb_default_opts(seed=5))
+    with pytest.raises(P.TBError):
+        P.tb_shifted_cocg(h1, z[:2], [0], opts=P.tb_default_opts(panel=48))
+
+
+def test_overlap_not_positive_definite(P, c1):
+    s = c1[0]
+    sv = s.S_vals.copy()
+    bo = s.block_offsets()
+    for i in range(s.n_atoms):
+        for b in range(s.brow_ptr[i], s.brow_ptr[i + 1]):
+            if s.bcol[b] != i:
+                sv[bo[b]:bo[b + 1]] *= 3.0       # eigenvalues 1 + 3(l - 1) < 0
+    h = P.tb_create(s.orb_per_atom, s.brow_ptr, s.bcol, sv, None, s.eps, s.K)
+    with pytest.raises(P.TBError) as e:
+        P.tb_shifted_cocg(h, linspace_grid(4)[0], [0])
+    assert e.value.status == 3
+
+
+def test_max_shift_count(P, c1, h1):
+    s, H, S, z, w, cols = c1
+    zz = np.linspace(-20, 5, 1024) + 0.05j
+    opts = P.tb_default_opts(tol=1e-9)
+    G, st = P.tb_green_elements(h1, zz, [int(cols[0])], [0, 1], [int(cols[0])], opts=opts)
+    ref = dense.green_columns(H, S, zz[::97], [int(cols[0])])[:, cols[0], 0]
+    assert np.abs(G.cpu().numpy()[0, ::97] - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# full-size workload (Si 4096 atoms, N = 16384, 256 Gauss-Legendre shifts),
+# bench launch configuration (panel of 64 columns, Mulliken projection):
+# sampled columns against the oracle's method after the same number of steps
+# ---------------------------------------------------------------------------
+@pytest.mark.slow
+def test_full_size_sampled_columns(P):
+    import torch
+    s = si_system((8, 8, 8), sigma=0.05, seed=3, cutoff=4.0)
+    z, w = gauss_legendre_grid(256, -20.0, 5.0, 0.01)
+    cols = choose_columns(s.n_orb, 64, seed=5)
+    n = 12
+    h = P.tb_create_system(s)
+    opts = P.tb_default_opts(max_iter=n, panel=64)
+    q, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts, allow_unconverged=True)
+    q = q.cpu().numpy()
+    Sc = s.to_csr()
+    Hc = dense.ased_hamiltonian_sparse(Sc, s.eps, s.K, s.orbital_atom())
+    for c in (0, 37):
+        j = int(cols[c])
+        F = Sc[j].toarray()
+        out = method.generalized_shifted_cocg(Hc, Sc, z, j, max_iter=n, keep_full=False, functionals=F)
+        qref = -(2.0 / math.pi) * np.imag(np.sum(w * out["t"][:, 0]))
+        assert abs(q[c] - qref) <= 1e-9 * max(1.0, abs(qref))
