@@ -1,0 +1,351 @@
+"""Throughput benchmark of the generalized shifted COCG hot path on GB300.
+
+Workload: Si diamond supercell of 4096 atoms (8x8x8 conventional cells,
+a = 5.431 A, Gaussian displacements 0.05 A, seed 3), sp3 STO basis
+(N = 16384 orbitals, ~17 4x4 blocks per block row), H by the ASED rule
+(K = 1.75), 256 shifts z_k = E_k + 0.01i eV with E_k the Gauss-Legendre
+nodes on [-20, 5] eV, Mulliken projection (a7).  One step = one panel of
+P right-hand sides e_j run through ``iters`` outer iterations of the whole
+hot path (seed SpMM, inner CG for S^-1, shift updates, seed switching,
+charge accumulation), started from r_0 = e_j.  The full solve of this
+workload needs ~10^4-10^5 outer iterations per column, so a step is a
+fixed chunk of it; the metric is the rate shift*RHS*iterations/s.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank solves its own panel of columns (weak
+scaling); no collective touches the data path, only the timing barrier and
+the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "shift*RHS*iterations/s at 1e-8 residual"
+UNIT = "shift*RHS*iterations/s"
+CELLS = (8, 8, 8)
+SEED = 3
+K_SHIFTS = 256
+FP64_PEAK_TFLOPS = 1.25       # GB300 FP64 (vector and tensor), nominal
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--panel", type=int, default=64)
+    ap.add_argument("--iters", type=int, default=40, help="outer iterations per step")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from tbinputs import si_system, gauss_legendre_grid
+    s = si_system(CELLS, sigma=0.05, seed=SEED, cutoff=4.0)
+    z, w = gauss_legendre_grid(K_SHIFTS, -20.0, 5.0, 0.01)
+    return s, z, w
+
+
+def rank_columns(n_orb, panel, rank, seed=100):
+    """Right-hand sides of one rank: a slice of one seeded permutation of all
+    orbitals, so ranks never share a column (weak scaling by columns)."""
+    perm = np.random.default_rng(seed).permutation(n_orb)
+    lo = (rank * panel) % n_orb
+    return np.sort(perm[lo:lo + panel]).astype(np.int32)
+
+
+def reduce_max(value, world, device=None):
+    """Max over ranks (timing only; no data-path collective)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def config_dict(args, s, precision="fp64"):
+    return {
+        "workload": (f"Si diamond {s.n_atoms} atoms ({CELLS[0]}x{CELLS[1]}x{CELLS[2]} cells), N={s.n_orb} sp3 "
+                     f"orbitals, {K_SHIFTS} Gauss-Legendre shifts on [-20,5] eV + 0.01i eV, Mulliken projection, "
+                     f"panel of {args.panel} RHS, {args.iters} outer iterations per step"),
+        "n_atoms": s.n_atoms, "N": s.n_orb, "blocks": int(s.nb), "shifts": K_SHIFTS, "panel": args.panel,
+        "iterations_per_step": args.iters, "tol": args.tol, "inner_tol": 1e-13, "precision": precision,
+        "l2": "flushed (256 MiB write) before every timed step", "seed": SEED,
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(s, z, w, n_iter, col):
+    """The oracle's method on one column for n_iter outer iterations (all
+    shifts, Mulliken functional); returns seconds."""
+    from oracle import dense, method
+    Sc = s.to_csr()
+    Hc = dense.ased_hamiltonian_sparse(Sc, s.eps, s.K, s.orbital_atom())
+    F = Sc[col].toarray()
+    c0 = time.process_time()
+    t0 = time.perf_counter()
+    method.generalized_shifted_cocg(Hc, Sc, z, col, tol=1e-8, max_iter=n_iter, keep_full=False, functionals=F)
+    t = time.perf_counter() - t0
+    cores = max(1, math.ceil((time.process_time() - c0) / t - 0.05))
+    return t, cores
+
+
+def cpu_baseline(s, z, w, target_s):
+    col = 1234
+    t1, _ = oracle_sample(s, z, w, 2, col)
+    per = t1 / 2.0
+    n = int(max(2, min(400, target_s / max(per, 1e-6))))
+    t, cores = oracle_sample(s, z, w, n, col)
+    return {"value": K_SHIFTS * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle.method.generalized_shifted_cocg (numpy + scipy.sparse CSR, inner CG to 1e-13), "
+                       f"1 column x {n} outer iterations x {K_SHIFTS} shifts of the same workload, {t:.1f} s")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    s, z, w = workload()
+    n_iter = args.iters
+    times = []
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        t, c = oracle_sample(s, z, w, n_iter, 1234 + i)
+        if i >= args.warmup:
+            times.append(t)
+            cores = max(cores, c)
+    tot = sum(times)
+    value = K_SHIFTS * n_iter * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(config_dict(args, s), panel=1, iterations_per_step=n_iter,
+                       workload=config_dict(args, s)["workload"] + "; reference arm: CPU oracle, 1 column per step"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"1 column x {n_iter} outer iterations x {K_SHIFTS} shifts per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def stored_traffic(kernel_file, kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, valid only while
+    the kernel source it was taken from is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel_name)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = open(os.path.join(ROOT, "paper_1002_1202_gb300", "csrc", kernel_file), "rb").read()
+    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1002_1202_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P.build()
+    s, z, w = workload()
+    cols = rank_columns(s.n_orb, args.panel, rank)
+    h = P.tb_create_system(s)
+    opts = P.tb_default_opts(max_iter=args.iters, panel=args.panel, tol=args.tol)
+    q_dev = torch.empty(args.panel, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(out):
+        return P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts, out=out, allow_unconverged=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(q_dev)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    P.tb_profile_enable(True)
+    launches0 = P.tb_launch_count()
+    times = []
+    stats = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, st = step(q_dev)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+        stats.append(st)
+    barrier()
+    launches = P.tb_launch_count() - launches0
+    n_spmv, ms_spmv = P.tb_profile_read("inner_spmv")
+    kernel_ms = {k: P.tb_profile_read(k) for k in P.tb.KERNELS}
+    P.tb_profile_enable(False)
+    clk = clocks.stop()
+    total = reduce_max(sum(times), world, "cuda")
+    units_per_step = K_SHIFTS * args.panel * args.iters
+    value = world * units_per_step * args.steps / total
+    # active-shift variant: (column, shift) pairs not yet converged at each step
+    act = 0
+    for st in stats:
+        ci = st["conv_iter"]
+        act += int(np.sum(np.where(ci < 0, args.iters, np.minimum(ci, args.iters))))
+    active_value = world * act / total
+
+    # e2e: the same call with pinned host buffers (inputs copied in, charges read back)
+    z_h = torch.from_numpy(np.ascontiguousarray(z)).pin_memory().numpy()
+    w_h = torch.from_numpy(np.ascontiguousarray(w)).pin_memory().numpy()
+    c_h = torch.from_numpy(np.ascontiguousarray(cols)).pin_memory().numpy()
+    q_h = torch.empty(args.panel, dtype=torch.float64).pin_memory().numpy()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        P.tb_mulliken_orbital(h, z_h, w_h, c_h, 2.0, opts=opts, out=q_h, allow_unconverged=True)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_tot = reduce_max(sum(e2e_times), world, "cuda")
+    e2e = {"value": world * units_per_step * args.steps / e2e_tot, "unit": UNIT,
+           "h2d_bytes_per_step": int(z_h.nbytes + w_h.nbytes + c_h.nbytes), "d2h_bytes_per_step": int(q_h.nbytes)}
+
+    # roofline of the dominant kernel (inner-CG SpMV w = S r on 2P real columns):
+    # 2 flops per stored matrix entry per real column
+    nnz = 16 * s.nb
+    flops_per_launch = 2.0 * nnz * 2 * args.panel
+    avg_s = ms_spmv / max(n_spmv, 1) / 1e3
+    achieved = flops_per_launch / avg_s / 1e12 if avg_s > 0 else None
+    traffic = stored_traffic("tb_kernels.cu", "k_inner_spmv")
+    roofline = {"kernel": "k_inner_spmv", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": traffic, "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on file)",
+                "launches": n_spmv, "avg_launch_us": avg_s * 1e6,
+                "algorithmic_bytes_per_launch": int(128 * s.nb + 4 * s.nb + 2 * 16 * s.n_orb * args.panel),
+                "flops_per_launch": flops_per_launch}
+    share = {k: round(v[1], 3) for k, v in kernel_ms.items()}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, s), "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roofline, "active_shift_value": active_value, "kernel_ms": share,
+        "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
+                                       / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(s, z, w, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

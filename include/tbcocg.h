@@ -183,6 +183,33 @@ tb_status tb_mulliken_charges(tb_handle *h, int32_t K, const double *z, const do
 tb_status tb_generalized_lanczos(tb_handle *h, int32_t j, int32_t n_steps, double inner_tol,
                                  double *a, double *b, double *norm, void *stream);
 
+/*
+ * Launch accounting for measurement tools (no counterpart in the paper).
+ * tb_launch_count: number of kernels this library has launched since it was
+ * loaded (all threads, all devices).
+ * tb_profile_enable(1) resets the per-kernel totals and from then on
+ * brackets every launch with a pair of CUDA events on the launch's stream;
+ * tb_profile_enable(0) stops it.  tb_profile_read waits for the recorded
+ * events and returns, for one kernel class TB_K_*, the launches counted since
+ * the last reset and their summed device time in milliseconds (0 ms while
+ * profiling is off).  Not thread-safe; intended for a single benchmarking
+ * thread.
+ */
+enum {
+    TB_K_INNER_SPMV = 0,   /* w = S r and the inner-CG dot products        */
+    TB_K_INNER_UPDATE = 1, /* inner-CG vector updates                      */
+    TB_K_OUTER_SPMM = 2,   /* q = (z_s S - H) r', A p and mu               */
+    TB_K_OUTER_UPDATE = 3, /* r_{n+1} = r_n - alpha A p                    */
+    TB_K_FINISH = 4,       /* rho_{n+1}                                    */
+    TB_K_SHIFT_STEP = 5,   /* all shifts, projections, seed switching      */
+    TB_K_FULL_UPDATE = 6,  /* full-mode x^k, p^k updates                   */
+    TB_K_OTHER = 7,        /* set-up, outputs, Lanczos helpers             */
+    TB_K_COUNT = 8
+};
+int64_t tb_launch_count(void);
+void tb_profile_enable(int32_t enable);
+tb_status tb_profile_read(int32_t kernel, int64_t *launches, double *total_ms);
+
 /* Static string naming a status code. */
 const char *tb_status_string(tb_status s);
 

@@ -117,6 +117,7 @@ tb_status inner_cg(tb_handle* h, const PanelDev& p, int inner_max, int& pred, in
         TB_CK(cudaGetLastError());
         TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
         TB_CK(cudaStreamSynchronize(st));
+        prof_harvest();
         if (h->flags_host[1] == 0) {
             inner_total += h->flags_host[3];
             pred = h->flags_host[3] + 1;
@@ -370,6 +371,16 @@ void tb_default_opts(tb_solve_opts* o) {
     o->seed = 0;
     o->switching = 1;
     o->force_switch_every = 0;
+}
+
+int64_t tb_launch_count(void) { return launch_count(); }
+
+void tb_profile_enable(int32_t enable) { profile_enable(enable != 0); }
+
+tb_status tb_profile_read(int32_t kernel, int64_t* launches, double* total_ms) {
+    if (kernel < 0 || kernel >= K_COUNT || !launches || !total_ms) return TB_ERR_INVALID_ARG;
+    profile_read(kernel, launches, total_ms);
+    return TB_OK;
 }
 
 int64_t tb_num_orbitals(const tb_handle* h) { return h ? h->n_orb : 0; }

@@ -87,6 +87,15 @@ struct PanelDev {
     int* flags = nullptr;          // [4]: errors, inner active, active columns, inner iters
 };
 
+// kernel classes for launch accounting (same order as the TB_K_* constants
+// of the public header)
+enum { K_INNER_SPMV = 0, K_INNER_UPDATE, K_OUTER_SPMM, K_OUTER_UPDATE, K_FINISH, K_SHIFT_STEP,
+       K_FULL_UPDATE, K_OTHER, K_COUNT };
+void profile_enable(bool on);
+void prof_harvest();
+void profile_read(int id, int64_t* launches, double* ms);
+int64_t launch_count();
+
 // ---- launchers (tb_kernels.cu) -------------------------------------------
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st);
 void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);

@@ -16,6 +16,8 @@
 
 #include <math.h>
 
+#include <vector>
+
 namespace tb {
 
 namespace {
@@ -694,6 +696,76 @@ __global__ void k_lz_scale(PanelDev p, const double2* __restrict__ w, double2* _
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// launch accounting: a count of every kernel launch, and (when enabled) a
+// pair of CUDA events around each launch on its own stream
+// ---------------------------------------------------------------------------
+namespace {
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;      // start/stop pairs
+    std::vector<int> kid;             // kernel id of each pair in use
+    size_t used = 0;
+    int64_t launches[K_COUNT] = {};
+    double ms[K_COUNT] = {};
+    int64_t total = 0;
+};
+Profiler g_prof;
+
+struct LaunchScope {
+    cudaStream_t st;
+    size_t pair = (size_t)-1;
+    LaunchScope(int id, cudaStream_t s) : st(s) {
+        ++g_prof.total;
+        ++g_prof.launches[id];
+        if (!g_prof.on) return;
+        if (2 * g_prof.used + 2 > g_prof.ev.size()) {
+            for (int i = 0; i < 2; ++i) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                g_prof.ev.push_back(e);
+            }
+        }
+        pair = g_prof.used++;
+        if (g_prof.kid.size() < g_prof.used) g_prof.kid.resize(g_prof.used);
+        g_prof.kid[pair] = id;
+        cudaEventRecord(g_prof.ev[2 * pair], st);
+    }
+    ~LaunchScope() {
+        if (pair != (size_t)-1) cudaEventRecord(g_prof.ev[2 * pair + 1], st);
+    }
+};
+}  // namespace
+
+void profile_enable(bool on) {
+    prof_harvest();
+    g_prof.on = on;
+    for (int i = 0; i < K_COUNT; ++i) {
+        g_prof.launches[i] = 0;
+        g_prof.ms[i] = 0.0;
+    }
+}
+
+void prof_harvest() {
+    for (size_t i = 0; i < g_prof.used; ++i) {
+        float t = 0.f;
+        cudaEventSynchronize(g_prof.ev[2 * i + 1]);
+        if (cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) == cudaSuccess)
+            g_prof.ms[g_prof.kid[i]] += t;
+        else
+            cudaGetLastError();
+    }
+    g_prof.used = 0;
+}
+
+void profile_read(int id, int64_t* launches, double* ms) {
+    prof_harvest();
+    *launches = g_prof.launches[id];
+    *ms = g_prof.ms[id];
+}
+
+int64_t launch_count() { return g_prof.total; }
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static int g_gmax = 0;
@@ -715,68 +787,125 @@ static int grid_for(long long items) {
 }
 
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st) {
-    k_ased_build<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s.n_atoms, s.brow, s.bcol, s.S, s.H, eps_pad, K);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_ased_build<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s.n_atoms, s.brow, s.bcol, s.S, s.H, eps_pad, K);
+    }
 }
 void launch_panel_init(const DevSystem&, const PanelDev& p, cudaStream_t st) {
-    k_panel_init<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_panel_init<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+    }
 }
 void launch_outer_spmm(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
-    k_outer_spmm<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+    {
+        LaunchScope ls_(K_OUTER_SPMM, st);
+        k_outer_spmm<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+    }
 }
 void launch_outer_update(const DevSystem&, const PanelDev& p, cudaStream_t st) {
-    k_outer_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+    {
+        LaunchScope ls_(K_OUTER_UPDATE, st);
+        k_outer_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+    }
 }
 void launch_inner_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st) {
-    k_inner_spmv<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
+    {
+        LaunchScope ls_(K_INNER_SPMV, st);
+        k_inner_spmv<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
+    }
 }
 void launch_inner_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
-    k_inner_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
+    {
+        LaunchScope ls_(K_INNER_UPDATE, st);
+        k_inner_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
+    }
 }
 void launch_finish(const DevSystem&, const PanelDev& p, cudaStream_t st) {
-    k_finish<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+    {
+        LaunchScope ls_(K_FINISH, st);
+        k_finish<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+    }
 }
 static size_t shift_smem(const PanelDev& p) { return sizeof(double2) * ((size_t)(p.M > 0 ? p.M : 1) + 3 * (size_t)p.K); }
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     const size_t sm = shift_smem(p);
     cudaFuncSetAttribute(k_shift_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_shift_init<<<p.P, THREADS, sm, st>>>(s, p);
-    if (p.proj == PROJ_NONE) k_full_init<<<grid_for((long long)p.npad * p.P * p.K), THREADS, 0, st>>>(p);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_shift_init<<<p.P, THREADS, sm, st>>>(s, p);
+    }
+    if (p.proj == PROJ_NONE) {
+        LaunchScope ls_(K_OTHER, st);
+        k_full_init<<<grid_for((long long)p.npad * p.P * p.K), THREADS, 0, st>>>(p);
+    }
 }
 void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     const size_t sm = shift_smem(p);
     cudaFuncSetAttribute(k_shift_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_shift_step<<<p.P, THREADS, sm, st>>>(s, p);
+    {
+        LaunchScope ls_(K_SHIFT_STEP, st);
+        k_shift_step<<<p.P, THREADS, sm, st>>>(s, p);
+    }
 }
 void launch_full_update(const DevSystem&, const PanelDev& p, cudaStream_t st) {
-    k_full_update<<<grid_for((long long)p.npad * p.P * p.K), THREADS, 0, st>>>(p);
+    {
+        LaunchScope ls_(K_FULL_UPDATE, st);
+        k_full_update<<<grid_for((long long)p.npad * p.P * p.K), THREADS, 0, st>>>(p);
+    }
 }
 void launch_full_output(const PanelDev& p, const int32_t* orb2pad, int n_orb, int R, int ncols, int c0,
                         double2* out, cudaStream_t st) {
-    k_full_output<<<grid_for((long long)p.K * ncols * n_orb), THREADS, 0, st>>>(p, orb2pad, n_orb, R, ncols, c0, out);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_full_output<<<grid_for((long long)p.K * ncols * n_orb), THREADS, 0, st>>>(p, orb2pad, n_orb, R, ncols, c0, out);
+    }
 }
 void launch_green_output(const PanelDev& p, int ncols, const int64_t* off, double2* out, cudaStream_t st) {
-    k_green_output<<<p.P, THREADS, 0, st>>>(p, ncols, off, out);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_green_output<<<p.P, THREADS, 0, st>>>(p, ncols, off, out);
+    }
 }
 void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
                             cudaStream_t st) {
-    k_mulliken_output<<<p.P, THREADS, 0, st>>>(p, ncols, w, g_s, out);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_mulliken_output<<<p.P, THREADS, 0, st>>>(p, ncols, w, g_s, out);
+    }
 }
 void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, cudaStream_t st) {
-    k_lz_spmv<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s, M, x, y);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_lz_spmv<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s, M, x, y);
+    }
 }
 void launch_lz_dot(const PanelDev& p, const double2* x, const double2* y, double* out, int mode, cudaStream_t st) {
-    k_lz_dot<<<grid_for(p.npad), THREADS, 0, st>>>(p, x, y, out, mode);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_lz_dot<<<grid_for(p.npad), THREADS, 0, st>>>(p, x, y, out, mode);
+    }
 }
 void launch_lz_combine(const PanelDev& p, const double2* y, double2* u, double2* u_prev, double2* w,
                        const double* a, const double* b, cudaStream_t st) {
-    k_lz_combine<<<grid_for(p.npad), THREADS, 0, st>>>(p, y, u, u_prev, w, a, b);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_lz_combine<<<grid_for(p.npad), THREADS, 0, st>>>(p, y, u, u_prev, w, a, b);
+    }
 }
 void launch_lz_scale(const PanelDev& p, double2* w, double2* u, double2* u_prev, const double* bnext,
                      cudaStream_t st) {
-    k_lz_scale<<<grid_for(p.npad), THREADS, 0, st>>>(p, w, u, u_prev, bnext);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_lz_scale<<<grid_for(p.npad), THREADS, 0, st>>>(p, w, u, u_prev, bnext);
+    }
 }
 void launch_lz_start(const PanelDev& p, const double2* v, int row, double2* u, double* nrm2, cudaStream_t st) {
-    k_lz_start<<<grid_for(p.npad), THREADS, 0, st>>>(p, v, row, u, nrm2);
+    {
+        LaunchScope ls_(K_OTHER, st);
+        k_lz_start<<<grid_for(p.npad), THREADS, 0, st>>>(p, v, row, u, nrm2);
+    }
 }
 
 }  // namespace tb

@@ -94,7 +94,13 @@ SIGNATURES = [
                                       C.POINTER(Stats), _VP]),
     ("tb_generalized_lanczos", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
+    ("tb_launch_count", C.c_int64, []),
+    ("tb_profile_enable", None, [C.c_int32]),
+    ("tb_profile_read", C.c_int, [C.c_int32, _I64P, _DP]),
 ]
+
+KERNELS = {"inner_spmv": 0, "inner_update": 1, "outer_spmm": 2, "outer_update": 3, "finish": 4,
+           "shift_step": 5, "full_update": 6, "other": 7}
 
 _lib = None
 
@@ -319,3 +325,20 @@ def tb_generalized_lanczos(h: Handle, j: int, n_steps: int, inner_tol=1e-13, str
 
 def tb_status_string(s: int) -> str:
     return load_library().tb_status_string(int(s)).decode()
+
+
+def tb_launch_count() -> int:
+    return int(load_library().tb_launch_count())
+
+
+def tb_profile_enable(enable: bool = True) -> None:
+    load_library().tb_profile_enable(1 if enable else 0)
+
+
+def tb_profile_read(kernel) -> tuple:
+    """(launches, total_ms) of a kernel class (name or TB_K_* id)."""
+    kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(load_library().tb_profile_read(kid, C.byref(n), C.byref(ms)), "tb_profile_read", False)
+    return int(n.value), float(ms.value)
