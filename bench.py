@@ -40,6 +40,7 @@ CELLS = (8, 8, 8)
 SEED = 3
 K_SHIFTS = 256
 FP64_PEAK_TFLOPS = 1.25       # GB300 FP64 (vector and tensor), nominal
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x clock
 
 
 def parse():
@@ -48,11 +49,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--panel", type=int, default=64)
+    ap.add_argument("--panel", type=int, default=0, help="RHS per panel; 0 = autotune over 64/128/256")
     ap.add_argument("--iters", type=int, default=40, help="outer iterations per step")
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--inner-tol", type=float, default=1e-12, help="relative accuracy of r' = S^-1 r (both precisions)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="mixed: FP32 inner CG inside FP64 refinement (FP64-accurate); fp64: every product in FP64")
+    ap.add_argument("--compare-steps", type=int, default=2,
+                    help="timed steps of the other precision, reported beside the headline (0: skip)")
     return ap.parse_args()
 
 
@@ -82,13 +88,16 @@ def reduce_max(value, world, device=None):
     return float(t.item())
 
 
-def config_dict(args, s, precision="fp64"):
+def config_dict(args, s, precision=None):
+    precision = precision or getattr(args, "precision", "fp64")
     return {
         "workload": (f"Si diamond {s.n_atoms} atoms ({CELLS[0]}x{CELLS[1]}x{CELLS[2]} cells), N={s.n_orb} sp3 "
                      f"orbitals, {K_SHIFTS} Gauss-Legendre shifts on [-20,5] eV + 0.01i eV, Mulliken projection, "
                      f"panel of {args.panel} RHS, {args.iters} outer iterations per step"),
         "n_atoms": s.n_atoms, "N": s.n_orb, "blocks": int(s.nb), "shifts": K_SHIFTS, "panel": args.panel,
-        "iterations_per_step": args.iters, "tol": args.tol, "inner_tol": 1e-13, "precision": precision,
+        "iterations_per_step": args.iters, "tol": args.tol, "inner_tol": args.inner_tol,
+        "precision": ("FP32 inner CG (to 1e-6 per round) inside FP64 iterative refinement; FP64 outer SpMM, "
+                      "vectors, recurrences, switching and charges" if precision == "mixed" else "FP64 throughout"),
         "l2": "flushed (256 MiB write) before every timed step", "seed": SEED,
     }
 
@@ -105,7 +114,8 @@ def oracle_sample(s, z, w, n_iter, col):
     F = Sc[col].toarray()
     c0 = time.process_time()
     t0 = time.perf_counter()
-    method.generalized_shifted_cocg(Hc, Sc, z, col, tol=1e-8, max_iter=n_iter, keep_full=False, functionals=F)
+    method.generalized_shifted_cocg(Hc, Sc, z, col, tol=1e-8, inner_tol=1e-12, max_iter=n_iter, keep_full=False,
+                                    functionals=F)
     t = time.perf_counter() - t0
     cores = max(1, math.ceil((time.process_time() - c0) / t - 0.05))
     return t, cores
@@ -118,7 +128,7 @@ def cpu_baseline(s, z, w, target_s):
     n = int(max(2, min(400, target_s / max(per, 1e-6))))
     t, cores = oracle_sample(s, z, w, n, col)
     return {"value": K_SHIFTS * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle.method.generalized_shifted_cocg (numpy + scipy.sparse CSR, inner CG to 1e-13), "
+            "sample": (f"oracle.method.generalized_shifted_cocg (numpy + scipy.sparse CSR, inner CG to 1e-12), "
                        f"1 column x {n} outer iterations x {K_SHIFTS} shifts of the same workload, {t:.1f} s")}
 
 
@@ -217,6 +227,57 @@ def stored_traffic(kernel_file, kernel_name):
     return rec.get("dram_bytes_per_launch")
 
 
+KERNEL_INFO = {
+    # name: (source file, kernel name, dtype bytes of matrix / vector elements, FP64?)
+    "inner_spmv": ("k_inner_spmv", 8, 16, True),
+    "outer_spmm": ("k_outer_spmm", 8, 16, True),
+    "refine_residual": ("k_refine_residual", 8, 16, True),
+    "inner32_spmv": ("k_inner32_spmv", 4, 8, False),
+}
+
+
+def roofline_for(kname, ms, launches, s, panel, peaks):
+    """Roofline of one SpMM-type kernel: algorithmic flops and bytes per
+    launch over its CUDA-event time."""
+    kern, mb, vb, fp64 = KERNEL_INFO[kname]
+    nnz = 16 * s.nb
+    mats = 2 if kname == "outer_spmm" else 1
+    flops = 2.0 * nnz * 2 * panel * mats
+    vec_io = {"inner_spmv": 2, "inner32_spmv": 2, "refine_residual": 3, "outer_spmm": 5}[kname]
+    nbytes = mats * nnz * mb + 4 * s.nb + 4 * (s.n_atoms + 1) + vec_io * s.n_orb * panel * vb
+    avg_s = ms / max(launches, 1) / 1e3
+    if avg_s <= 0:
+        return None
+    tf = flops / avg_s / 1e12
+    gbs = nbytes / avg_s / 1e9
+    if fp64:
+        rec = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": tf / FP64_PEAK_TFLOPS,
+               "peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s (no measured FP64 peak on file)"}
+    else:
+        f_alu = tf / FP32_PEAK_TFLOPS
+        f_mem = gbs / peaks["hbm_gbs"]
+        if f_mem >= f_alu:
+            rec = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": f_mem,
+                   "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"}
+        else:
+            rec = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
+                   "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+    rec.update({"kernel": kern, "launches": launches, "avg_launch_us": avg_s * 1e6,
+                "flops_per_launch": flops, "algorithmic_bytes_per_launch": int(nbytes),
+                "traffic": stored_traffic("tb_kernels.cu", kern)})
+    return rec
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -233,9 +294,30 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.build()
     s, z, w = workload()
-    cols = rank_columns(s.n_orb, args.panel, rank)
     h = P.tb_create_system(s)
-    opts = P.tb_default_opts(max_iter=args.iters, panel=args.panel, tol=args.tol)
+    prec = 1 if args.precision == "mixed" else 0
+    tune = None
+    if args.panel == 0:
+        # panel-width autotune: 3 outer iterations per candidate, best rate wins
+        tune = {}
+        for cand in (64, 128, 256):
+            o_t = P.tb_default_opts(max_iter=3, panel=cand, tol=args.tol, precision=prec, inner_tol=args.inner_tol)
+            c_t = rank_columns(s.n_orb, cand, rank)
+            P.tb_mulliken_orbital(h, z, w, c_t, 2.0, opts=o_t, allow_unconverged=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.tb_mulliken_orbital(h, z, w, c_t, 2.0, opts=o_t, allow_unconverged=True)
+            torch.cuda.synchronize()
+            tune[cand] = K_SHIFTS * cand * 3 / (time.perf_counter() - t0)
+        best = max(tune, key=tune.get)
+        if world > 1:
+            t = torch.tensor([best], device="cuda", dtype=torch.int64)
+            dist.broadcast(t, 0)
+            best = int(t.item())
+        args.panel = best
+    cols = rank_columns(s.n_orb, args.panel, rank)
+    opts = P.tb_default_opts(max_iter=args.iters, panel=args.panel, tol=args.tol, precision=prec,
+                             inner_tol=args.inner_tol)
     q_dev = torch.empty(args.panel, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -270,7 +352,6 @@ def run_ours(args):
         stats.append(st)
     barrier()
     launches = P.tb_launch_count() - launches0
-    n_spmv, ms_spmv = P.tb_profile_read("inner_spmv")
     kernel_ms = {k: P.tb_profile_read(k) for k in P.tb.KERNELS}
     P.tb_profile_enable(False)
     clk = clocks.stop()
@@ -302,20 +383,35 @@ def run_ours(args):
     e2e = {"value": world * units_per_step * args.steps / e2e_tot, "unit": UNIT,
            "h2d_bytes_per_step": int(z_h.nbytes + w_h.nbytes + c_h.nbytes), "d2h_bytes_per_step": int(q_h.nbytes)}
 
-    # roofline of the dominant kernel (inner-CG SpMV w = S r on 2P real columns):
-    # 2 flops per stored matrix entry per real column
-    nnz = 16 * s.nb
-    flops_per_launch = 2.0 * nnz * 2 * args.panel
-    avg_s = ms_spmv / max(n_spmv, 1) / 1e3
-    achieved = flops_per_launch / avg_s / 1e12 if avg_s > 0 else None
-    traffic = stored_traffic("tb_kernels.cu", "k_inner_spmv")
-    roofline = {"kernel": "k_inner_spmv", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": traffic, "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on file)",
-                "launches": n_spmv, "avg_launch_us": avg_s * 1e6,
-                "algorithmic_bytes_per_launch": int(128 * s.nb + 4 * s.nb + 2 * 16 * s.n_orb * args.panel),
-                "flops_per_launch": flops_per_launch}
-    share = {k: round(v[1], 3) for k, v in kernel_ms.items()}
+    # roofline of the dominant kernel (largest device time in the timed region)
+    peaks = measured_peaks()
+    dom = max((k for k in KERNEL_INFO), key=lambda k: kernel_ms[k][1])
+    roofline = roofline_for(dom, kernel_ms[dom][1], kernel_ms[dom][0], s, args.panel, peaks)
+    others = {k: roofline_for(k, kernel_ms[k][1], kernel_ms[k][0], s, args.panel, peaks)
+              for k in KERNEL_INFO if k != dom and kernel_ms[k][0] > 0}
+    share = {k: round(v[1], 3) for k, v in kernel_ms.items() if v[0] > 0}
+
+    # the other precision on the same panel, for comparison
+    compare = None
+    if args.compare_steps > 0:
+        o2 = P.tb_default_opts(max_iter=args.iters, panel=args.panel, tol=args.tol, precision=1 - prec,
+                               inner_tol=args.inner_tol)
+        P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=o2, out=q_dev, allow_unconverged=True)
+        ct = []
+        for _ in range(args.compare_steps):
+            flush.zero_()
+            barrier()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=o2, out=q_dev, allow_unconverged=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            ct.append(ev0.elapsed_time(ev1) / 1e3)
+        ctot = reduce_max(sum(ct), world, "cuda")
+        compare = {"precision": "fp64" if prec == 1 else "mixed", "steps": args.compare_steps,
+                   "value": world * units_per_step * args.compare_steps / ctot,
+                   "ms_per_step": 1e3 * ctot / args.compare_steps}
 
     if rank != 0:
         if world > 1:
@@ -325,9 +421,11 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32" if prec else "f64", "data": "synthetic",
         "config": config_dict(args, s), "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
-        "roofline": roofline, "active_shift_value": active_value, "kernel_ms": share,
+        "roofline": roofline, "roofline_other_kernels": others, "active_shift_value": active_value,
+        "kernel_ms": share, "other_precision": compare, "peaks": peaks,
+        "panel_autotune": {str(k): v for k, v in tune.items()} if tune else None,
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
                                        / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),
     }

@@ -57,7 +57,7 @@ typedef enum {
     TB_ERR_NO_DEVICE = 9       /* no usable CUDA device                   */
 } tb_status;
 
-enum { TB_FP64 = 0 };
+enum { TB_FP64 = 0, TB_MIXED = 1 };
 
 /*
  * Block-sparse system in atom blocks (Section 2.2: one block per pair of
@@ -82,7 +82,8 @@ typedef struct {
     const double *eps;           /* [N] on-site levels (eV); needed when
                                     H_vals == NULL, else may be NULL     */
     double K;                    /* ASED constant of Eq. Hap-1           */
-    int32_t precision;           /* TB_FP64                              */
+    int32_t precision;           /* TB_FP64 (the handle serves both
+                                    solve precisions)                    */
 } tb_system_desc;
 
 /* Validate the system, copy it to the device (H built by Eq. Hap-1 if not
@@ -110,6 +111,13 @@ typedef struct {
     int32_t seed;             /* index of the initial seed shift; default 0           */
     int32_t switching;        /* 1 = seed switching (default), 0 = keep the seed       */
     int32_t force_switch_every; /* > 0: also switch every that many steps (testing)    */
+    int32_t precision;        /* TB_FP64 (default): every product in FP64;
+                                 TB_MIXED: the inner solve S r' = r runs as FP32 CG
+                                 corrections inside FP64 iterative refinement
+                                 (residual r - S r' in FP64 each round) until
+                                 ||r - S r'|| <= inner_tol ||r||; all other steps FP64 */
+    double inner_lo_tol;      /* TB_MIXED: relative tolerance of each FP32 CG round;
+                                 default 1e-6                                            */
 } tb_solve_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -204,7 +212,11 @@ enum {
     TB_K_SHIFT_STEP = 5,   /* all shifts, projections, seed switching      */
     TB_K_FULL_UPDATE = 6,  /* full-mode x^k, p^k updates                   */
     TB_K_OTHER = 7,        /* set-up, outputs, Lanczos helpers             */
-    TB_K_COUNT = 8
+    TB_K_INNER32_SPMV = 8, /* TB_MIXED: FP32 w = S r and dot products      */
+    TB_K_INNER32_UPDATE = 9, /* TB_MIXED: FP32 CG vector updates           */
+    TB_K_REFINE_RESIDUAL = 10, /* TB_MIXED: FP64 residual r - S r'         */
+    TB_K_REFINE_AUX = 11,  /* TB_MIXED: refinement start and correction add */
+    TB_K_COUNT = 12
 };
 int64_t tb_launch_count(void);
 void tb_profile_enable(int32_t enable);

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -24,7 +26,7 @@ struct tb_handle {
     std::vector<int32_t> orb2pad_h;   // caller orbital -> padded slot
     int32_t* orb2pad = nullptr;       // device copy
     double* eps_pad = nullptr;
-    int* flags_host = nullptr;        // pinned, 4 ints
+    int* flags_host = nullptr;        // pinned, NFLAGS ints
 };
 
 namespace {
@@ -99,6 +101,8 @@ tb_status check_opts(const tb_solve_opts* o) {
     if (!(o->tol > 0.0) || !(o->inner_tol > 0.0) || o->max_iter < 1 || o->inner_max_iter < 1) return TB_ERR_INVALID_ARG;
     if (o->panel < 0 || o->panel > MAX_P || (o->panel & (o->panel - 1)) != 0) return TB_ERR_INVALID_ARG;
     if (o->seed < 0 || o->force_switch_every < 0) return TB_ERR_INVALID_ARG;
+    if (o->precision != TB_FP64 && o->precision != TB_MIXED) return TB_ERR_INVALID_ARG;
+    if (o->precision == TB_MIXED && !(o->inner_lo_tol > 0.0 && o->inner_lo_tol < 1.0)) return TB_ERR_INVALID_ARG;
     return TB_OK;
 }
 
@@ -115,7 +119,7 @@ tb_status inner_cg(tb_handle* h, const PanelDev& p, int inner_max, int& pred, in
         }
         launched = target;
         TB_CK(cudaGetLastError());
-        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
         TB_CK(cudaStreamSynchronize(st));
         prof_harvest();
         if (h->flags_host[1] == 0) {
@@ -126,6 +130,98 @@ tb_status inner_cg(tb_handle* h, const PanelDev& p, int inner_max, int& pred, in
         if (launched >= inner_max) return TB_ERR_NOT_CONVERGED;
         target = std::min(launched + 8, inner_max);
     }
+}
+
+// FP32 CG of one refinement round (same prediction scheme as inner_cg).
+tb_status inner_cg32(tb_handle* h, const PanelDev& p, int inner_max, int& pred, int64_t& inner_total,
+                     cudaStream_t st) {
+    int launched = 0;
+    int target = std::min(std::max(pred, 1), inner_max);
+    while (true) {
+        for (int i = launched; i < target; ++i) {
+            launch_inner32_spmv(h->ds, p, i, st);
+            launch_inner32_update(h->ds, p, i, st);
+        }
+        launched = target;
+        TB_CK(cudaGetLastError());
+        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaStreamSynchronize(st));
+        prof_harvest();
+        if (h->flags_host[1] == 0) {
+            if (h->flags_host[4] > 0) {      // the round had work (flags[3] is this round's count)
+                inner_total += h->flags_host[3];
+                pred = h->flags_host[3] + 1;
+            }
+            return TB_OK;
+        }
+        if (launched >= inner_max) return TB_ERR_NOT_CONVERGED;
+        target = std::min(launched + 4, inner_max);
+    }
+}
+
+// r' = S^-1 b by FP32 CG corrections inside FP64 iterative refinement
+// (TB_MIXED).  The expected number of rounds is carried between calls so
+// that the common case costs one host synchronisation per round.
+void debug_inner32(tb_handle* h, const PanelDev& p, int round, cudaStream_t st) {
+    std::vector<InnerState> is(2 * p.P);
+    cudaMemcpyAsync(is.data(), p.inner32, sizeof(InnerState) * 2 * p.P, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    std::fprintf(stderr, "[tb] round %d flags %d %d %d %d %d\n", round, h->flags_host[0], h->flags_host[1],
+                 h->flags_host[2], h->flags_host[3], h->flags_host[4]);
+    double dbg[8] = {0};
+    if (p.dbg) {
+        cudaMemcpyAsync(dbg, p.dbg, sizeof(dbg), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        std::fprintf(stderr, "[tb] breakdown it %g rc %g gam %.6e del %.6e den %.6e b2 %.6e gprev %.6e alpha %.6e\n",
+                     dbg[0], dbg[1], dbg[2], dbg[3], dbg[4], dbg[5], dbg[6], dbg[7]);
+    }
+    for (int i = 0; i < 2 * p.P && i < 8; ++i)
+        std::fprintf(stderr, "[tb]   col %d: gprev %.3e alpha %.3e beta %.3e b2 %.3e conv %d skip %d scale %.3e\n",
+                     i, is[i].gamma_prev, is[i].alpha, is[i].beta, is[i].bnorm2, is[i].conv, is[i].skip,
+                     is[i].scale);
+}
+
+tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inner_max, int& pred32,
+                      int& rounds_pred, int64_t& inner_total, cudaStream_t st) {
+    launch_refine_start(h->ds, p, b, st);
+    launch_refine_scale(h->ds, p, b, st);
+    for (int round = 0;; ++round) {
+        tb_status s = inner_cg32(h, p, inner_max, pred32, inner_total, st);
+        if (s != TB_OK) return s;
+        if (h->flags_host[0] & ERR_NOT_SPD) {
+            debug_inner32(h, p, round, st);
+            return TB_ERR_S_NOT_SPD;
+        }
+        if (round > 0 && h->flags_host[4] == 0) {   // the last residual was already within tolerance
+            rounds_pred = round;
+            return TB_OK;
+        }
+        launch_refine_add(h->ds, p, st);
+        launch_refine_residual(h->ds, p, b, st);
+        launch_refine_scale(h->ds, p, p.Rin, st);
+        if (round + 1 >= rounds_pred) {
+            TB_CK(cudaGetLastError());
+            TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
+            TB_CK(cudaStreamSynchronize(st));
+            prof_harvest();
+            if (h->flags_host[4] == 0) {
+                rounds_pred = round + 1;
+                return TB_OK;
+            }
+        }
+        if (round + 1 >= 16) return TB_ERR_NOT_CONVERGED;
+    }
+}
+
+struct InnerCtx {
+    int pred = 64, pred32 = 32, rounds = 2;
+    int64_t total = 0;
+};
+
+tb_status inner_solve(tb_handle* h, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic,
+                      cudaStream_t st) {
+    if (p.mixed) return mixed_inner(h, p, b, inner_max, ic.pred32, ic.rounds, ic.total, st);
+    return inner_cg(h, p, inner_max, ic.pred, ic.total, st);
 }
 
 tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
@@ -158,11 +254,22 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
     p.inner_tol = o->inner_tol;
     p.switching = o->switching;
     p.force_switch_every = o->force_switch_every;
+    p.mixed = o->precision == TB_MIXED ? 1 : 0;
+    p.inner_lo_tol = o->inner_lo_tol;
     const size_t nv = (size_t)npad * P;
     tb_status s;
     double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
     for (double2** v : vecs)
         if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
+    if (p.mixed) {
+        float2** v32[] = {&p.r32, &p.p32, &p.s32, &p.w32, &p.x32};
+        for (float2** v : v32)
+            if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.inner32, 3 * 2 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.acc32, 8 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.dbg, 8)) != TB_OK) return s;
+        TB_CK(cudaMemsetAsync(p.dbg, 0, 8 * sizeof(double), st));
+    }
     if ((s = dalloc(cl, &p.col, P)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.inner, 2 * P)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.z, K)) != TB_OK) return s;
@@ -170,8 +277,9 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
     if ((s = dalloc(cl, &p.pi_prev, (size_t)P * K)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.conv_iter, (size_t)P * K)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.partials, (size_t)p.grid * 4 * P)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.counter, 1)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.flags, 4)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.counter, 1 + MAX_GROUPS)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.partials2, (size_t)MAX_GROUPS * 4 * std::max(p.P, 1))) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.flags, NFLAGS)) != TB_OK) return s;
     if (q.proj == PROJ_NONE) {
         if ((s = dalloc(cl, &p.ak, (size_t)P * K)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.bk, (size_t)P * K)) != TB_OK) return s;
@@ -194,14 +302,14 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         TB_CK(cudaMemcpyAsync(off_dev, q.row_ptr, sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, st));
     }
     TB_CK(cudaMemcpyAsync(p.z, q.z, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
-    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned), st));
+    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned) * (1 + MAX_GROUPS), st));
 
     std::vector<ColState> colh(P);
     std::vector<int32_t> convh((size_t)P * K);
     std::vector<int32_t> frowh((size_t)P * std::max(M, 1));
-    int64_t outer_total = 0, inner_total = 0, max_col_iters = 0;
+    int64_t outer_total = 0, max_col_iters = 0;
     int switches = 0, unconverged = 0, errbits = 0;
-    int pred = 64;
+    InnerCtx ic;
     tb_status final_status = TB_OK;
 
     for (int c0 = 0; c0 < R; c0 += P) {
@@ -230,13 +338,17 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         }
         TB_CK(cudaMemcpyAsync(p.col, colh.data(), sizeof(ColState) * P, cudaMemcpyHostToDevice, st));
         TB_CK(cudaMemsetAsync(p.inner, 0, sizeof(InnerState) * 2 * P, st));
-        TB_CK(cudaMemsetAsync(p.flags, 0, sizeof(int) * 4, st));
+        if (p.mixed) {
+            TB_CK(cudaMemsetAsync(p.inner32, 0, sizeof(InnerState) * 3 * 2 * P, st));
+            TB_CK(cudaMemsetAsync(p.acc32, 0, sizeof(double) * 8 * P, st));
+        }
+        TB_CK(cudaMemsetAsync(p.flags, 0, sizeof(int) * NFLAGS, st));
         if (q.proj == PROJ_ROWS)
             TB_CK(cudaMemcpyAsync(p.frow, frowh.data(), sizeof(int32_t) * P * M, cudaMemcpyHostToDevice, st));
 
         // r_0 = e_j, r'_0 = S^-1 r_0, rho_0, pi = 1, x^k = 0, p^k = r'_0
         launch_panel_init(h->ds, p, st);
-        if ((s = inner_cg(h, p, o->inner_max_iter, pred, inner_total, st)) != TB_OK) return s;
+        if ((s = inner_solve(h, p, p.Rcur, o->inner_max_iter, ic, st)) != TB_OK) return s;
         if (h->flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
         launch_finish(h->ds, p, st);
         launch_shift_init(h->ds, p, st);
@@ -246,7 +358,7 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         for (int n = 0; n < o->max_iter && active > 0; ++n) {
             launch_outer_spmm(h->ds, p, st);
             launch_outer_update(h->ds, p, st);
-            s = inner_cg(h, p, o->inner_max_iter, pred, inner_total, st);
+            s = inner_solve(h, p, p.Rcur, o->inner_max_iter, ic, st);
             if (s != TB_OK) return s;
             active = h->flags_host[2];     // columns still active after step n-1
             errbits |= h->flags_host[0];
@@ -267,7 +379,7 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         TB_CK(cudaGetLastError());
         TB_CK(cudaMemcpyAsync(colh.data(), p.col, sizeof(ColState) * P, cudaMemcpyDeviceToHost, st));
         TB_CK(cudaMemcpyAsync(convh.data(), p.conv_iter, sizeof(int32_t) * P * K, cudaMemcpyDeviceToHost, st));
-        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
         TB_CK(cudaStreamSynchronize(st));
         errbits |= h->flags_host[0];
         for (int c = 0; c < ncols; ++c) {
@@ -286,7 +398,7 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
     else if (unconverged > 0) final_status = TB_ERR_NOT_CONVERGED;
     if (stats) {
         stats->outer_iterations = outer_total;
-        stats->inner_iterations = inner_total;
+        stats->inner_iterations = ic.total;
         stats->max_column_iterations = max_col_iters;
         stats->switches = switches;
         stats->unconverged = unconverged;
@@ -371,6 +483,8 @@ void tb_default_opts(tb_solve_opts* o) {
     o->seed = 0;
     o->switching = 1;
     o->force_switch_every = 0;
+    o->precision = TB_FP64;
+    o->inner_lo_tol = 1e-6;
 }
 
 int64_t tb_launch_count(void) { return launch_count(); }
@@ -393,6 +507,7 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->ds.bcol);
     cudaFree(h->ds.S);
     cudaFree(h->ds.H);
+    cudaFree(h->ds.S32);
     cudaFree(h->orb2pad);
     cudaFree(h->eps_pad);
     if (h->flags_host) cudaFreeHost(h->flags_host);
@@ -526,12 +641,15 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     if ((e = cudaMalloc(&h->ds.bcol, sizeof(int) * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.S, sizeof(double) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.H, sizeof(double) * 16 * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.S32, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->orb2pad, sizeof(int32_t) * N)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->eps_pad, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
-    if ((e = cudaMallocHost(&h->flags_host, 4 * sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost(&h->flags_host, NFLAGS * sizeof(int))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.brow, browh.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.bcol, bcolh.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.S, Sp.data(), sizeof(double) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    std::vector<float> Sp32(Sp.begin(), Sp.end());
+    if ((e = cudaMemcpyAsync(h->ds.S32, Sp32.data(), sizeof(float) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->orb2pad, o2p.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->eps_pad, epsp.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if (d->H_vals) {
@@ -660,8 +778,9 @@ tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, doubl
     if ((s = dalloc(cl, &p.col, 1)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.inner, 2)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.partials, (size_t)p.grid * 4)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.counter, 1)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.flags, 4)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.counter, 1 + MAX_GROUPS)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.partials2, (size_t)MAX_GROUPS * 4 * std::max(p.P, 1))) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.flags, NFLAGS)) != TB_OK) return s;
     double *ad, *bd, *nd;
     if ((s = dalloc(cl, &ad, n_steps)) != TB_OK) return s;
     if ((s = dalloc(cl, &bd, (size_t)n_steps + 1)) != TB_OK) return s;
@@ -672,8 +791,8 @@ tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, doubl
     cs.row = h->orb2pad_h[j];
     TB_CK(cudaMemcpyAsync(p.col, &cs, sizeof(cs), cudaMemcpyHostToDevice, st));
     TB_CK(cudaMemsetAsync(p.inner, 0, 2 * sizeof(InnerState), st));
-    TB_CK(cudaMemsetAsync(p.flags, 0, 4 * sizeof(int), st));
-    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned), st));
+    TB_CK(cudaMemsetAsync(p.flags, 0, NFLAGS * sizeof(int), st));
+    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned) * (1 + MAX_GROUPS), st));
     TB_CK(cudaMemsetAsync(Uprev, 0, sizeof(double2) * npad, st));
     TB_CK(cudaMemsetAsync(ad, 0, sizeof(double) * n_steps, st));
     TB_CK(cudaMemsetAsync(bd, 0, sizeof(double) * (n_steps + 1), st));

@@ -12,6 +12,10 @@ constexpr int MAX_P = 256;     // right-hand sides per panel (power of two)
 constexpr int MAX_K = 1024;    // shifts per call
 constexpr int MAX_M = 1024;    // projected rows per column
 
+constexpr int NFLAGS = 8;      // device status words of a panel (see PanelDev::flags)
+constexpr int RED_GROUP = 32;  // CTAs per first-level group of the grid reductions
+constexpr int MAX_GROUPS = 64; // upper bound on first-level groups (grids <= 2048 CTAs)
+
 // error bits in PanelDev::flags[0]
 constexpr int ERR_BREAKDOWN = 1;
 constexpr int ERR_NOT_SPD = 2;
@@ -32,6 +36,7 @@ struct DevSystem {
     int* bcol = nullptr;       // [nb]
     double* S = nullptr;       // [nb][16] row-major 4x4 blocks
     double* H = nullptr;       // [nb][16]
+    float* S32 = nullptr;      // [nb][16] S rounded to FP32 (mixed-precision inner solve)
 };
 
 // Per right-hand side (complex column) state of a panel.
@@ -62,17 +67,23 @@ struct InnerState {
     double beta;
     double bnorm2;
     int32_t conv;
-    int32_t pad_;
+    int32_t skip;        // refinement: this real column needs no further correction
+    double scale;        // refinement: FP32 right-hand side = FP64 residual * scale
 };
 
 struct PanelDev {
     int P = 0, K = 0, npad = 0, M = 0, proj = PROJ_NONE;
     int grid = 0;                 // CTAs of the grid-stride kernels
-    double tol = 1e-10, inner_tol = 1e-13;
+    int mixed = 0;                // 1: inner S^-1 by FP32 CG inside FP64 refinement
+    double tol = 1e-10, inner_tol = 1e-13, inner_lo_tol = 1e-6;
     int switching = 1, force_switch_every = 0;
     // panel vectors, [npad][P] complex
     double2 *Rcur = nullptr, *Rprev = nullptr, *Rp = nullptr, *W = nullptr;
     double2 *Rin = nullptr, *Pin = nullptr, *Sin = nullptr;
+    // FP32 inner CG of the mixed-precision solve, [npad][P] complex floats
+    float2 *r32 = nullptr, *p32 = nullptr, *s32 = nullptr, *w32 = nullptr, *x32 = nullptr;
+    InnerState* inner32 = nullptr; // [3][2P]: refinement state, CG state slots 0 and 1
+    double* acc32 = nullptr;       // [2][4][P]: FP32 CG sums (gamma, delta per real column), two slots
     ColState* col = nullptr;       // [P]
     InnerState* inner = nullptr;   // [2P]
     double2* z = nullptr;          // [K]
@@ -82,15 +93,19 @@ struct PanelDev {
     int32_t* frow = nullptr;       // [P][M] padded rows (PROJ_ROWS)
     double2 *t = nullptr, *u = nullptr;          // [P][K][M] projected x, p
     double2 *X = nullptr, *Pk = nullptr;         // [K][npad][P] full mode x, p
-    double* partials = nullptr;    // [grid][4][P]
-    unsigned* counter = nullptr;   // arrival counter of the last-CTA reductions
-    int* flags = nullptr;          // [4]: errors, inner active, active columns, inner iters
+    double* partials = nullptr;    // [grid][4][P] per-CTA sums
+    double* partials2 = nullptr;   // [MAX_GROUPS][4][P] per-group sums
+    unsigned* counter = nullptr;   // [1 + MAX_GROUPS] arrival tickets of the grid reductions
+    double* dbg = nullptr;         // [8] record of the first inner-CG breakdown (diagnostics)
+    int* flags = nullptr;          // [NFLAGS]: 0 errors, 1 inner active, 2 active columns,
+                                   // 3 inner iterations used, 4 refinement: unconverged real columns,
+                                   // 5 FP32 CG rounds stopped early by a rounding breakdown
 };
 
 // kernel classes for launch accounting (same order as the TB_K_* constants
 // of the public header)
 enum { K_INNER_SPMV = 0, K_INNER_UPDATE, K_OUTER_SPMM, K_OUTER_UPDATE, K_FINISH, K_SHIFT_STEP,
-       K_FULL_UPDATE, K_OTHER, K_COUNT };
+       K_FULL_UPDATE, K_OTHER, K_INNER32_SPMV, K_INNER32_UPDATE, K_REFINE_RESIDUAL, K_REFINE_AUX, K_COUNT };
 void profile_enable(bool on);
 void prof_harvest();
 void profile_read(int id, int64_t* launches, double* ms);
@@ -104,6 +119,12 @@ void launch_outer_update(const DevSystem& s, const PanelDev& p, cudaStream_t st)
 void launch_inner_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_inner_update(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_finish(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_refine_start(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st);
+void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st);
+void launch_refine_add(const DevSystem& s, const PanelDev& p, cudaStream_t st);
+void launch_refine_scale(const DevSystem& s, const PanelDev& p, const double2* src, cudaStream_t st);
+void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
+void launch_inner32_update(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_full_update(const DevSystem& s, const PanelDev& p, cudaStream_t st);

@@ -56,21 +56,29 @@ __device__ void block_reduce_cols(const double (&v)[NV], int P, double* smem) {
     }
 }
 
-// Grid-wide per-column sums.  Returns true in the last CTA to finish, whose
-// threads tid < P then find the total of column tid in smem[q*THREADS + tid].
+// Grid-wide per-column sums, as a deterministic two-level tree.  Each CTA
+// writes its block sums; the last CTA of every group of RED_GROUP CTAs
+// (atomic ticket) adds its group's sums in CTA order; the last group
+// reducer adds the group sums in group order.  Returns true in that final
+// CTA, whose threads tid < P then find the total of column tid in
+// smem[q*THREADS + tid].  No CTA waits on another.
 template <int NV>
-__device__ bool grid_reduce_cols(const double (&v)[NV], int P, double* partials, unsigned* counter,
-                                 double* smem) {
+__device__ bool grid_reduce_cols(const double (&v)[NV], int P, const PanelDev& p, double* smem) {
     __shared__ int s_last;
     const int tid = threadIdx.x;
+    const int nblk = gridDim.x;
+    const int ngrp = (nblk + RED_GROUP - 1) / RED_GROUP;
+    const int grp = blockIdx.x / RED_GROUP;
+    const int gbeg = grp * RED_GROUP;
+    const int gsize = min(RED_GROUP, nblk - gbeg);
     block_reduce_cols<NV>(v, P, smem);
     if (tid < P) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) partials[((size_t)blockIdx.x * NV + q) * P + tid] = smem[q * THREADS + tid];
+        for (int q = 0; q < NV; ++q) p.partials[((size_t)blockIdx.x * NV + q) * P + tid] = smem[q * THREADS + tid];
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (tid == 0) s_last = (atomicAdd(&p.counter[1 + grp], 1u) == (unsigned)gsize - 1);
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
@@ -78,13 +86,33 @@ __device__ bool grid_reduce_cols(const double (&v)[NV], int P, double* partials,
     double acc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-    for (int b = g; b < (int)gridDim.x; b += G) {
+    for (int b = gbeg + g; b < gbeg + gsize; b += G) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&partials[((size_t)b * NV + q) * P + c]);
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&p.partials[((size_t)b * NV + q) * P + c]);
     }
     __syncthreads();
     block_reduce_cols<NV>(acc, P, smem);
-    if (tid == 0) *counter = 0u;
+    if (tid == 0) p.counter[1 + grp] = 0u;
+    if (ngrp == 1) return true;
+    if (tid < P) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) p.partials2[((size_t)grp * NV + q) * P + tid] = smem[q * THREADS + tid];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&p.counter[0], 1u) == (unsigned)ngrp - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    for (int b = g; b < ngrp; b += G) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&p.partials2[((size_t)b * NV + q) * P + c]);
+    }
+    __syncthreads();
+    block_reduce_cols<NV>(acc, P, smem);
+    if (tid == 0) p.counter[0] = 0u;
     return true;
 }
 
@@ -175,7 +203,7 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
             }
         }
     }
-    if (grid_reduce_cols<2>(mu, P, p.partials, p.counter, smem)) {
+    if (grid_reduce_cols<2>(mu, P, p, smem)) {
         const int t = threadIdx.x;
         if (t < P && p.col[t].active) {
             const double2 m = cmk(smem[t], smem[THREADS + t]);
@@ -257,7 +285,7 @@ __global__ void __launch_bounds__(THREADS) k_inner_spmv(DevSystem s, PanelDev p,
             }
         }
     }
-    if (grid_reduce_cols<4>(v, P, p.partials, p.counter, smem)) {
+    if (grid_reduce_cols<4>(v, P, p, smem)) {
         const int t = threadIdx.x;
         int nact = 0;
         if (t < P) {
@@ -338,6 +366,378 @@ __global__ void k_inner_update(PanelDev p, int it) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision inner solve (TB_MIXED): r' = S^-1 b by iterative
+// refinement.  x_0 = 0; round m computes res_m = b - S x_m in FP64, scales
+// it to unit norm, solves S d = res_m / ||res_m|| by CG in FP32 to relative
+// inner_lo_tol, and sets x_{m+1} = x_m + ||res_m|| d in FP64, until
+// ||res_m|| <= inner_tol ||b|| per real column.  The unit scaling keeps the
+// FP32 values away from underflow however small b or the residual are.
+// The FP32 CG reuses the Chronopoulos-Gear form of the FP64 one.
+// ---------------------------------------------------------------------------
+__device__ void refine_finish_counts(PanelDev& p, int nact) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    if (nact) atomicAdd(&s_cnt, nact);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        p.flags[1] = s_cnt;
+        p.flags[4] = s_cnt;
+    }
+}
+
+// round 0: ||b||, x = 0
+__global__ void __launch_bounds__(THREADS) k_refine_start(PanelDev p, const double2* __restrict__ b) {
+    __shared__ double smem[2 * THREADS];
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    const bool act = p.col[c].active != 0;
+    double v[2] = {0.0, 0.0};
+    const long long items = (long long)p.npad * P;
+    if (act) {
+        for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+             idx += (long long)gridDim.x * THREADS) {
+            const double2 bv = b[idx];
+            p.Rp[idx] = cmk(0.0, 0.0);
+            v[0] += bv.x * bv.x;
+            v[1] += bv.y * bv.y;
+        }
+    }
+    if (grid_reduce_cols<2>(v, P, p, smem)) {
+        const int t = threadIdx.x;
+        int nact = 0;
+        if (t < P) {
+            const bool cact = p.col[t].active != 0;
+            if (cact) p.col[t].rnorm = sqrt(smem[t] + smem[THREADS + t]);
+            for (int part = 0; part < 2; ++part) {
+                const double b2 = smem[part * THREADS + t];
+                p.inner[2 * t + part].bnorm2 = b2;
+                InnerState st = p.inner32[2 * t + part];
+                st.skip = (!cact || b2 == 0.0) ? 1 : 0;
+                st.scale = st.skip ? 0.0 : 1.0 / sqrt(b2);
+                p.inner32[2 * t + part] = st;
+                nact += st.skip ? 0 : 1;
+            }
+        }
+        refine_finish_counts(p, nact);
+    }
+}
+
+// res = b - S x in FP64 (x = r') into Rin; columns already within inner_tol
+// are marked to skip the next round, the others get scale = 1 / ||res||.
+__global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelDev p, const double2* __restrict__ b) {
+    __shared__ double smem[2 * THREADS];
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    const bool act = p.col[c].active != 0 && !(p.inner32[2 * c].skip && p.inner32[2 * c + 1].skip);
+    double v[2] = {0.0, 0.0};
+    const long long items = (long long)s.n_atoms * P;
+    if (act) {
+        for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+             idx += (long long)gridDim.x * THREADS) {
+            const int I = (int)(idx / P);
+            double2 acc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = cmk(0.0, 0.0);
+            for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
+                const int J = s.bcol[bb];
+                const double2* xr = p.Rp + (size_t)4 * J * P + c;
+                const double2 x0 = xr[0], x1 = xr[P], x2 = xr[2 * P], x3 = xr[3 * P];
+                const double2* Sb = reinterpret_cast<const double2*>(s.S + 16 * (size_t)bb);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const double2 s01 = __ldg(Sb + 2 * a), s23 = __ldg(Sb + 2 * a + 1);
+                    acc[a].x += s01.x * x0.x + s01.y * x1.x + s23.x * x2.x + s23.y * x3.x;
+                    acc[a].y += s01.x * x0.y + s01.y * x1.y + s23.x * x2.y + s23.y * x3.y;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const size_t e = (size_t)(4 * I + a) * P + c;
+                const double2 r = csub(b[e], acc[a]);
+                p.Rin[e] = r;
+                v[0] += r.x * r.x;
+                v[1] += r.y * r.y;
+            }
+        }
+    }
+    if (grid_reduce_cols<2>(v, P, p, smem)) {
+        const int t = threadIdx.x;
+        int nact = 0;
+        if (t < P) {
+            const bool cact = p.col[t].active != 0;
+            for (int part = 0; part < 2; ++part) {
+                InnerState st = p.inner32[2 * t + part];
+                if (!st.skip) {
+                    const double r2 = smem[part * THREADS + t];
+                    const double b2 = p.inner[2 * t + part].bnorm2;
+                    if (!cact || r2 <= p.inner_tol * p.inner_tol * b2 || r2 == 0.0) st.skip = 1;
+                    st.scale = st.skip ? 0.0 : 1.0 / sqrt(r2);
+                }
+                nact += st.skip ? 0 : 1;
+                p.inner32[2 * t + part] = st;
+            }
+        }
+        refine_finish_counts(p, nact);
+    }
+}
+
+// FP32 right-hand side of the round: src * scale (0 for skipped columns)
+__global__ void k_refine_scale(PanelDev p, const double2* __restrict__ src) {
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    if (blockIdx.x == 0)
+        for (int q = threadIdx.x; q < 8 * P; q += THREADS) p.acc32[q] = 0.0;   // both CG sum slots
+    if (!p.col[c].active) return;
+    const double s0 = p.inner32[2 * c].scale, s1 = p.inner32[2 * c + 1].scale;
+    const long long items = (long long)p.npad * P;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const double2 v = src[idx];
+        p.r32[idx] = make_float2((float)(v.x * s0), (float)(v.y * s1));
+    }
+}
+
+// x += d / scale (FP32 correction added in FP64) for the columns that took the round
+__global__ void k_refine_add(PanelDev p) {
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    if (!p.col[c].active) return;
+    const InnerState i0 = p.inner32[2 * c], i1 = p.inner32[2 * c + 1];
+    const bool u0 = !i0.skip, u1 = !i1.skip;
+    if (!u0 && !u1) return;
+    const double f0 = u0 ? 1.0 / i0.scale : 0.0, f1 = u1 ? 1.0 / i1.scale : 0.0;
+    const long long items = (long long)p.npad * P;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const float2 d = p.x32[idx];
+        double2 x = p.Rp[idx];
+        if (u0) x.x += (double)d.x * f0;
+        if (u1) x.y += (double)d.y * f1;
+        p.Rp[idx] = x;
+    }
+}
+
+// FP32 CG of one refinement round, Chronopoulos-Gear form, with no serial
+// tail: the SpMV kernel adds its per-column sums to a double-buffered FP64
+// accumulator with atomics, and every CTA of the following update kernel
+// derives the same alpha, beta and convergence flags from them (identical
+// inputs, identical arithmetic).  The CG state is double-buffered as well:
+// update(it) reads slot it&1 and CTA 0 writes slot (it+1)&1.
+//   inner32[0 .. 2P)        refinement state (skip, scale), written by k_refine_*
+//   inner32[2P .. 4P)       CG state slot 0
+//   inner32[4P .. 6P)       CG state slot 1
+//   acc32[(slot*4 + q)*P + c]  gamma_re, gamma_im, delta_re, delta_im of column c
+
+// w = S r (FP32) and the sums gamma = r.r, delta = w.r of every real column.
+// CPT complex columns per thread (2: one float4 per orbital row), P / CPT
+// threads per block row; the block-column index of the next block is loaded
+// one block ahead so the panel-row gathers do not wait on it.
+template <int CPT>
+__global__ void __launch_bounds__(THREADS, 4) k_inner32_spmv(DevSystem s, PanelDev p, int it) {
+    __shared__ double smem[4 * CPT * THREADS];
+    if (*(volatile int*)&p.flags[1] == 0) return;
+    const int P = p.P;
+    const int TPR = P / CPT;                    // threads per block row
+    const int t0 = threadIdx.x % TPR;
+    const int c0 = t0 * CPT;
+    const InnerState* base = p.inner32;
+    const InnerState* cgp = p.inner32 + (size_t)(1 + (it & 1)) * 2 * P;
+    bool live = false;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+        const int c = c0 + j;
+        live |= p.col[c].active && (it == 0 ? !(base[2 * c].skip && base[2 * c + 1].skip)
+                                            : !(cgp[2 * c].conv && cgp[2 * c + 1].conv));
+    }
+    float v32[4 * CPT];
+#pragma unroll
+    for (int q = 0; q < 4 * CPT; ++q) v32[q] = 0.f;
+    const long long items = (long long)s.n_atoms * TPR;
+    if (live) {
+        for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+             idx += (long long)gridDim.x * THREADS) {
+            const int I = (int)(idx / TPR);
+            float acc[4][2 * CPT];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 2 * CPT; ++q) acc[a][q] = 0.f;
+            const int b0 = s.brow[I], b1 = s.brow[I + 1];
+            int Jn = __ldg(s.bcol + b0);
+            for (int bb = b0; bb < b1; ++bb) {
+                const int J = Jn;
+                if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
+                float xv[4][2 * CPT];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2* xr = p.r32 + (size_t)(4 * J + e) * P + c0;
+                    if (CPT == 2) {
+                        const float4 q4 = *reinterpret_cast<const float4*>(xr);
+                        xv[e][0] = q4.x; xv[e][1] = q4.y; xv[e][2] = q4.z; xv[e][3] = q4.w;
+                    } else {
+                        const float2 q2 = *xr;
+                        xv[e][0] = q2.x; xv[e][1] = q2.y;
+                    }
+                }
+                const float4* Sb = reinterpret_cast<const float4*>(s.S32 + 16 * (size_t)bb);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float4 sr = __ldg(Sb + a);
+#pragma unroll
+                    for (int q = 0; q < 2 * CPT; ++q)
+                        acc[a][q] += sr.x * xv[0][q] + sr.y * xv[1][q] + sr.z * xv[2][q] + sr.w * xv[3][q];
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const size_t e = (size_t)(4 * I + a) * P + c0;
+                float r[2 * CPT];
+                if (CPT == 2) {
+                    const float4 r4 = *reinterpret_cast<const float4*>(p.r32 + e);
+                    r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
+                    *reinterpret_cast<float4*>(p.w32 + e) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                } else {
+                    const float2 r2 = p.r32[e];
+                    r[0] = r2.x; r[1] = r2.y;
+                    p.w32[e] = make_float2(acc[a][0], acc[a][1]);
+                }
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    v32[4 * j + 0] += r[2 * j] * r[2 * j];
+                    v32[4 * j + 1] += r[2 * j + 1] * r[2 * j + 1];
+                    v32[4 * j + 2] += acc[a][2 * j] * r[2 * j];
+                    v32[4 * j + 3] += acc[a][2 * j + 1] * r[2 * j + 1];
+                }
+            }
+        }
+    }
+    double v[4 * CPT];
+#pragma unroll
+    for (int q = 0; q < 4 * CPT; ++q) v[q] = v32[q];
+    block_reduce_cols<4 * CPT>(v, TPR, smem);
+    if (threadIdx.x < TPR) {
+        double* acc_slot = p.acc32 + (size_t)(it & 1) * 4 * P;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const int c = threadIdx.x * CPT + j;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double val = smem[(4 * j + q) * THREADS + threadIdx.x];
+                if (val != 0.0) atomicAdd(acc_slot + (size_t)q * P + c, val);
+            }
+        }
+    }
+}
+
+// CG scalars of iteration it from the accumulated sums (every CTA), then
+// p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s (FP32).
+__global__ void __launch_bounds__(THREADS) k_inner32_update(PanelDev p, int it) {
+    __shared__ float s_alpha[2 * MAX_P], s_beta[2 * MAX_P];
+    __shared__ unsigned char s_upd[2 * MAX_P];
+    __shared__ int s_cnt, s_err;
+    if (*(volatile int*)&p.flags[1] == 0) return;
+    const int P = p.P;
+    const InnerState* base = p.inner32;
+    const InnerState* prev = p.inner32 + (size_t)(1 + (it & 1)) * 2 * P;
+    InnerState* next = p.inner32 + (size_t)(1 + ((it + 1) & 1)) * 2 * P;
+    const double* acc_slot = p.acc32 + (size_t)(it & 1) * 4 * P;
+    if (threadIdx.x == 0) { s_cnt = 0; s_err = 0; }
+    __syncthreads();
+    for (int rc = threadIdx.x; rc < 2 * P; rc += THREADS) {
+        const int c = rc >> 1, part = rc & 1;
+        const bool cact = p.col[c].active != 0;
+        InnerState st = prev[rc];
+        const double gam = acc_slot[(size_t)part * P + c];
+        const double del = acc_slot[(size_t)(2 + part) * P + c];
+        if (it == 0) {
+            st.bnorm2 = gam;
+            st.conv = (!cact || base[rc].skip || gam == 0.0) ? 1 : 0;
+        }
+        if (!st.conv) {
+            if (gam <= p.inner_lo_tol * p.inner_lo_tol * st.bnorm2) {
+                st.conv = 1;
+            } else {
+                // FP32 scalars of the FP32 correction solve (the right-hand side
+                // is scaled to unit norm, so they stay in range); FP64 division
+                // is slow on this part and every CTA evaluates these.
+                const float gf = (float)gam;
+                const float beta = (it == 0) ? 0.f : gf / (float)st.gamma_prev;
+                const float den = (float)del - ((it == 0) ? 0.f : beta * gf / (float)st.alpha);
+                if (!(den > 0.f)) {
+                    // p^T S p <= 0.  At the first iteration (r^T S r <= 0), or
+                    // while the residual is still above 1 % of its start, rounding
+                    // cannot explain it: S is not positive definite.  Closer to
+                    // the FP32 rounding floor the round stops early and the FP64
+                    // refinement residual decides what is left (counted in
+                    // flags[5]).
+                    if (it == 0 || gam > 1e-4 * st.bnorm2) s_err = 1;
+                    else if (gam > 1e-10 * st.bnorm2) s_err = 2;
+                    if (s_err) {
+                        if (blockIdx.x == 0 && p.dbg) {
+                            p.dbg[0] = it; p.dbg[1] = rc; p.dbg[2] = gam; p.dbg[3] = del;
+                            p.dbg[4] = den; p.dbg[5] = st.bnorm2; p.dbg[6] = st.gamma_prev; p.dbg[7] = st.alpha;
+                        }
+                    }
+                    st.conv = 1;
+                } else {
+                    st.alpha = gf / den;
+                    st.beta = beta;
+                    st.gamma_prev = gam;
+                }
+            }
+        }
+        s_alpha[rc] = (float)st.alpha;
+        s_beta[rc] = (float)st.beta;
+        s_upd[rc] = st.conv ? 0 : 1;
+        if (!st.conv) atomicAdd(&s_cnt, 1);
+        if (blockIdx.x == 0) next[rc] = st;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        double* acc_next = p.acc32 + (size_t)((it + 1) & 1) * 4 * P;
+        for (int q = threadIdx.x; q < 4 * P; q += THREADS) acc_next[q] = 0.0;
+        if (threadIdx.x == 0) {
+            p.flags[1] = s_cnt;
+            if (s_cnt == 0) p.flags[3] = it;
+            if (s_err == 1) atomicOr(&p.flags[0], ERR_NOT_SPD);
+            if (s_err == 2) atomicAdd(&p.flags[5], 1);
+        }
+    }
+    if (s_cnt == 0) return;
+    const int c = threadIdx.x % P;
+    if (!p.col[c].active) return;
+    const bool u0 = s_upd[2 * c] != 0, u1 = s_upd[2 * c + 1] != 0;
+    if (!u0 && !u1 && it > 0) return;
+    const float a0 = s_alpha[2 * c], a1 = s_alpha[2 * c + 1], b0 = s_beta[2 * c], b1 = s_beta[2 * c + 1];
+    const long long items = (long long)p.npad * P;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const float2 r = p.r32[idx], w = p.w32[idx];
+        float2 pv = (it == 0) ? make_float2(0.f, 0.f) : p.p32[idx];
+        float2 sv = (it == 0) ? make_float2(0.f, 0.f) : p.s32[idx];
+        float2 x = (it == 0) ? make_float2(0.f, 0.f) : p.x32[idx];
+        float2 rn = r;
+        if (u0) {
+            pv.x = r.x + b0 * pv.x;
+            sv.x = w.x + b0 * sv.x;
+            x.x += a0 * pv.x;
+            rn.x = r.x - a0 * sv.x;
+        }
+        if (u1) {
+            pv.y = r.y + b1 * pv.y;
+            sv.y = w.y + b1 * sv.y;
+            x.y += a1 * pv.y;
+            rn.y = r.y - a1 * sv.y;
+        }
+        p.p32[idx] = pv;
+        p.s32[idx] = sv;
+        p.x32[idx] = x;
+        p.r32[idx] = rn;
+    }
+}
+
 // rho_{n+1} = r_{n+1}^T r'_{n+1} (unconjugated); also clears the count of
 // active columns that the shift step rebuilds.
 __global__ void __launch_bounds__(THREADS) k_finish(PanelDev p) {
@@ -354,7 +754,7 @@ __global__ void __launch_bounds__(THREADS) k_finish(PanelDev p) {
             v[1] += m.y;
         }
     }
-    if (grid_reduce_cols<2>(v, P, p.partials, p.counter, smem)) {
+    if (grid_reduce_cols<2>(v, P, p, smem)) {
         const int t = threadIdx.x;
         if (t < P && p.col[t].active) p.col[t].rho_new = cmk(smem[t], smem[THREADS + t]);
         if (t == 0) p.flags[2] = 0;
@@ -662,7 +1062,7 @@ __global__ void __launch_bounds__(THREADS) k_lz_dot(PanelDev p, const double2* _
     double v[1] = {0.0};
     for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS)
         v[0] += x[i].x * y[i].x;
-    if (grid_reduce_cols<1>(v, 1, p.partials, p.counter, smem)) {
+    if (grid_reduce_cols<1>(v, 1, p, smem)) {
         if (threadIdx.x == 0) *out = (mode == 0) ? smem[0] : sqrt(fmax(smem[0], 0.0));
     }
 }
@@ -827,6 +1227,33 @@ void launch_finish(const DevSystem&, const PanelDev& p, cudaStream_t st) {
         LaunchScope ls_(K_FINISH, st);
         k_finish<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
     }
+}
+void launch_refine_start(const DevSystem&, const PanelDev& p, const double2* b, cudaStream_t st) {
+    LaunchScope ls_(K_REFINE_AUX, st);
+    k_refine_start<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, b);
+}
+void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st) {
+    LaunchScope ls_(K_REFINE_RESIDUAL, st);
+    k_refine_residual<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
+}
+void launch_refine_scale(const DevSystem&, const PanelDev& p, const double2* src, cudaStream_t st) {
+    LaunchScope ls_(K_REFINE_AUX, st);
+    k_refine_scale<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, src);
+}
+void launch_refine_add(const DevSystem&, const PanelDev& p, cudaStream_t st) {
+    LaunchScope ls_(K_REFINE_AUX, st);
+    k_refine_add<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
+}
+void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st) {
+    LaunchScope ls_(K_INNER32_SPMV, st);
+    if (p.P >= 2)
+        k_inner32_spmv<2><<<grid_for((long long)s.n_atoms * (p.P / 2)), THREADS, 0, st>>>(s, p, it);
+    else
+        k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
+}
+void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
+    LaunchScope ls_(K_INNER32_UPDATE, st);
+    k_inner32_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
 }
 static size_t shift_smem(const PanelDev& p) { return sizeof(double2) * ((size_t)(p.M > 0 ? p.M : 1) + 3 * (size_t)p.K); }
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {

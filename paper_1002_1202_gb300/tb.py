@@ -19,6 +19,7 @@ from . import _build_lib
 TB_OK = 0
 TB_ERR_NOT_CONVERGED = 6
 TB_FP64 = 0
+TB_MIXED = 1
 
 _STATUS = {
     0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_NOT_SYMMETRIC", 3: "TB_ERR_S_NOT_SPD",
@@ -57,6 +58,8 @@ class SolveOpts(C.Structure):
         ("seed", C.c_int32),
         ("switching", C.c_int32),
         ("force_switch_every", C.c_int32),
+        ("precision", C.c_int32),
+        ("inner_lo_tol", C.c_double),
     ]
 
 
@@ -100,7 +103,8 @@ SIGNATURES = [
 ]
 
 KERNELS = {"inner_spmv": 0, "inner_update": 1, "outer_spmm": 2, "outer_update": 3, "finish": 4,
-           "shift_step": 5, "full_update": 6, "other": 7}
+           "shift_step": 5, "full_update": 6, "other": 7, "inner32_spmv": 8, "inner32_update": 9,
+           "refine_residual": 10, "refine_aux": 11}
 
 _lib = None
 

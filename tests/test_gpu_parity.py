@@ -49,6 +49,13 @@ def h1(P, c1):
     return P.tb_create_system(c1[0])
 
 
+@pytest.fixture(params=[0, 1], ids=["fp64", "mixed"])
+def prec(request):
+    """TB_FP64, or TB_MIXED (FP32 inner CG inside FP64 refinement): both must
+    meet the same parity bars."""
+    return request.param
+
+
 def _true_rel_res(H, S, z, X, cols):
     out = np.zeros((len(z), len(cols)))
     for k, zk in enumerate(z):
@@ -60,9 +67,9 @@ def _true_rel_res(H, S, z, X, cols):
     return out
 
 
-def test_full_mode_c1(P, c1, c1_ref, h1):
+def test_full_mode_c1(P, c1, c1_ref, h1, prec):
     s, H, S, z, w, cols = c1
-    x, st = P.tb_shifted_cocg(h1, z, cols)
+    x, st = P.tb_shifted_cocg(h1, z, cols, opts=P.tb_default_opts(precision=prec))
     X = x.cpu().numpy()
     assert st["status"] == "TB_OK" and st["unconverged"] == 0
     assert np.all(st["conv_iter"] > 0) and st["switches"] >= 1
@@ -84,10 +91,10 @@ def test_complex_symmetry(P, c1, h1):
 
 
 @pytest.mark.parametrize("force", [0, 6])
-def test_fixed_iterations_match_method_oracle(P, c1, h1, force):
+def test_fixed_iterations_match_method_oracle(P, c1, h1, force, prec):
     s, H, S, z, w, cols = c1
     n = 30
-    opts = P.tb_default_opts(max_iter=n, force_switch_every=force)
+    opts = P.tb_default_opts(max_iter=n, force_switch_every=force, precision=prec)
     x, st = P.tb_shifted_cocg(h1, z, cols[:3], opts=opts, allow_unconverged=True)
     X = x.cpu().numpy()
     for c, j in enumerate(cols[:3]):
@@ -126,16 +133,16 @@ def c1_mulliken(c1):
     return dense.mulliken_orbital(H, S, z, w, 2.0)
 
 
-def test_mulliken_orbital(P, c1, c1_mulliken, h1):
+def test_mulliken_orbital(P, c1, c1_mulliken, h1, prec):
     s, H, S, z, w, cols = c1
-    q, st = P.tb_mulliken_orbital(h1, z, w, cols, 2.0)
+    q, st = P.tb_mulliken_orbital(h1, z, w, cols, 2.0, opts=P.tb_default_opts(precision=prec))
     q = q.cpu().numpy()
     assert np.abs(q - c1_mulliken[cols]).max() <= 1e-6
 
 
-def test_mulliken_charges_and_sum_rule(P, c1, c1_mulliken, h1):
+def test_mulliken_charges_and_sum_rule(P, c1, c1_mulliken, h1, prec):
     s, H, S, z, w, cols = c1
-    q, st = P.tb_mulliken_charges(h1, z, w, 2.0)
+    q, st = P.tb_mulliken_charges(h1, z, w, 2.0, opts=P.tb_default_opts(precision=prec))
     q = q.cpu().numpy()
     ref = dense.mulliken_atom(c1_mulliken, s.orbital_atom(), s.n_atoms)
     assert np.abs(q - ref).max() <= 1e-6
@@ -168,11 +175,11 @@ def test_explicit_H_same_as_ased(P, c1, h1):
     assert np.abs(x1.cpu().numpy() - x2.cpu().numpy()).max() <= 1e-12 * np.abs(x1.cpu().numpy()).max()
 
 
-def test_panel_split_with_ragged_tail(P, c1, c1_ref, h1):
+def test_panel_split_with_ragged_tail(P, c1, c1_ref, h1, prec):
     s, H, S, z, w, cols = c1
     cols13 = choose_columns(256, 13, seed=7)
     zz = z[::6]
-    opts = P.tb_default_opts(panel=8)
+    opts = P.tb_default_opts(panel=8, precision=prec)
     x, st = P.tb_shifted_cocg(h1, zz, cols13, opts=opts)
     X = x.cpu().numpy()
     res = _true_rel_res(H, S, zz, X, cols13)
@@ -187,17 +194,18 @@ def test_single_shift_single_column(P, c1, h1):
     assert st["switches"] == 0
 
 
-def test_water_ragged_blocks(P):
+def test_water_ragged_blocks(P, prec):
     s = water_system(32, seed=4)
     S = s.dense_S()
     H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
     z, w = linspace_grid(8, -35.0, 5.0, 0.05)
     cols = [0, 1, 4, s.n_orb - 1]
     h = P.tb_create_system(s)
-    x, st = P.tb_shifted_cocg(h, z, cols)
+    opts = P.tb_default_opts(precision=prec)
+    x, st = P.tb_shifted_cocg(h, z, cols, opts=opts)
     X = x.cpu().numpy()
     assert _true_rel_res(H, S, z, X, cols).max() <= 1e-8
-    q, _ = P.tb_mulliken_orbital(h, z, w, cols, 2.0)
+    q, _ = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts)
     ref = dense.mulliken_orbital(H, S, z, w, 2.0)[cols]
     assert np.abs(q.cpu().numpy() - ref).max() <= 1e-6
 
@@ -238,7 +246,7 @@ def test_invalid_arguments(P, c1, h1):
         P.tb_shifted_cocg(h1, z[:2], [0], opts=P.tb_default_opts(panel=48))
 
 
-def test_overlap_not_positive_definite(P, c1):
+def test_overlap_not_positive_definite(P, c1, prec):
     s = c1[0]
     sv = s.S_vals.copy()
     bo = s.block_offsets()
@@ -248,7 +256,7 @@ def test_overlap_not_positive_definite(P, c1):
                 sv[bo[b]:bo[b + 1]] *= 3.0       # eigenvalues 1 + 3(l - 1) < 0
     h = P.tb_create(s.orb_per_atom, s.brow_ptr, s.bcol, sv, None, s.eps, s.K)
     with pytest.raises(P.TBError) as e:
-        P.tb_shifted_cocg(h, linspace_grid(4)[0], [0])
+        P.tb_shifted_cocg(h, linspace_grid(4)[0], [0], opts=P.tb_default_opts(precision=prec))
     assert e.value.status == 3
 
 
@@ -267,14 +275,15 @@ def test_max_shift_count(P, c1, h1):
 # sampled columns against the oracle's method after the same number of steps
 # ---------------------------------------------------------------------------
 @pytest.mark.slow
-def test_full_size_sampled_columns(P):
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_full_size_sampled_columns(P, precision):
     import torch
     s = si_system((8, 8, 8), sigma=0.05, seed=3, cutoff=4.0)
     z, w = gauss_legendre_grid(256, -20.0, 5.0, 0.01)
     cols = choose_columns(s.n_orb, 64, seed=5)
     n = 12
     h = P.tb_create_system(s)
-    opts = P.tb_default_opts(max_iter=n, panel=64)
+    opts = P.tb_default_opts(max_iter=n, panel=64, precision=precision)
     q, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts, allow_unconverged=True)
     q = q.cpu().numpy()
     Sc = s.to_csr()
@@ -285,3 +294,17 @@ def test_full_size_sampled_columns(P):
         out = method.generalized_shifted_cocg(Hc, Sc, z, j, max_iter=n, keep_full=False, functionals=F)
         qref = -(2.0 / math.pi) * np.imag(np.sum(w * out["t"][:, 0]))
         assert abs(q[c] - qref) <= 1e-9 * max(1.0, abs(qref))
+
+
+def test_mixed_inner_tolerances(P, c1, h1):
+    """TB_MIXED with a looser outer inner_tol still meets the residual bar,
+    and invalid FP32 round tolerances are rejected."""
+    s, H, S, z, w, cols = c1
+    opts = P.tb_default_opts(precision=1, inner_tol=1e-12, inner_lo_tol=1e-5)
+    x, st = P.tb_shifted_cocg(h1, z[::4], cols[:3], opts=opts)
+    assert _true_rel_res(H, S, z[::4], x.cpu().numpy(), cols[:3]).max() <= 1e-8
+    for bad in (0.0, 1.0, -1e-6):
+        with pytest.raises(P.TBError):
+            P.tb_shifted_cocg(h1, z[:2], [0], opts=P.tb_default_opts(precision=1, inner_lo_tol=bad))
+    with pytest.raises(P.TBError):
+        P.tb_shifted_cocg(h1, z[:2], [0], opts=P.tb_default_opts(precision=2))
