@@ -13,6 +13,7 @@
 
 using namespace tb;
 
+
 namespace tb {
 int max_grid();
 }
@@ -188,9 +189,9 @@ tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inn
     for (int round = 0;; ++round) {
         tb_status s = inner_cg32(h, p, inner_max, pred32, inner_total, st);
         if (s != TB_OK) return s;
-        if (h->flags_host[0] & ERR_NOT_SPD) {
+        if (h->flags_host[0] & (ERR_NOT_SPD | ERR_BREAKDOWN)) {
             debug_inner32(h, p, round, st);
-            return TB_ERR_S_NOT_SPD;
+            return (h->flags_host[0] & ERR_NOT_SPD) ? TB_ERR_S_NOT_SPD : TB_ERR_BREAKDOWN;
         }
         if (round > 0 && h->flags_host[4] == 0) {   // the last residual was already within tolerance
             rounds_pred = round;
@@ -263,8 +264,10 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
     if (p.mixed) {
         float2** v32[] = {&p.r32, &p.p32, &p.s32, &p.w32, &p.x32};
-        for (float2** v : v32)
+        for (float2** v : v32) {
             if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
+            TB_CK(cudaMemsetAsync(*v, 0, sizeof(float2) * nv, st));
+        }
         if ((s = dalloc(cl, &p.inner32, 3 * 2 * P)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.acc32, 8 * P)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.dbg, 8)) != TB_OK) return s;

@@ -472,7 +472,16 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
                 if (!st.skip) {
                     const double r2 = smem[part * THREADS + t];
                     const double b2 = p.inner[2 * t + part].bnorm2;
-                    if (!cact || r2 <= p.inner_tol * p.inner_tol * b2 || r2 == 0.0) st.skip = 1;
+                    if (!isfinite(r2)) {
+                        atomicOr(&p.flags[0], ERR_BREAKDOWN);
+                        if (p.dbg) {
+                            p.dbg[0] = -1.0; p.dbg[1] = 2 * t + part; p.dbg[2] = r2; p.dbg[3] = st.scale;
+                            p.dbg[4] = b2; p.dbg[5] = st.bnorm2; p.dbg[6] = st.gamma_prev; p.dbg[7] = st.alpha;
+                        }
+                        st.skip = 1;
+                    } else if (!cact || r2 <= p.inner_tol * p.inner_tol * b2 || r2 == 0.0) {
+                        st.skip = 1;
+                    }
                     st.scale = st.skip ? 0.0 : 1.0 / sqrt(r2);
                 }
                 nact += st.skip ? 0 : 1;
@@ -705,7 +714,7 @@ __global__ void __launch_bounds__(THREADS) k_inner32_update(PanelDev p, int it) 
             if (s_err == 2) atomicAdd(&p.flags[5], 1);
         }
     }
-    if (s_cnt == 0) return;
+    if (s_cnt == 0 && it > 0) return;   // at it == 0 the vectors are initialised in any case
     const int c = threadIdx.x % P;
     if (!p.col[c].active) return;
     const bool u0 = s_upd[2 * c] != 0, u1 = s_upd[2 * c + 1] != 0;
