@@ -54,7 +54,9 @@ typedef enum {
     TB_ERR_NOT_CONVERGED = 6,  /* max_iter reached; converged shifts valid*/
     TB_ERR_BREAKDOWN = 7,      /* COCG breakdown (rho or mu == 0)         */
     TB_ERR_TIMEOUT = 8,        /* a bounded device wait ran out           */
-    TB_ERR_NO_DEVICE = 9       /* no usable CUDA device                   */
+    TB_ERR_NO_DEVICE = 9,      /* no usable CUDA device                   */
+    TB_ERR_TOO_LARGE = 10      /* request exceeds the fixed scratch of the
+                                  allocation-free entry point              */
 } tb_status;
 
 enum { TB_FP64 = 0, TB_MIXED = 1 };
@@ -190,6 +192,37 @@ tb_status tb_mulliken_charges(tb_handle *h, int32_t K, const double *z, const do
  */
 tb_status tb_generalized_lanczos(tb_handle *h, int32_t j, int32_t n_steps, double inner_tol,
                                  double *a, double *b, double *norm, void *stream);
+
+/*
+ * Allocation-free generalized Lanczos.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate GPU memory while they
+ * call the library -- for example code that runs with the whole device
+ * memory already handed to another allocator, or that must not touch the
+ * allocator at all (a real-time loop that may not block on cudaMalloc, or a
+ * host that only hands over buffers it owns).  It takes the same arguments
+ * and gives the same results and errors as tb_generalized_lanczos, but it
+ * calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * memory is one fixed device array inside the library,
+ * TB_NOALLOC_SCRATCH_BYTES (16 MiB) long, which every GPU that loads the
+ * library holds until the process exits.  The handle (made by tb_create,
+ * which does allocate) and the outputs a, b, norm are the caller's.
+ *  - Size limit: the call needs about 160 * 4 * n_atoms + 16 * n_steps bytes
+ *    (plus ~50 kB); a request that does not fit returns TB_ERR_TOO_LARGE
+ *    before any device work (N up to ~100 000 orbitals with a few hundred
+ *    steps).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make
+ *    that first call before any stream capture on the device.
+ *  - All calls share the one array and it keeps the previous call's
+ *    contents (each call clears what it needs zeroed).  Calls whose GPU work
+ *    overlaps -- on different streams or from different threads, with this
+ *    or any other handle -- race on it; serialise them.
+ *  - Kernel timing (tb_profile_enable(1)) creates CUDA events on first use;
+ *    leave it off in callers that must not allocate.
+ */
+#define TB_NOALLOC_SCRATCH_BYTES (16u << 20)
+tb_status tb_generalized_lanczos_noalloc(tb_handle *h, int32_t j, int32_t n_steps, double inner_tol,
+                                         double *a, double *b, double *norm, void *stream);
 
 /*
  * Launch accounting for measurement tools (no counterpart in the paper).

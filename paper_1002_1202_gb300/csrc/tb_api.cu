@@ -9,10 +9,16 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 using namespace tb;
 
+// Fixed scratch of tb_generalized_lanczos_noalloc: one file-scope device
+// array, present on every GPU that loads this library until the process
+// exits.  Host code must not use the symbol as an address; it asks the
+// runtime for the array's device address once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TB_NOALLOC_SCRATCH_BYTES];
 
 namespace tb {
 int max_grid();
@@ -472,6 +478,7 @@ const char* tb_status_string(tb_status s) {
         case TB_ERR_BREAKDOWN: return "TB_ERR_BREAKDOWN";
         case TB_ERR_TIMEOUT: return "TB_ERR_TIMEOUT";
         case TB_ERR_NO_DEVICE: return "TB_ERR_NO_DEVICE";
+        case TB_ERR_TOO_LARGE: return "TB_ERR_TOO_LARGE";
     }
     return "TB_UNKNOWN_STATUS";
 }
@@ -813,6 +820,134 @@ tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, doubl
         launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, st);  // w = S^-1 H u - a u - b u_prev
         launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, st);                 // S w
         launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, st);                // b_{n+1} = ||w||_S
+        launch_lz_scale(p, Wv, U, Uprev, bd + n + 1, st);
+        TB_CK(cudaGetLastError());
+    }
+    if (h->flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
+    const bool ad_dev = is_device_ptr(a), bd_dev = is_device_ptr(b), nd_dev = is_device_ptr(norm);
+    TB_CK(cudaMemcpyAsync(a, ad, sizeof(double) * n_steps, ad_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaMemcpyAsync(b, bd, sizeof(double) * (n_steps + 1), bd_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaMemcpyAsync(norm, nd, sizeof(double), nd_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaStreamSynchronize(st));
+    return TB_OK;
+}
+
+}  // extern "C"
+
+// Device address of g_noalloc_scratch for the current device, looked up once
+// per device (with that device current) and cached.
+static tb_status noalloc_scratch(unsigned char** out) {
+    static std::mutex mu;
+    static void* addr[256] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        cudaGetLastError();
+        return TB_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return TB_ERR_CUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(addr[dev]);
+    return TB_OK;
+}
+
+// Carves aligned pieces out of the fixed scratch; fails when it would overrun.
+struct ScratchCarver {
+    unsigned char* base;
+    size_t used = 0, cap;
+    bool ok = true;
+    ScratchCarver(unsigned char* b, size_t c) : base(b), cap(c) {}
+    template <class T>
+    T* take(size_t count) {
+        const size_t bytes = ((count * sizeof(T) + 255) / 256) * 256;
+        if (used + bytes > cap) {
+            ok = false;
+            return nullptr;
+        }
+        T* r = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return r;
+    }
+};
+
+extern "C" {
+
+tb_status tb_generalized_lanczos_noalloc(tb_handle* h, int32_t j, int32_t n_steps, double inner_tol, double* a,
+                                         double* b, double* norm, void* stream) {
+    if (!h || !a || !b || !norm || n_steps < 1 || j < 0 || j >= h->n_orb) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int npad = h->ds.npad;
+    PanelDev p;
+    p.P = 1;
+    p.K = 1;
+    p.npad = npad;
+    p.grid = max_grid();
+    p.inner_tol = inner_tol > 0.0 ? inner_tol : 1e-13;
+    // size check before any device work: everything must fit in the fixed array
+    ScratchCarver dry(nullptr, TB_NOALLOC_SCRATCH_BYTES);
+    for (int v = 0; v < 10; ++v) dry.take<double2>(npad);
+    dry.take<ColState>(1);
+    dry.take<InnerState>(2);
+    dry.take<double>((size_t)p.grid * 4);
+    dry.take<double>((size_t)MAX_GROUPS * 4);
+    dry.take<unsigned>(1 + MAX_GROUPS);
+    dry.take<int>(NFLAGS);
+    dry.take<double>(n_steps);
+    dry.take<double>((size_t)n_steps + 1);
+    dry.take<double>(1);
+    if (!dry.ok) return TB_ERR_TOO_LARGE;
+    unsigned char* base = nullptr;
+    tb_status s = noalloc_scratch(&base);
+    if (s != TB_OK) return s;
+    ScratchCarver sc(base, TB_NOALLOC_SCRATCH_BYTES);
+    double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
+    for (double2** v : vecs) *v = sc.take<double2>(npad);
+    double2* U = sc.take<double2>(npad);
+    double2* Uprev = sc.take<double2>(npad);
+    double2* Wv = sc.take<double2>(npad);
+    p.col = sc.take<ColState>(1);
+    p.inner = sc.take<InnerState>(2);
+    p.partials = sc.take<double>((size_t)p.grid * 4);
+    p.partials2 = sc.take<double>((size_t)MAX_GROUPS * 4);
+    p.counter = sc.take<unsigned>(1 + MAX_GROUPS);
+    p.flags = sc.take<int>(NFLAGS);
+    double* ad = sc.take<double>(n_steps);
+    double* bd = sc.take<double>((size_t)n_steps + 1);
+    double* nd = sc.take<double>(1);
+    if (!sc.ok) return TB_ERR_TOO_LARGE;
+    // the array keeps the previous call's contents: clear everything that
+    // the step loop reads before writing
+    ColState cs;
+    std::memset(&cs, 0, sizeof(cs));
+    cs.active = 1;
+    cs.row = h->orb2pad_h[j];
+    TB_CK(cudaMemcpyAsync(p.col, &cs, sizeof(cs), cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemsetAsync(p.inner, 0, 2 * sizeof(InnerState), st));
+    TB_CK(cudaMemsetAsync(p.flags, 0, NFLAGS * sizeof(int), st));
+    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned) * (1 + MAX_GROUPS), st));
+    TB_CK(cudaMemsetAsync(Uprev, 0, sizeof(double2) * npad, st));
+    TB_CK(cudaMemsetAsync(ad, 0, sizeof(double) * n_steps, st));
+    TB_CK(cudaMemsetAsync(bd, 0, sizeof(double) * (n_steps + 1), st));
+    int pred = 64;
+    int64_t inner_total = 0;
+    const int inner_max = 1000;
+    launch_panel_init(h->ds, p, st);
+    if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
+    launch_lz_start(p, p.Rp, cs.row, U, nd, st);
+    for (int n = 0; n < n_steps; ++n) {
+        launch_lz_spmv(h->ds, h->ds.H, U, p.W, st);
+        launch_lz_dot(p, U, p.W, ad + n, 0, st);
+        TB_CK(cudaMemcpyAsync(p.Rin, p.W, sizeof(double2) * npad, cudaMemcpyDeviceToDevice, st));
+        if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
+        launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, st);
+        launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, st);
+        launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, st);
         launch_lz_scale(p, Wv, U, Uprev, bd + n + 1, st);
         TB_CK(cudaGetLastError());
     }

@@ -24,7 +24,7 @@ TB_MIXED = 1
 _STATUS = {
     0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_NOT_SYMMETRIC", 3: "TB_ERR_S_NOT_SPD",
     4: "TB_ERR_OOM", 5: "TB_ERR_CUDA", 6: "TB_ERR_NOT_CONVERGED", 7: "TB_ERR_BREAKDOWN",
-    8: "TB_ERR_TIMEOUT", 9: "TB_ERR_NO_DEVICE",
+    8: "TB_ERR_TIMEOUT", 9: "TB_ERR_NO_DEVICE", 10: "TB_ERR_TOO_LARGE",
 }
 
 
@@ -96,6 +96,7 @@ SIGNATURES = [
     ("tb_mulliken_charges", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP,
                                       C.POINTER(Stats), _VP]),
     ("tb_generalized_lanczos", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
+    ("tb_generalized_lanczos_noalloc", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
     ("tb_launch_count", C.c_int64, []),
     ("tb_profile_enable", None, [C.c_int32]),
@@ -325,6 +326,20 @@ def tb_generalized_lanczos(h: Handle, j: int, n_steps: int, inner_tol=1e-13, str
                                               C.c_void_p(nrm.ctypes.data), _stream(stream))
     _check(s, "tb_generalized_lanczos", False)
     return a, b, float(nrm[0])
+
+
+def tb_generalized_lanczos_noalloc(h: Handle, j: int, n_steps: int, inner_tol=1e-13, stream=None, out=None):
+    """Allocation-free variant of tb_generalized_lanczos: the library takes
+    its scratch from one fixed device array instead of allocating, for callers
+    that cannot allocate GPU memory during the call.  ``out`` may hold
+    preallocated (a, b, norm) host arrays or device tensors; returns them."""
+    if out is None:
+        out = (np.zeros(n_steps), np.zeros(n_steps + 1), np.zeros(1))
+    a, b, nrm = out
+    s = load_library().tb_generalized_lanczos_noalloc(h.ptr, int(j), int(n_steps), float(inner_tol),
+                                                      _out_ptr(a), _out_ptr(b), _out_ptr(nrm), _stream(stream))
+    _check(s, "tb_generalized_lanczos_noalloc", False)
+    return a, b, nrm
 
 
 def tb_status_string(s: int) -> str:
