@@ -426,6 +426,7 @@ def run_ours(args):
         "roofline": roofline, "roofline_other_kernels": others, "active_shift_value": active_value,
         "kernel_ms": share, "other_precision": compare, "peaks": peaks,
         "panel_autotune": {str(k): v for k, v in tune.items()} if tune else None,
+        "inner_redos": sum(st["inner_redos"] for st in stats),
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
                                        / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),
     }

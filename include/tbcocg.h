@@ -135,6 +135,8 @@ typedef struct {
     int32_t switches;          /* seed switches, all columns                       */
     int32_t unconverged;       /* (column, shift) pairs not converged              */
     double seconds;            /* wall time of the solve                           */
+    int32_t inner_redos;       /* TB_MIXED: inner solves whose FP32 corrections did
+                                  not converge and were redone with the FP64 CG     */
 } tb_stats;
 
 /*

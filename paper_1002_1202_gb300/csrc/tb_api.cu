@@ -170,6 +170,7 @@ tb_status inner_cg32(tb_handle* h, const PanelDev& p, int inner_max, int& pred, 
 // (TB_MIXED).  The expected number of rounds is carried between calls so
 // that the common case costs one host synchronisation per round.
 void debug_inner32(tb_handle* h, const PanelDev& p, int round, cudaStream_t st) {
+    if (!std::getenv("TB_DEBUG")) return;
     std::vector<InnerState> is(2 * p.P);
     cudaMemcpyAsync(is.data(), p.inner32, sizeof(InnerState) * 2 * p.P, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -188,6 +189,9 @@ void debug_inner32(tb_handle* h, const PanelDev& p, int round, cudaStream_t st) 
                      is[i].scale);
 }
 
+// TB_TRACE=1 in the environment prints the progress of every refinement round
+static const bool g_trace = std::getenv("TB_TRACE") != nullptr;
+
 tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inner_max, int& pred32,
                       int& rounds_pred, int64_t& inner_total, cudaStream_t st) {
     launch_refine_start(h->ds, p, b, st);
@@ -195,6 +199,31 @@ tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inn
     for (int round = 0;; ++round) {
         tb_status s = inner_cg32(h, p, inner_max, pred32, inner_total, st);
         if (s != TB_OK) return s;
+        if (g_trace && p.hist) {
+            const size_t nh = (size_t)HIST_IT * 2 * p.P * 4;
+            std::vector<double> hv(nh);
+            cudaMemcpyAsync(hv.data(), p.hist, sizeof(double) * nh, cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            for (int rc = 0; rc < 2 * p.P; ++rc) {
+                const double g0 = hv[((size_t)0 * 2 * p.P + rc) * 4];
+                double gmax = 0.0;
+                int itmax = 0;
+                for (int it = 0; it < HIST_IT; ++it) {
+                    const double g = hv[((size_t)it * 2 * p.P + rc) * 4];
+                    if (g > gmax) { gmax = g; itmax = it; }
+                }
+                if (g0 > 0.0 && gmax > 10.0 * g0) {
+                    std::fprintf(stderr, "[tb] round %d col %d: gamma grows %.3e -> %.3e at it %d\n", round, rc, g0,
+                                 gmax, itmax);
+                    for (int it = 0; it < 30; ++it) {
+                        const double* e = &hv[((size_t)it * 2 * p.P + rc) * 4];
+                        std::fprintf(stderr, "[tb]     it %2d gam %.6e del %.6e alpha %.6e beta %.6e\n", it, e[0], e[1],
+                                     e[2], e[3]);
+                    }
+                }
+            }
+            cudaMemsetAsync(p.hist, 0, sizeof(double) * nh, st);
+        }
         if (h->flags_host[0] & (ERR_NOT_SPD | ERR_BREAKDOWN)) {
             debug_inner32(h, p, round, st);
             return (h->flags_host[0] & ERR_NOT_SPD) ? TB_ERR_S_NOT_SPD : TB_ERR_BREAKDOWN;
@@ -206,6 +235,19 @@ tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inn
         launch_refine_add(h->ds, p, st);
         launch_refine_residual(h->ds, p, b, st);
         launch_refine_scale(h->ds, p, p.Rin, st);
+        if (g_trace) {
+            cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            std::vector<InnerState> is(2 * p.P);
+            cudaMemcpyAsync(is.data(), p.inner32, sizeof(InnerState) * 2 * p.P, cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            double smin = 1e300, smax = 0.0;
+            for (auto& x : is)
+                if (!x.skip) { smin = std::min(smin, x.scale); smax = std::max(smax, x.scale); }
+            std::fprintf(stderr, "[tb] round %d: cg iters %d, unconverged real columns %d, early stops %d, "
+                         "scale range %.3e .. %.3e\n", round, h->flags_host[3], h->flags_host[4],
+                         h->flags_host[5], smin, smax);
+        }
         if (round + 1 >= rounds_pred) {
             TB_CK(cudaGetLastError());
             TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -216,19 +258,33 @@ tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inn
                 return TB_OK;
             }
         }
-        if (round + 1 >= 16) return TB_ERR_NOT_CONVERGED;
+        if (round + 1 >= 8) return TB_ERR_NOT_CONVERGED;
     }
 }
 
 struct InnerCtx {
     int pred = 64, pred32 = 32, rounds = 2;
     int64_t total = 0;
+    int redo = 0;
 };
 
 tb_status inner_solve(tb_handle* h, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic,
                       cudaStream_t st) {
-    if (p.mixed) return mixed_inner(h, p, b, inner_max, ic.pred32, ic.rounds, ic.total, st);
-    return inner_cg(h, p, inner_max, ic.pred, ic.total, st);
+    if (!p.mixed) return inner_cg(h, p, inner_max, ic.pred, ic.total, st);
+    tb_status s = mixed_inner(h, p, b, inner_max, ic.pred32, ic.rounds, ic.total, st);
+    if (s != TB_ERR_BREAKDOWN && s != TB_ERR_NOT_CONVERGED) return s;
+    // The FP32 corrections failed to converge (or produced a non-finite
+    // residual): redo this inner solve with the FP64 CG, on the device.
+    // flags[0] keeps no trace of the failed attempt.
+    int zero = 0;
+    TB_CK(cudaMemcpyAsync(p.flags, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(p.Rin, b, sizeof(double2) * (size_t)p.npad * p.P, cudaMemcpyDeviceToDevice, st));
+    s = inner_cg(h, p, inner_max, ic.pred, ic.total, st);
+    if (s != TB_OK) return s;
+    launch_split_panel(p, st);
+    TB_CK(cudaGetLastError());
+    ++ic.redo;
+    return TB_OK;
 }
 
 tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
@@ -266,17 +322,26 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
     const size_t nv = (size_t)npad * P;
     tb_status s;
     double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
-    for (double2** v : vecs)
+    for (double2** v : vecs) {
         if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
+    }
     if (p.mixed) {
         float2** v32[] = {&p.r32, &p.p32, &p.s32, &p.w32, &p.x32};
         for (float2** v : v32) {
             if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
             TB_CK(cudaMemsetAsync(*v, 0, sizeof(float2) * nv, st));
         }
+        if ((s = dalloc(cl, &p.RpS, nv)) != TB_OK) return s;
+        TB_CK(cudaMemsetAsync(p.RpS, 0, sizeof(float4) * nv, st));
         if ((s = dalloc(cl, &p.inner32, 3 * 2 * P)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.acc32, 8 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.cgs, 4 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.cgu, 2 * P)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.dbg, 8)) != TB_OK) return s;
+        if (std::getenv("TB_TRACE")) {
+            if ((s = dalloc(cl, &p.hist, (size_t)HIST_IT * 2 * P * 4)) != TB_OK) return s;
+            TB_CK(cudaMemsetAsync(p.hist, 0, sizeof(double) * HIST_IT * 2 * P * 4, st));
+        }
         TB_CK(cudaMemsetAsync(p.dbg, 0, 8 * sizeof(double), st));
     }
     if ((s = dalloc(cl, &p.col, P)) != TB_OK) return s;
@@ -412,6 +477,7 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         stats->switches = switches;
         stats->unconverged = unconverged;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->inner_redos = ic.redo;
     }
     return final_status;
 }
@@ -518,6 +584,9 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->ds.S);
     cudaFree(h->ds.H);
     cudaFree(h->ds.S32);
+    cudaFree(h->ds.S32lo);
+    cudaFree(h->ds.H32hi);
+    cudaFree(h->ds.H32lo);
     cudaFree(h->orb2pad);
     cudaFree(h->eps_pad);
     if (h->flags_host) cudaFreeHost(h->flags_host);
@@ -652,14 +721,16 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     if ((e = cudaMalloc(&h->ds.S, sizeof(double) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.H, sizeof(double) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.S32, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.S32lo, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.H32hi, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.H32lo, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->orb2pad, sizeof(int32_t) * N)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->eps_pad, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&h->flags_host, NFLAGS * sizeof(int))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.brow, browh.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.bcol, bcolh.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.S, Sp.data(), sizeof(double) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
-    std::vector<float> Sp32(Sp.begin(), Sp.end());
-    if ((e = cudaMemcpyAsync(h->ds.S32, Sp32.data(), sizeof(float) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+
     if ((e = cudaMemcpyAsync(h->orb2pad, o2p.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->eps_pad, epsp.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if (d->H_vals) {
@@ -668,6 +739,10 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
         launch_ased_build(h->ds, h->eps_pad, d->K, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     }
+    // double-float splits of S and H for the mixed path's FP64-accurate products
+    launch_split_f64(h->ds.S, h->ds.S32, h->ds.S32lo, 16 * (long long)nb, st);
+    launch_split_f64(h->ds.H, h->ds.H32hi, h->ds.H32lo, 16 * (long long)nb, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
     *out = h;
     return TB_OK;

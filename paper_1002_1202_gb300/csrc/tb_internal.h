@@ -15,6 +15,7 @@ constexpr int MAX_M = 1024;    // projected rows per column
 constexpr int NFLAGS = 8;      // device status words of a panel (see PanelDev::flags)
 constexpr int RED_GROUP = 32;  // CTAs per first-level group of the grid reductions
 constexpr int MAX_GROUPS = 64; // upper bound on first-level groups (grids <= 2048 CTAs)
+constexpr int HIST_IT = 64;    // FP32 CG iterations kept by the trace history
 
 // error bits in PanelDev::flags[0]
 constexpr int ERR_BREAKDOWN = 1;
@@ -36,7 +37,10 @@ struct DevSystem {
     int* bcol = nullptr;       // [nb]
     double* S = nullptr;       // [nb][16] row-major 4x4 blocks
     double* H = nullptr;       // [nb][16]
-    float* S32 = nullptr;      // [nb][16] S rounded to FP32 (mixed-precision inner solve)
+    float* S32 = nullptr;      // [nb][16] S rounded to FP32 (S_hi of the double-float split)
+    float* S32lo = nullptr;    // [nb][16] S - S_hi in FP32
+    float* H32hi = nullptr;    // [nb][16] H rounded to FP32
+    float* H32lo = nullptr;    // [nb][16] H - H_hi in FP32
 };
 
 // Per right-hand side (complex column) state of a panel.
@@ -80,10 +84,13 @@ struct PanelDev {
     // panel vectors, [npad][P] complex
     double2 *Rcur = nullptr, *Rprev = nullptr, *Rp = nullptr, *W = nullptr;
     double2 *Rin = nullptr, *Pin = nullptr, *Sin = nullptr;
+    float4* RpS = nullptr;        // mixed: r' split (re_hi, re_lo, im_hi, im_lo) for double-float SpMVs
     // FP32 inner CG of the mixed-precision solve, [npad][P] complex floats
     float2 *r32 = nullptr, *p32 = nullptr, *s32 = nullptr, *w32 = nullptr, *x32 = nullptr;
     InnerState* inner32 = nullptr; // [3][2P]: refinement state, CG state slots 0 and 1
     double* acc32 = nullptr;       // [2][4][P]: FP32 CG sums (gamma, delta per real column), two slots
+    double* cgs = nullptr;         // [2][2P]: alpha, beta of the current FP32 CG iteration
+    unsigned char* cgu = nullptr;  // [2P]: real column updated in the current FP32 CG iteration
     ColState* col = nullptr;       // [P]
     InnerState* inner = nullptr;   // [2P]
     double2* z = nullptr;          // [K]
@@ -97,9 +104,12 @@ struct PanelDev {
     double* partials2 = nullptr;   // [MAX_GROUPS][4][P] per-group sums
     unsigned* counter = nullptr;   // [1 + MAX_GROUPS] arrival tickets of the grid reductions
     double* dbg = nullptr;         // [8] record of the first inner-CG breakdown (diagnostics)
+    double* hist = nullptr;        // trace only: [HIST_IT][2P][4] gamma, delta, alpha, beta per FP32 CG iteration
     int* flags = nullptr;          // [NFLAGS]: 0 errors, 1 inner active, 2 active columns,
                                    // 3 inner iterations used, 4 refinement: unconverged real columns,
-                                   // 5 FP32 CG rounds stopped early by a rounding breakdown
+                                   // 5 FP32 CG rounds stopped early by a rounding breakdown,
+                                   // 6 mixed inner solves redone with the FP64 CG,
+                                   // 7 FP32 CG iteration whose scalars are current
 };
 
 // kernel classes for launch accounting (same order as the TB_K_* constants
@@ -113,6 +123,7 @@ int64_t launch_count();
 
 // ---- launchers (tb_kernels.cu) -------------------------------------------
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st);
+void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaStream_t st);
 void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_outer_spmm(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_outer_update(const DevSystem& s, const PanelDev& p, cudaStream_t st);
@@ -123,6 +134,7 @@ void launch_refine_start(const DevSystem& s, const PanelDev& p, const double2* b
 void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st);
 void launch_refine_add(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_refine_scale(const DevSystem& s, const PanelDev& p, const double2* src, cudaStream_t st);
+void launch_split_panel(const PanelDev& p, cudaStream_t st);
 void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_inner32_update(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);

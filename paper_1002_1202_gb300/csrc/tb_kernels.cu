@@ -39,6 +39,32 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
 
+// Double-float products for FP64-accurate SpMVs on FP32 units (mixed path).
+// A value is carried as hi + lo (two FP32 numbers, |lo| <= ulp(hi)/2).
+// acc += s * x: the rounded product p = sh*xh and its exact error
+// fma(sh, xh, -p) (Dekker / Ogita-Rump-Oishi error-free transformations),
+// the cross terms sh*xl + sl*xh (sl*xl is below the working accuracy), and a
+// two-sum of hi + p whose error goes to lo.  The _rn intrinsics keep the
+// compiler from contracting these steps into FMAs, which would break the
+// error terms.  Relative accuracy of a sum of n products ~ n * 2^-46.
+__device__ __forceinline__ void df_mac(float& hi, float& lo, float sh, float sl, float xh, float xl) {
+    const float pr = __fmul_rn(sh, xh);
+    float e = fmaf(sh, xh, -pr);
+    e = fmaf(sh, xl, e);
+    e = fmaf(sl, xh, e);
+    const float t = __fadd_rn(hi, pr);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// complex double -> (re_hi, re_lo, im_hi, im_lo)
+__device__ __forceinline__ float4 df_split(double2 v) {
+    const float rh = (float)v.x, ih = (float)v.y;
+    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
 // Sum NV per-thread values over the threads of a CTA that share a column
 // (column = tid % P).  Result for column c (< P) in smem[q*THREADS + c].
 template <int NV>
@@ -137,6 +163,15 @@ __global__ void k_ased_build(int n_atoms, const int* __restrict__ brow, const in
     }
 }
 
+// hi + lo FP32 split of a FP64 array
+__global__ void k_split_f64(const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float h = (float)v[i];
+        hi[i] = h;
+        lo[i] = (float)(v[i] - (double)h);
+    }
+}
+
 // r_0 = b = e_j, r_{-1} = 0, inner right-hand side = b
 __global__ void k_panel_init(PanelDev p) {
     const long long items = (long long)p.npad * p.P;
@@ -156,6 +191,7 @@ __global__ void k_panel_init(PanelDev p) {
 // alpha_n = rho_n / mu (Eqs. CGp:p, CGp:r and the alpha_n of Section 3.3).
 // Pending seed-switch scales of r_n, r'_n, r_{n-1} are applied on the fly.
 // ---------------------------------------------------------------------------
+template <bool DF>
 __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p) {
     __shared__ double smem[2 * THREADS];
     const int P = p.P;
@@ -171,22 +207,59 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
              idx += (long long)gridDim.x * THREADS) {
             const int I = (int)(idx / P);
             double2 aS[4], aH[4];
+            if (DF) {
+                // double-float products: S_hi/S_lo, H_hi/H_lo times the split r'
+                float sh[4][2], sl[4][2], hh[4][2], hl[4][2];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) { aS[a] = cmk(0.0, 0.0); aH[a] = cmk(0.0, 0.0); }
-            for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
-                const int J = s.bcol[b];
-                const double2* xr = p.Rp + (size_t)4 * J * P + c;
-                const double2 x0 = xr[0], x1 = xr[P], x2 = xr[2 * P], x3 = xr[3 * P];
-                const double2* Sb = reinterpret_cast<const double2*>(s.S + 16 * (size_t)b);
-                const double2* Hb = reinterpret_cast<const double2*>(s.H + 16 * (size_t)b);
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) { sh[a][q] = 0.f; sl[a][q] = 0.f; hh[a][q] = 0.f; hl[a][q] = 0.f; }
+                for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
+                    const int J = s.bcol[b];
+                    const float4* xr = p.RpS + (size_t)4 * J * P + c;
+                    const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
+                    const float4* Sh = reinterpret_cast<const float4*>(s.S32 + 16 * (size_t)b);
+                    const float4* Sl = reinterpret_cast<const float4*>(s.S32lo + 16 * (size_t)b);
+                    const float4* Hh = reinterpret_cast<const float4*>(s.H32hi + 16 * (size_t)b);
+                    const float4* Hl = reinterpret_cast<const float4*>(s.H32lo + 16 * (size_t)b);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const float4 s4h = __ldg(Sh + a), s4l = __ldg(Sl + a);
+                        const float4 h4h = __ldg(Hh + a), h4l = __ldg(Hl + a);
+                        const float svh[4] = {s4h.x, s4h.y, s4h.z, s4h.w}, svl[4] = {s4l.x, s4l.y, s4l.z, s4l.w};
+                        const float hvh[4] = {h4h.x, h4h.y, h4h.z, h4h.w}, hvl[4] = {h4l.x, h4l.y, h4l.z, h4l.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            df_mac(sh[a][0], sl[a][0], svh[e], svl[e], x[e].x, x[e].y);
+                            df_mac(sh[a][1], sl[a][1], svh[e], svl[e], x[e].z, x[e].w);
+                            df_mac(hh[a][0], hl[a][0], hvh[e], hvl[e], x[e].x, x[e].y);
+                            df_mac(hh[a][1], hl[a][1], hvh[e], hvl[e], x[e].z, x[e].w);
+                        }
+                    }
+                }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const double2 s01 = __ldg(Sb + 2 * a), s23 = __ldg(Sb + 2 * a + 1);
-                    const double2 h01 = __ldg(Hb + 2 * a), h23 = __ldg(Hb + 2 * a + 1);
-                    aS[a].x += s01.x * x0.x + s01.y * x1.x + s23.x * x2.x + s23.y * x3.x;
-                    aS[a].y += s01.x * x0.y + s01.y * x1.y + s23.x * x2.y + s23.y * x3.y;
-                    aH[a].x += h01.x * x0.x + h01.y * x1.x + h23.x * x2.x + h23.y * x3.x;
-                    aH[a].y += h01.x * x0.y + h01.y * x1.y + h23.x * x2.y + h23.y * x3.y;
+                    aS[a] = cmk((double)sh[a][0] + (double)sl[a][0], (double)sh[a][1] + (double)sl[a][1]);
+                    aH[a] = cmk((double)hh[a][0] + (double)hl[a][0], (double)hh[a][1] + (double)hl[a][1]);
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) { aS[a] = cmk(0.0, 0.0); aH[a] = cmk(0.0, 0.0); }
+                for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
+                    const int J = s.bcol[b];
+                    const double2* xr = p.Rp + (size_t)4 * J * P + c;
+                    const double2 x0 = xr[0], x1 = xr[P], x2 = xr[2 * P], x3 = xr[3 * P];
+                    const double2* Sb = reinterpret_cast<const double2*>(s.S + 16 * (size_t)b);
+                    const double2* Hb = reinterpret_cast<const double2*>(s.H + 16 * (size_t)b);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const double2 s01 = __ldg(Sb + 2 * a), s23 = __ldg(Sb + 2 * a + 1);
+                        const double2 h01 = __ldg(Hb + 2 * a), h23 = __ldg(Hb + 2 * a + 1);
+                        aS[a].x += s01.x * x0.x + s01.y * x1.x + s23.x * x2.x + s23.y * x3.x;
+                        aS[a].y += s01.x * x0.y + s01.y * x1.y + s23.x * x2.y + s23.y * x3.y;
+                        aH[a].x += h01.x * x0.x + h01.y * x1.x + h23.x * x2.x + h23.y * x3.x;
+                        aH[a].y += h01.x * x0.y + h01.y * x1.y + h23.x * x2.y + h23.y * x3.y;
+                    }
                 }
             }
 #pragma unroll
@@ -400,6 +473,7 @@ __global__ void __launch_bounds__(THREADS) k_refine_start(PanelDev p, const doub
              idx += (long long)gridDim.x * THREADS) {
             const double2 bv = b[idx];
             p.Rp[idx] = cmk(0.0, 0.0);
+            p.RpS[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
             v[0] += bv.x * bv.x;
             v[1] += bv.y * bv.y;
         }
@@ -426,6 +500,7 @@ __global__ void __launch_bounds__(THREADS) k_refine_start(PanelDev p, const doub
 
 // res = b - S x in FP64 (x = r') into Rin; columns already within inner_tol
 // are marked to skip the next round, the others get scale = 1 / ||res||.
+template <bool DF>
 __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelDev p, const double2* __restrict__ b) {
     __shared__ double smem[2 * THREADS];
     const int P = p.P;
@@ -438,18 +513,44 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
              idx += (long long)gridDim.x * THREADS) {
             const int I = (int)(idx / P);
             double2 acc[4];
+            if (DF) {
+                float ah[4][2], al[4][2];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a] = cmk(0.0, 0.0);
-            for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
-                const int J = s.bcol[bb];
-                const double2* xr = p.Rp + (size_t)4 * J * P + c;
-                const double2 x0 = xr[0], x1 = xr[P], x2 = xr[2 * P], x3 = xr[3 * P];
-                const double2* Sb = reinterpret_cast<const double2*>(s.S + 16 * (size_t)bb);
+                for (int a = 0; a < 4; ++a) { ah[a][0] = ah[a][1] = al[a][0] = al[a][1] = 0.f; }
+                for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
+                    const int J = s.bcol[bb];
+                    const float4* xr = p.RpS + (size_t)4 * J * P + c;
+                    const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
+                    const float4* Sh = reinterpret_cast<const float4*>(s.S32 + 16 * (size_t)bb);
+                    const float4* Sl = reinterpret_cast<const float4*>(s.S32lo + 16 * (size_t)bb);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const double2 s01 = __ldg(Sb + 2 * a), s23 = __ldg(Sb + 2 * a + 1);
-                    acc[a].x += s01.x * x0.x + s01.y * x1.x + s23.x * x2.x + s23.y * x3.x;
-                    acc[a].y += s01.x * x0.y + s01.y * x1.y + s23.x * x2.y + s23.y * x3.y;
+                    for (int a = 0; a < 4; ++a) {
+                        const float4 s4h = __ldg(Sh + a), s4l = __ldg(Sl + a);
+                        const float svh[4] = {s4h.x, s4h.y, s4h.z, s4h.w}, svl[4] = {s4l.x, s4l.y, s4l.z, s4l.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            df_mac(ah[a][0], al[a][0], svh[e], svl[e], x[e].x, x[e].y);
+                            df_mac(ah[a][1], al[a][1], svh[e], svl[e], x[e].z, x[e].w);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    acc[a] = cmk((double)ah[a][0] + (double)al[a][0], (double)ah[a][1] + (double)al[a][1]);
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a] = cmk(0.0, 0.0);
+                for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
+                    const int J = s.bcol[bb];
+                    const double2* xr = p.Rp + (size_t)4 * J * P + c;
+                    const double2 x0 = xr[0], x1 = xr[P], x2 = xr[2 * P], x3 = xr[3 * P];
+                    const double2* Sb = reinterpret_cast<const double2*>(s.S + 16 * (size_t)bb);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const double2 s01 = __ldg(Sb + 2 * a), s23 = __ldg(Sb + 2 * a + 1);
+                        acc[a].x += s01.x * x0.x + s01.y * x1.x + s23.x * x2.x + s23.y * x3.x;
+                        acc[a].y += s01.x * x0.y + s01.y * x1.y + s23.x * x2.y + s23.y * x3.y;
+                    }
                 }
             }
 #pragma unroll
@@ -496,8 +597,10 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
 __global__ void k_refine_scale(PanelDev p, const double2* __restrict__ src) {
     const int P = p.P;
     const int c = threadIdx.x % P;
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int q = threadIdx.x; q < 8 * P; q += THREADS) p.acc32[q] = 0.0;   // both CG sum slots
+        if (threadIdx.x == 0) p.flags[7] = -1;                                  // no CG scalars yet
+    }
     if (!p.col[c].active) return;
     const double s0 = p.inner32[2 * c].scale, s1 = p.inner32[2 * c + 1].scale;
     const long long items = (long long)p.npad * P;
@@ -506,6 +609,18 @@ __global__ void k_refine_scale(PanelDev p, const double2* __restrict__ src) {
         const double2 v = src[idx];
         p.r32[idx] = make_float2((float)(v.x * s0), (float)(v.y * s1));
     }
+}
+
+// r' copied into the FP64 inner right-hand side slot and split for the
+// double-float products (after an FP64 redo of a mixed inner solve)
+__global__ void k_split_panel(PanelDev p) {
+    const int P = p.P;
+    const int c = threadIdx.x % P;
+    if (!p.col[c].active) return;
+    const long long items = (long long)p.npad * P;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS)
+        p.RpS[idx] = df_split(p.Rp[idx]);
 }
 
 // x += d / scale (FP32 correction added in FP64) for the columns that took the round
@@ -522,9 +637,12 @@ __global__ void k_refine_add(PanelDev p) {
          idx += (long long)gridDim.x * THREADS) {
         const float2 d = p.x32[idx];
         double2 x = p.Rp[idx];
-        if (u0) x.x += (double)d.x * f0;
-        if (u1) x.y += (double)d.y * f1;
+        // a non-finite correction is dropped: the next round starts again
+        // from the FP64 residual
+        if (u0 && isfinite(d.x)) x.x += (double)d.x * f0;
+        if (u1 && isfinite(d.y)) x.y += (double)d.y * f1;
         p.Rp[idx] = x;
+        p.RpS[idx] = df_split(x);
     }
 }
 
@@ -640,11 +758,11 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_spmv(DevSystem s, PanelD
     }
 }
 
-// CG scalars of iteration it from the accumulated sums (every CTA), then
-// p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s (FP32).
-__global__ void __launch_bounds__(THREADS) k_inner32_update(PanelDev p, int it) {
-    __shared__ float s_alpha[2 * MAX_P], s_beta[2 * MAX_P];
-    __shared__ unsigned char s_upd[2 * MAX_P];
+// CG scalars of iteration it, once, in one CTA: FP64 alpha, beta and the
+// convergence of every real column from the accumulated sums; the update
+// kernel that follows only reads them (cgs[0..2P) alpha, [2P..4P) beta,
+// upd flags in cgu[0..2P)).
+__global__ void __launch_bounds__(THREADS) k_inner32_scalars(PanelDev p, int it) {
     __shared__ int s_cnt, s_err;
     if (*(volatile int*)&p.flags[1] == 0) return;
     const int P = p.P;
@@ -668,58 +786,62 @@ __global__ void __launch_bounds__(THREADS) k_inner32_update(PanelDev p, int it) 
             if (gam <= p.inner_lo_tol * p.inner_lo_tol * st.bnorm2) {
                 st.conv = 1;
             } else {
-                // FP32 scalars of the FP32 correction solve (the right-hand side
-                // is scaled to unit norm, so they stay in range); FP64 division
-                // is slow on this part and every CTA evaluates these.
-                const float gf = (float)gam;
-                const float beta = (it == 0) ? 0.f : gf / (float)st.gamma_prev;
-                const float den = (float)del - ((it == 0) ? 0.f : beta * gf / (float)st.alpha);
-                if (!(den > 0.f)) {
-                    // p^T S p <= 0.  At the first iteration (r^T S r <= 0), or
-                    // while the residual is still above 1 % of its start, rounding
-                    // cannot explain it: S is not positive definite.  Closer to
-                    // the FP32 rounding floor the round stops early and the FP64
-                    // refinement residual decides what is left (counted in
-                    // flags[5]).
-                    if (it == 0 || gam > 1e-4 * st.bnorm2) s_err = 1;
-                    else if (gam > 1e-10 * st.bnorm2) s_err = 2;
-                    if (s_err) {
-                        if (blockIdx.x == 0 && p.dbg) {
-                            p.dbg[0] = it; p.dbg[1] = rc; p.dbg[2] = gam; p.dbg[3] = del;
-                            p.dbg[4] = den; p.dbg[5] = st.bnorm2; p.dbg[6] = st.gamma_prev; p.dbg[7] = st.alpha;
-                        }
+                const double beta = (it == 0) ? 0.0 : gam / st.gamma_prev;
+                const double den = del - ((it == 0) ? 0.0 : beta * gam / st.alpha);
+                // In exact arithmetic p^T S p >= r^T S r / cond(S); p^T S p <= 0 at
+                // the first iteration (r^T S r <= 0), or while the residual is above
+                // 1 % of its start, means S is not positive definite.  Otherwise a
+                // non-positive or collapsed value is cancellation in the FP32
+                // recurrences: the round stops and the FP64 refinement residual
+                // decides what is left (counted in flags[5]).
+                if (!(den > 0.0) || (it > 0 && den < 1e-4 * del)) {
+                    if (it == 0 || (!(den > 0.0) && gam > 1e-4 * st.bnorm2)) s_err = 1;
+                    else s_err = 2;
+                    if (p.dbg) {
+                        p.dbg[0] = it; p.dbg[1] = rc; p.dbg[2] = gam; p.dbg[3] = del;
+                        p.dbg[4] = den; p.dbg[5] = st.bnorm2; p.dbg[6] = st.gamma_prev; p.dbg[7] = st.alpha;
                     }
                     st.conv = 1;
                 } else {
-                    st.alpha = gf / den;
+                    st.alpha = gam / den;
                     st.beta = beta;
                     st.gamma_prev = gam;
                 }
             }
         }
-        s_alpha[rc] = (float)st.alpha;
-        s_beta[rc] = (float)st.beta;
-        s_upd[rc] = st.conv ? 0 : 1;
+        p.cgs[rc] = st.alpha;
+        p.cgs[2 * P + rc] = st.beta;
+        p.cgu[rc] = st.conv ? 0 : 1;
         if (!st.conv) atomicAdd(&s_cnt, 1);
-        if (blockIdx.x == 0) next[rc] = st;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0) {
-        double* acc_next = p.acc32 + (size_t)((it + 1) & 1) * 4 * P;
-        for (int q = threadIdx.x; q < 4 * P; q += THREADS) acc_next[q] = 0.0;
-        if (threadIdx.x == 0) {
-            p.flags[1] = s_cnt;
-            if (s_cnt == 0) p.flags[3] = it;
-            if (s_err == 1) atomicOr(&p.flags[0], ERR_NOT_SPD);
-            if (s_err == 2) atomicAdd(&p.flags[5], 1);
+        next[rc] = st;
+        if (p.hist && it < HIST_IT) {
+            double* hh = p.hist + ((size_t)it * 2 * P + rc) * 4;
+            hh[0] = gam; hh[1] = del; hh[2] = st.conv ? 0.0 : st.alpha; hh[3] = st.conv ? 0.0 : st.beta;
         }
     }
-    if (s_cnt == 0 && it > 0) return;   // at it == 0 the vectors are initialised in any case
+    double* acc_next = p.acc32 + (size_t)((it + 1) & 1) * 4 * P;
+    for (int q = threadIdx.x; q < 4 * P; q += THREADS) acc_next[q] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        p.flags[1] = s_cnt;
+        if (s_cnt == 0) p.flags[3] = it;
+        if (s_err == 1) atomicOr(&p.flags[0], ERR_NOT_SPD);
+        if (s_err == 2) atomicAdd(&p.flags[5], 1);
+        p.flags[7] = it;            // iteration whose scalars cgs/cgu hold
+    }
+}
+
+// p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s (FP32) with the
+// scalars of k_inner32_scalars.  At it == 0 every vector is initialised.
+__global__ void k_inner32_update(PanelDev p, int it) {
+    const int P = p.P;
+    if (*(volatile int*)&p.flags[7] != it) return;      // the scalar kernel of this iteration did not run
     const int c = threadIdx.x % P;
     if (!p.col[c].active) return;
-    const bool u0 = s_upd[2 * c] != 0, u1 = s_upd[2 * c + 1] != 0;
+    const bool u0 = p.cgu[2 * c] != 0, u1 = p.cgu[2 * c + 1] != 0;
     if (!u0 && !u1 && it > 0) return;
-    const float a0 = s_alpha[2 * c], a1 = s_alpha[2 * c + 1], b0 = s_beta[2 * c], b1 = s_beta[2 * c + 1];
+    const float a0 = (float)p.cgs[2 * c], a1 = (float)p.cgs[2 * c + 1];
+    const float b0 = (float)p.cgs[2 * P + 2 * c], b1 = (float)p.cgs[2 * P + 2 * c + 1];
     const long long items = (long long)p.npad * P;
     for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
          idx += (long long)gridDim.x * THREADS) {
@@ -1195,6 +1317,10 @@ static int grid_for(long long items) {
     return (int)(g < 1 ? 1 : (g > gm ? gm : g));
 }
 
+void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_split_f64<<<grid_for(n), THREADS, 0, st>>>(v, hi, lo, n);
+}
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st) {
     {
         LaunchScope ls_(K_OTHER, st);
@@ -1210,7 +1336,10 @@ void launch_panel_init(const DevSystem&, const PanelDev& p, cudaStream_t st) {
 void launch_outer_spmm(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     {
         LaunchScope ls_(K_OUTER_SPMM, st);
-        k_outer_spmm<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+        if (p.mixed)
+            k_outer_spmm<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+        else
+            k_outer_spmm<false><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
     }
 }
 void launch_outer_update(const DevSystem&, const PanelDev& p, cudaStream_t st) {
@@ -1243,11 +1372,15 @@ void launch_refine_start(const DevSystem&, const PanelDev& p, const double2* b, 
 }
 void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_RESIDUAL, st);
-    k_refine_residual<<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
+    k_refine_residual<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
 }
 void launch_refine_scale(const DevSystem&, const PanelDev& p, const double2* src, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_AUX, st);
     k_refine_scale<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, src);
+}
+void launch_split_panel(const PanelDev& p, cudaStream_t st) {
+    LaunchScope ls_(K_REFINE_AUX, st);
+    k_split_panel<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
 }
 void launch_refine_add(const DevSystem&, const PanelDev& p, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_AUX, st);
@@ -1261,6 +1394,10 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
 }
 void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
+    {
+        LaunchScope ls_(K_INNER32_UPDATE, st);
+        k_inner32_scalars<<<1, THREADS, 0, st>>>(p, it);
+    }
     LaunchScope ls_(K_INNER32_UPDATE, st);
     k_inner32_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
 }

@@ -72,6 +72,7 @@ class Stats(C.Structure):
         ("switches", C.c_int32),
         ("unconverged", C.c_int32),
         ("seconds", C.c_double),
+        ("inner_redos", C.c_int32),
     ]
 
 
@@ -240,6 +241,7 @@ def _stats_dict(st: Stats, conv, R, K, status):
     return {"status": _STATUS.get(status, status), "outer_iterations": st.outer_iterations,
             "inner_iterations": st.inner_iterations, "max_column_iterations": st.max_column_iterations,
             "switches": st.switches, "unconverged": st.unconverged, "seconds": st.seconds,
+            "inner_redos": st.inner_redos,
             "conv_iter": None if conv is None else conv.reshape(R, K)}
 
 
