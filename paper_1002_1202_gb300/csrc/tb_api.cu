@@ -528,6 +528,51 @@ tb_status out_finish(const OutBuf& ob, cudaStream_t st) {
 
 tb_status merge(tb_status run, tb_status fin) { return run != TB_OK && run != TB_ERR_NOT_CONVERGED ? run : (fin != TB_OK ? fin : run); }
 
+// Groups of consecutive atoms for the grouped FP32 SpMV: for each group the
+// ascending list of its distinct block columns and, per block, the position
+// of its column in that list.  G is the largest of 16, 8, 4, 2 whose shared
+// memory (neighbour-union panel rows of a 32-column slice plus the group's
+// S blocks) lets two CTAs share an SM; TB_SPMV_GROUP=G overrides the choice
+// (0 turns the grouped SpMV off).
+struct SpmvGroups {
+    int G = 0, n_groups = 0, max_union = 0, max_gblocks = 0;
+    std::vector<int> ptr, cols, loc;
+};
+
+SpmvGroups build_spmv_groups(const std::vector<int>& brow, const std::vector<int>& bcol, int n) {
+    const size_t budget = 113 * 1024;
+    int forced = -1;
+    if (const char* env = std::getenv("TB_SPMV_GROUP")) forced = std::atoi(env);
+    SpmvGroups out;
+    if (forced == 0) return out;
+    for (int G : {16, 8, 4, 2}) {
+        if (forced > 0 && G != forced) continue;
+        SpmvGroups g;
+        g.G = G;
+        g.n_groups = (n + G - 1) / G;
+        g.ptr.assign(g.n_groups + 1, 0);
+        g.loc.assign(bcol.size(), 0);
+        std::vector<int> u;
+        for (int q = 0; q < g.n_groups; ++q) {
+            const int a0 = q * G, a1 = std::min(n, a0 + G);
+            u.assign(bcol.begin() + brow[a0], bcol.begin() + brow[a1]);
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            for (int b = brow[a0]; b < brow[a1]; ++b)
+                g.loc[b] = (int)(std::lower_bound(u.begin(), u.end(), bcol[b]) - u.begin());
+            g.cols.insert(g.cols.end(), u.begin(), u.end());
+            g.ptr[q + 1] = (int)g.cols.size();
+            g.max_union = std::max(g.max_union, (int)u.size());
+            g.max_gblocks = std::max(g.max_gblocks, brow[a1] - brow[a0]);
+        }
+        const size_t xregion = (size_t)g.max_union * 4 * 32 * 8;
+        const size_t red = (size_t)(G / 2) * 16 * 8 * 8;
+        const size_t smem = 128 + std::max(xregion, red) + (size_t)g.max_gblocks * 64;
+        if (smem <= budget || (forced > 0 && smem <= 227 * 1024)) return g;
+    }
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -587,6 +632,9 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->ds.S32lo);
     cudaFree(h->ds.H32hi);
     cudaFree(h->ds.H32lo);
+    cudaFree(h->ds.grp_ptr);
+    cudaFree(h->ds.grp_cols);
+    cudaFree(h->ds.blk_loc);
     cudaFree(h->orb2pad);
     cudaFree(h->eps_pad);
     if (h->flags_host) cudaFreeHost(h->flags_host);
@@ -730,6 +778,23 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     if ((e = cudaMemcpyAsync(h->ds.brow, browh.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.bcol, bcolh.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.S, Sp.data(), sizeof(double) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    {
+        const SpmvGroups g = build_spmv_groups(browh, bcolh, n);
+        if (g.G > 0) {
+            if ((e = cudaMalloc(&h->ds.grp_ptr, sizeof(int) * g.ptr.size())) != cudaSuccess) return fail(e);
+            if ((e = cudaMalloc(&h->ds.grp_cols, sizeof(int) * std::max<size_t>(1, g.cols.size()))) != cudaSuccess) return fail(e);
+            if ((e = cudaMalloc(&h->ds.blk_loc, sizeof(int) * nb)) != cudaSuccess) return fail(e);
+            if ((e = cudaMemcpyAsync(h->ds.grp_ptr, g.ptr.data(), sizeof(int) * g.ptr.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+            if ((e = cudaMemcpyAsync(h->ds.grp_cols, g.cols.data(), sizeof(int) * g.cols.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+            if ((e = cudaMemcpyAsync(h->ds.blk_loc, g.loc.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+            // the host vectors are released at scope exit: wait for the copies
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+            h->ds.grpG = g.G;
+            h->ds.n_groups = g.n_groups;
+            h->ds.max_union = g.max_union;
+            h->ds.max_gblocks = g.max_gblocks;
+        }
+    }
 
     if ((e = cudaMemcpyAsync(h->orb2pad, o2p.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->eps_pad, epsp.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);

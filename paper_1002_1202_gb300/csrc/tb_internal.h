@@ -41,7 +41,16 @@ struct DevSystem {
     float* S32lo = nullptr;    // [nb][16] S - S_hi in FP32
     float* H32hi = nullptr;    // [nb][16] H rounded to FP32
     float* H32lo = nullptr;    // [nb][16] H - H_hi in FP32
+    // atom groups of the grouped FP32 SpMV: group g = atoms [g * grpG, (g + 1) * grpG)
+    int grpG = 0;              // atoms per group; 0: grouped SpMV not used
+    int n_groups = 0;
+    int max_union = 0;         // largest number of distinct block columns of a group
+    int max_gblocks = 0;       // largest number of blocks of a group
+    int* grp_ptr = nullptr;    // [n_groups + 1] offsets into grp_cols
+    int* grp_cols = nullptr;   // distinct block-column atoms of each group, ascending
+    int* blk_loc = nullptr;    // [nb] position of bcol[b] in the list of its group
 };
+size_t inner32_grp_smem(const DevSystem& s);   // dynamic shared memory of the grouped SpMV
 
 // Per right-hand side (complex column) state of a panel.
 struct ColState {

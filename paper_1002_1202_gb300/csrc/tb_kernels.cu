@@ -16,6 +16,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 namespace tb {
@@ -657,6 +659,21 @@ __global__ void k_refine_add(PanelDev p) {
 //   inner32[4P .. 6P)       CG state slot 1
 //   acc32[(slot*4 + q)*P + c]  gamma_re, gamma_im, delta_re, delta_im of column c
 
+// Packed FP32 FMA of Blackwell (two lanes per instruction): d = a * b + c
+// elementwise on float2.  The block products below broadcast one S entry
+// into both lanes, so one instruction updates the real and imaginary parts
+// of one complex column.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long ra, rb, rc, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+
 // w = S r (FP32) and the sums gamma = r.r, delta = w.r of every real column.
 // CPT complex columns per thread (2: one float4 per orbital row), P / CPT
 // threads per block row; the block-column index of the next block is loaded
@@ -757,6 +774,155 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_spmv(DevSystem s, PanelD
         }
     }
 }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+// Grouped form: CTA (g, slice) computes the 4G rows of the G consecutive
+// atoms of group g for the PC complex columns of one panel slice.  The panel
+// rows of the distinct block columns of the group (its neighbour union, built
+// on the host when the system is created) and the group's FP32 S blocks are
+// staged once in shared memory by 16-byte asynchronous copies; every block
+// product then reads shared memory.  The union of 16 neighbouring atoms is
+// ~3x smaller than the sum of their neighbour lists, so the L2 -> SM gather
+// traffic drops by that factor.  PC / 2 threads per atom, two complex
+// columns each; the block products pair (S[a][e], S[a][e+1]), two adjacent
+// lanes of a loaded S row, against (x[e][q], x[e+1][q]) in packed FP32 FMAs.
+constexpr int PC = 32;
+constexpr int GRP_HDR = 128;   // reserved head of the dynamic shared memory
+
+__global__ void __launch_bounds__(256) k_inner32_spmv_grp(DevSystem s, PanelDev p, int it) {
+    extern __shared__ __align__(128) unsigned char gsm[];
+    if (*(volatile int*)&p.flags[1] == 0) return;
+    const int P = p.P;
+    const int nslices = P / PC;
+    const int g = blockIdx.x / nslices;
+    const int slice = blockIdx.x - g * nslices;
+    const int a0 = g * s.grpG;
+    const int a1 = min(a0 + s.grpG, s.n_atoms);
+    const int u0 = s.grp_ptr[g];
+    const int U = s.grp_ptr[g + 1] - u0;
+    const int bb0 = s.brow[a0];
+    const int nbk = s.brow[a1] - bb0;
+    constexpr int TPA = PC / 2;
+    const int t = threadIdx.x;
+    const int I = a0 + t / TPA;
+    const int tc = t % TPA;
+    const int c0 = slice * PC + 2 * tc;
+    const InnerState* base = p.inner32;
+    const InnerState* cgp = p.inner32 + (size_t)(1 + (it & 1)) * 2 * P;
+    bool live = false;
+    if (I < a1) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int c = c0 + j;
+            live |= p.col[c].active && (it == 0 ? !(base[2 * c].skip && base[2 * c + 1].skip)
+                                                : !(cgp[2 * c].conv && cgp[2 * c + 1].conv));
+        }
+    }
+    if (!__syncthreads_or(live)) return;
+    const size_t xregion = (size_t)s.max_union * 4 * PC * sizeof(float2);
+    const size_t red_bytes = (size_t)(blockDim.x / 32) * TPA * 8 * sizeof(double);
+    float4* xs = reinterpret_cast<float4*>(gsm + GRP_HDR);                       // [U][4][PC/2]
+    double* red = reinterpret_cast<double*>(gsm + GRP_HDR);                      // aliases xs after use
+    const float4* ss = reinterpret_cast<const float4*>(gsm + GRP_HDR + (xregion > red_bytes ? xregion : red_bytes));
+    // stage the union's panel rows (16 float4 per row of the slice) and the
+    // group's S blocks with 16-byte asynchronous copies by every thread
+    {
+        const int nx = U * 4 * TPA;               // float4 of the union rows
+        const uint32_t xs_a = smem_u32(xs);
+        for (int k = t; k < nx; k += blockDim.x) {
+            const int row = k / TPA, q4 = k - row * TPA;
+            const int J = __ldg(s.grp_cols + u0 + row / 4);
+            const float2* src = p.r32 + (size_t)(4 * J + (row & 3)) * P + slice * PC + 2 * q4;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(xs_a + 16u * (uint32_t)k), "l"(src));
+        }
+        const uint32_t ss_a = smem_u32(ss);
+        const float4* sg = reinterpret_cast<const float4*>(s.S32 + 16 * (size_t)bb0);
+        for (int k = t; k < nbk * 4; k += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ss_a + 16u * (uint32_t)k), "l"(sg + k));
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    float v32[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v32[q] = 0.f;
+    if (live) {
+        float2 acc2[4][4];   // (even e, odd e) partial sums of row a, value q
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc2[a][q] = make_float2(0.f, 0.f);
+        const int b0 = s.brow[I], b1 = s.brow[I + 1];
+        int jn = __ldg(s.blk_loc + b0);
+        for (int bb = b0; bb < b1; ++bb) {
+            const int j = jn;
+            if (bb + 1 < b1) jn = __ldg(s.blk_loc + bb + 1);
+            const float4* xj = xs + (size_t)j * 4 * TPA + tc;
+            float xv[4][4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 q4 = xj[e * TPA];
+                xv[e][0] = q4.x; xv[e][1] = q4.y; xv[e][2] = q4.z; xv[e][3] = q4.w;
+            }
+            float2 xp[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) xp[h][q] = make_float2(xv[2 * h][q], xv[2 * h + 1][q]);
+            const float4* Sb = ss + (size_t)(bb - bb0) * 4;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float4 sr = Sb[a];
+                const float2 s01 = make_float2(sr.x, sr.y), s23 = make_float2(sr.z, sr.w);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc2[a][q] = ffma2(s01, xp[0][q], acc2[a][q]);
+                    acc2[a][q] = ffma2(s23, xp[1][q], acc2[a][q]);
+                }
+            }
+        }
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = acc2[a][q].x + acc2[a][q].y;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const size_t e = (size_t)(4 * I + a) * P + c0;
+            const float4 r4 = *reinterpret_cast<const float4*>(p.r32 + e);
+            *reinterpret_cast<float4*>(p.w32 + e) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+            const float r[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                v32[4 * j + 0] += r[2 * j] * r[2 * j];
+                v32[4 * j + 1] += r[2 * j + 1] * r[2 * j + 1];
+                v32[4 * j + 2] += acc[a][2 * j] * r[2 * j];
+                v32[4 * j + 3] += acc[a][2 * j + 1] * r[2 * j + 1];
+            }
+        }
+    }
+    // sums over the atoms of the CTA: the two atoms of a warp by shuffle, the
+    // warps through shared memory, then one atomic per column and sum
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (double)v32[q] + __shfl_xor_sync(0xffffffffu, (double)v32[q], TPA);
+    __syncthreads();   // all reads of the staged panel rows are done; red aliases them
+    const int warp = t / 32, lane = t % 32;
+    if (lane < TPA)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[((size_t)warp * TPA + lane) * 8 + q] = v[q];
+    __syncthreads();
+    for (int k = t; k < TPA * 8; k += blockDim.x) {
+        const int tcol = k % TPA, q = k / TPA;      // q = 4 * j + component
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) sum += red[((size_t)w * TPA + tcol) * 8 + q];
+        const int c = slice * PC + 2 * tcol + q / 4;
+        if (sum != 0.0) atomicAdd(p.acc32 + (size_t)(it & 1) * 4 * P + (size_t)(q % 4) * P + c, sum);
+    }
+}
+
 
 // CG scalars of iteration it, once, in one CTA: FP64 alpha, beta and the
 // convergence of every real column from the accumulated sums; the update
@@ -1386,9 +1552,27 @@ void launch_refine_add(const DevSystem&, const PanelDev& p, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_AUX, st);
     k_refine_add<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
 }
+size_t inner32_grp_smem(const DevSystem& s) {
+    const size_t xregion = (size_t)s.max_union * 4 * PC * sizeof(float2);
+    const size_t red_bytes = (size_t)(s.grpG * PC / 2 / 32) * (PC / 2) * 8 * sizeof(double);
+    return GRP_HDR + (xregion > red_bytes ? xregion : red_bytes) + (size_t)s.max_gblocks * 64;
+}
+
 void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st) {
     LaunchScope ls_(K_INNER32_SPMV, st);
-    if (p.P >= 2)
+    // the grouped form wins on narrow panels (measured on the Si 4096-atom
+    // system: 28 vs 35 us at 64 columns); from 128 columns on, the
+    // register-gather form with its higher occupancy is faster
+    if (s.grpG > 0 && p.P >= PC && p.P <= 64) {
+        const size_t sm = inner32_grp_smem(s);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            attr = true;
+        }
+        k_inner32_spmv_grp<<<s.n_groups * (p.P / PC), s.grpG * (PC / 2), sm, st>>>(s, p, it);
+    } else if (p.P >= 2)
         k_inner32_spmv<2><<<grid_for((long long)s.n_atoms * (p.P / 2)), THREADS, 0, st>>>(s, p, it);
     else
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);

@@ -308,3 +308,42 @@ def test_mixed_inner_tolerances(P, c1, h1):
             P.tb_shifted_cocg(h1, z[:2], [0], opts=P.tb_default_opts(precision=1, inner_lo_tol=bad))
     with pytest.raises(P.TBError):
         P.tb_shifted_cocg(h1, z[:2], [0], opts=P.tb_default_opts(precision=2))
+
+
+@pytest.mark.parametrize("group", ["0", "2", "16"], ids=["gather", "group2", "group16"])
+def test_mixed_spmv_forms(P, c1, monkeypatch, group):
+    """The FP32 inner SpMV of TB_MIXED in its register-gather form (no atom
+    groups) and its grouped shared-memory form (groups of 2 and 16 atoms,
+    40 columns: a 64-column panel, two 32-column slices, ragged tail) give
+    the oracle's fixed-iteration iterates and fully converged solutions."""
+    s, H, S, z, w, cols = c1
+    monkeypatch.setenv("TB_SPMV_GROUP", group)
+    h = P.tb_create_system(s)
+    monkeypatch.delenv("TB_SPMV_GROUP")
+    many = choose_columns(256, 40, seed=5)
+    n = 25
+    opts = P.tb_default_opts(max_iter=n, precision=1)
+    x, st = P.tb_shifted_cocg(h, z[::4], many, opts=opts, allow_unconverged=True)
+    X = x.cpu().numpy()
+    for c in (0, 17, 39):
+        ref = method.generalized_shifted_cocg(H, S, z[::4], int(many[c]), max_iter=n)["x"]
+        assert np.abs(X[:, c] - ref).max() <= 1e-9 * np.abs(ref).max()
+    x, st = P.tb_shifted_cocg(h, z[::4], many, opts=P.tb_default_opts(precision=1))
+    assert st["status"] == "TB_OK"
+    assert _true_rel_res(H, S, z[::4], x.cpu().numpy(), many).max() <= 1e-8
+
+
+def test_mixed_spmv_grouped_water(P, monkeypatch):
+    """Grouped FP32 SpMV on ragged blocks (O: 4 orbitals, H: 1) with a
+    partial last group: converged Mulliken populations of 36 columns."""
+    s = water_system(32, seed=4)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(8, -35.0, 5.0, 0.05)
+    cols = list(range(0, s.n_orb, max(1, s.n_orb // 36)))[:36]
+    monkeypatch.setenv("TB_SPMV_GROUP", "16")
+    h = P.tb_create_system(s)
+    monkeypatch.delenv("TB_SPMV_GROUP")
+    q, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1))
+    ref = dense.mulliken_orbital(H, S, z, w, 2.0)[cols]
+    assert np.abs(q.cpu().numpy() - ref).max() <= 1e-6
