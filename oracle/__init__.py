@@ -20,4 +20,8 @@ method  The method in the paper's order and notation: the generalized
         collinear residuals and seed switching (Section 3.3, Eqs. CGp:p,
         CGp:x, CGp:r, shift:pi, collinear), the inner CG for S^-1 r, and the
         generalized Lanczos process (Section 3.2, Eqs. 1.13, 1.18).
+csc     Charge self-consistency (Section 2.2, Eq. Hap-CSC): the potential
+        V = gamma dq, the correction 1/2 S (V_i + V_j), the second-order
+        energy it derives from, and a linear-mixing loop over dense
+        Mulliken populations.
 """
