@@ -183,6 +183,69 @@ tb_status tb_mulliken_orbital(tb_handle *h, int32_t K, const double *z, const do
 tb_status tb_mulliken_charges(tb_handle *h, int32_t K, const double *z, const double *w, double g_s,
                               const tb_solve_opts *opts, double *q_out, tb_stats *stats, void *stream);
 
+/* ---- charge self-consistency (Section 2.2, Eq. Hap-CSC) ------------------
+ *
+ * The charge-transfer term of the Hamiltonian,
+ *     H^CSC_{ia,jb} = 1/2 S_{ia,jb} sum_k (gamma_ik + gamma_jk) dq_k
+ *                   = 1/2 S_{ia,jb} (V_i + V_j),   V = gamma dq,
+ * with dq_k the deviation of the Mulliken population of atom k from a
+ * reference and gamma the atom-atom Coulomb interaction (chemical hardness
+ * on the diagonal).  The paper fixes neither gamma nor the iteration that
+ * makes the charges self-consistent: gamma is the caller's dense matrix and
+ * the iteration is linear mixing of dq.  The handle keeps the Hamiltonian
+ * it was created with (H0: explicit or ASED, Eq. Hap-1); these calls
+ * replace the Hamiltonian that every solve uses by H0 + H^CSC(dq).
+ */
+typedef struct {
+    int32_t max_scf;   /* SCF iterations, >= 1; default 50                          */
+    double scf_tol;    /* stop when max_i |dq_out_i - dq_in_i| <= scf_tol (electrons),
+                          > 0; default 1e-6                                         */
+    double mix;        /* dq_in <- dq_in + mix (dq_out - dq_in), 0 < mix <= 1;
+                          default 0.3                                               */
+} tb_csc_opts;
+
+/* Fill *opts with the defaults listed above. */
+void tb_default_csc_opts(tb_csc_opts *opts);
+
+typedef struct {
+    int32_t iterations;        /* SCF iterations run                                */
+    double residual;           /* max_i |dq_out_i - dq_in_i| of the last iteration  */
+    int64_t outer_iterations;  /* COCG outer steps summed over all SCF iterations   */
+    int64_t inner_iterations;  /* inner CG iterations summed likewise               */
+    double seconds;            /* wall time of the loop                             */
+} tb_csc_stats;
+
+/*
+ * Set the handle's Hamiltonian to H0 + H^CSC(dq): V = gamma dq on the device,
+ * then every stored block H_IJ = H0_IJ + 1/2 S_IJ (V_I + V_J) (and its FP32
+ * split for TB_MIXED).  gamma: double [n_atoms][n_atoms] row-major; dq:
+ * double [n_atoms]; either may be host or device memory.  dq == NULL
+ * restores H0 (gamma is then ignored).  Synchronous on the stream.
+ */
+tb_status tb_csc_hamiltonian(tb_handle *h, const double *gamma, const double *dq, void *stream);
+
+/*
+ * Self-consistent Mulliken charges by linear mixing.  Iteration m sets
+ * H = H0 + H^CSC(dq_in) (dq_in = dq_init, or 0 when dq_init is NULL, at
+ * m = 1), computes the atomic populations q as tb_mulliken_charges does
+ * (quadrature z, w; spin factor g_s; solver options opts), dq_out = q - q_ref
+ * and res = max_i |dq_out_i - dq_in_i|; it stops when res <= scf_tol or
+ * m = max_scf, else dq_in <- dq_in + mix (dq_out - dq_in).  Every step runs
+ * on the device; the host reads one number (res) per iteration.
+ * Inputs gamma [n_atoms][n_atoms], q_ref [n_atoms], dq_init [n_atoms]
+ * (optional): host or device.  Outputs q_out, dq_out [n_atoms], host or
+ * device: the populations of the last iteration and the dq_in that produced
+ * them; on return the handle's Hamiltonian is H0 + H^CSC(dq_out).
+ * Returns TB_OK when res <= scf_tol, TB_ERR_NOT_CONVERGED when max_scf ran
+ * out or a COCG solve did not converge (outputs still written),
+ * TB_ERR_BREAKDOWN on a non-finite residual, TB_ERR_INVALID_ARG for bad
+ * options, and the errors of tb_mulliken_charges.
+ */
+tb_status tb_csc_loop(tb_handle *h, int32_t K, const double *z, const double *w, double g_s,
+                      const double *gamma, const double *q_ref, const double *dq_init,
+                      const tb_csc_opts *copts, const tb_solve_opts *opts, double *q_out, double *dq_out,
+                      tb_csc_stats *stats, void *stream);
+
 /*
  * Generalized Lanczos process (Section 3.2, Eqs. 1.13 and 1.18) for the
  * operator S^-1 H with the S-product, started from u^0 = S^-1 e_j normalised
@@ -251,7 +314,9 @@ enum {
     TB_K_INNER32_UPDATE = 9, /* TB_MIXED: FP32 CG vector updates           */
     TB_K_REFINE_RESIDUAL = 10, /* TB_MIXED: FP64 residual r - S r'         */
     TB_K_REFINE_AUX = 11,  /* TB_MIXED: refinement start and correction add */
-    TB_K_COUNT = 12
+    TB_K_CSC = 12,         /* charge self-consistency: potential, Hamiltonian
+                              update, atom sums, mixing                        */
+    TB_K_COUNT = 13
 };
 int64_t tb_launch_count(void);
 void tb_profile_enable(int32_t enable);

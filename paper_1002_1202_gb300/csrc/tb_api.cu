@@ -34,6 +34,9 @@ struct tb_handle {
     int32_t* orb2pad = nullptr;       // device copy
     double* eps_pad = nullptr;
     int* flags_host = nullptr;        // pinned, NFLAGS ints
+    int64_t* atom_orb_off = nullptr;  // device [n_atoms + 1]: first caller orbital of every atom
+    double* H0 = nullptr;             // device [nb][16]: the Hamiltonian of tb_create, kept once
+                                      // the charge-self-consistent term first replaces H
 };
 
 namespace {
@@ -575,6 +578,71 @@ SpmvGroups build_spmv_groups(const std::vector<int>& brow, const std::vector<int
 
 }  // namespace
 
+namespace {
+
+// Keep the Hamiltonian of tb_create before the first charge-dependent one
+// replaces it.
+tb_status ensure_H0(tb_handle* h, cudaStream_t st) {
+    if (h->H0) return TB_OK;
+    const size_t bytes = sizeof(double) * 16 * (size_t)h->ds.nb;
+    cudaError_t e = cudaMalloc(&h->H0, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->H0 = nullptr;
+        return e == cudaErrorMemoryAllocation ? TB_ERR_OOM : TB_ERR_CUDA;
+    }
+    TB_CK(cudaMemcpyAsync(h->H0, h->ds.H, bytes, cudaMemcpyDeviceToDevice, st));
+    return TB_OK;
+}
+
+// A device copy of a host-or-device array (device arrays are used in place).
+template <class T>
+tb_status device_view(Cleanup& cl, const T* src, size_t count, const T** out, cudaStream_t st) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return TB_OK;
+    }
+    T* d = nullptr;
+    tb_status s = dalloc(cl, &d, count);
+    if (s != TB_OK) return s;
+    TB_CK(cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, st));
+    *out = d;
+    return TB_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Atomic populations of every atom into the device array q_atom: all N
+// orbitals solved (PROJ_SROW) into a device buffer, then summed per atom on
+// the device.
+tb_status mulliken_atoms_device(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,
+                                const tb_solve_opts* opts, double* q_atom, tb_stats* stats, cudaStream_t st) {
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    if (!w || !std::isfinite(g_s)) return TB_ERR_INVALID_ARG;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(w[k])) return TB_ERR_INVALID_ARG;
+    std::vector<int32_t> cols(h->n_orb);
+    for (int64_t o = 0; o < h->n_orb; ++o) cols[o] = (int32_t)o;
+    Cleanup cl;
+    cl.st = st;
+    double* q_orb = nullptr;
+    if ((s = dalloc(cl, &q_orb, (size_t)h->n_orb)) != TB_OK) return s;
+    Solve q;
+    q.K = K; q.z = z; q.R = (int)h->n_orb; q.cols = cols.data(); q.proj = PROJ_SROW; q.w = w; q.g_s = g_s;
+    q.q_out = q_orb;
+    const tb_status run = run_solve(h, q, opts, stats, st);
+    if (run != TB_OK && run != TB_ERR_NOT_CONVERGED) return run;
+    launch_atom_sum(q_orb, h->atom_orb_off, h->n_atoms, q_atom, st);
+    TB_CK(cudaGetLastError());
+    return run;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* tb_status_string(tb_status s) {
@@ -637,6 +705,8 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->ds.blk_loc);
     cudaFree(h->orb2pad);
     cudaFree(h->eps_pad);
+    cudaFree(h->atom_orb_off);
+    cudaFree(h->H0);
     if (h->flags_host) cudaFreeHost(h->flags_host);
     delete h;
     return TB_OK;
@@ -775,6 +845,8 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     if ((e = cudaMalloc(&h->orb2pad, sizeof(int32_t) * N)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->eps_pad, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&h->flags_host, NFLAGS * sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->atom_orb_off, sizeof(int64_t) * (n + 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->atom_orb_off, ooff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.brow, browh.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.bcol, bcolh.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->ds.S, Sp.data(), sizeof(double) * 16 * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
@@ -881,27 +953,126 @@ tb_status tb_mulliken_orbital(tb_handle* h, int32_t K, const double* z, const do
     return merge(run, out_finish(ob, st));
 }
 
+
 tb_status tb_mulliken_charges(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,
                               const tb_solve_opts* opts, double* q_out, tb_stats* stats, void* stream) {
     if (!h || !q_out) return TB_ERR_INVALID_ARG;
-    std::vector<int32_t> cols(h->n_orb);
-    for (int64_t o = 0; o < h->n_orb; ++o) cols[o] = (int32_t)o;
-    std::vector<double> qo(h->n_orb);
-    const tb_status run = tb_mulliken_orbital(h, K, z, w, g_s, (int32_t)h->n_orb, cols.data(), opts, qo.data(),
-                                              stats, stream);
-    if (run != TB_OK && run != TB_ERR_NOT_CONVERGED) return run;
-    std::vector<double> qa(h->n_atoms, 0.0);
-    int64_t o = 0;
-    for (int i = 0; i < h->n_atoms; ++i)
-        for (int a = 0; a < h->orb_per_atom[i]; ++a) qa[i] += qo[o++];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (is_device_ptr(q_out)) {
-        TB_CK(cudaMemcpyAsync(q_out, qa.data(), sizeof(double) * h->n_atoms, cudaMemcpyHostToDevice, st));
+    Cleanup cl;
+    cl.st = st;
+    OutBuf ob;
+    tb_status s;
+    if ((s = out_prepare(cl, ob, q_out, sizeof(double) * (size_t)h->n_atoms)) != TB_OK) return s;
+    const tb_status run = mulliken_atoms_device(h, K, z, w, g_s, opts, static_cast<double*>(ob.dev), stats, st);
+    if (run != TB_OK && run != TB_ERR_NOT_CONVERGED) return run;
+    return merge(run, out_finish(ob, st));
+}
+
+// ---- charge self-consistency (Eq. Hap-CSC) ---------------------------------
+
+void tb_default_csc_opts(tb_csc_opts* o) {
+    if (!o) return;
+    o->max_scf = 50;
+    o->scf_tol = 1e-6;
+    o->mix = 0.3;
+}
+
+
+tb_status tb_csc_hamiltonian(tb_handle* h, const double* gamma, const double* dq, void* stream) {
+    if (!h) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!dq) {
+        if (h->H0) {
+            TB_CK(cudaMemcpyAsync(h->ds.H, h->H0, sizeof(double) * 16 * (size_t)h->ds.nb, cudaMemcpyDeviceToDevice, st));
+            launch_split_f64(h->ds.H, h->ds.H32hi, h->ds.H32lo, 16 * (long long)h->ds.nb, st);
+            TB_CK(cudaGetLastError());
+        }
         TB_CK(cudaStreamSynchronize(st));
-    } else {
-        std::memcpy(q_out, qa.data(), sizeof(double) * h->n_atoms);
+        return TB_OK;
     }
-    return run;
+    if (!gamma) return TB_ERR_INVALID_ARG;
+    tb_status s;
+    if ((s = ensure_H0(h, st)) != TB_OK) return s;
+    Cleanup cl;
+    cl.st = st;
+    const int n = h->n_atoms;
+    const double *gd = nullptr, *dqd = nullptr;
+    double* V = nullptr;
+    if ((s = device_view(cl, gamma, (size_t)n * n, &gd, st)) != TB_OK) return s;
+    if ((s = device_view(cl, dq, (size_t)n, &dqd, st)) != TB_OK) return s;
+    if ((s = dalloc(cl, &V, (size_t)n)) != TB_OK) return s;
+    launch_csc_potential(gd, dqd, n, V, st);
+    launch_csc_hamiltonian(h->ds, h->H0, V, st);
+    TB_CK(cudaGetLastError());
+    TB_CK(cudaStreamSynchronize(st));
+    return TB_OK;
+}
+
+tb_status tb_csc_loop(tb_handle* h, int32_t K, const double* z, const double* w, double g_s, const double* gamma,
+                      const double* q_ref, const double* dq_init, const tb_csc_opts* copts,
+                      const tb_solve_opts* opts, double* q_out, double* dq_out, tb_csc_stats* stats,
+                      void* stream) {
+    if (!h || !gamma || !q_ref || !copts || !q_out || !dq_out) return TB_ERR_INVALID_ARG;
+    if (copts->max_scf < 1 || !(copts->scf_tol > 0.0) || !(copts->mix > 0.0 && copts->mix <= 1.0))
+        return TB_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    if (!w || !std::isfinite(g_s)) return TB_ERR_INVALID_ARG;
+    if ((s = ensure_H0(h, st)) != TB_OK) return s;
+    Cleanup cl;
+    cl.st = st;
+    const int n = h->n_atoms;
+    const double *gd = nullptr, *qrd = nullptr;
+    if ((s = device_view(cl, gamma, (size_t)n * n, &gd, st)) != TB_OK) return s;
+    if ((s = device_view(cl, q_ref, (size_t)n, &qrd, st)) != TB_OK) return s;
+    double *dq_in, *dq_next, *V, *q;
+    unsigned long long* res_bits;
+    if ((s = dalloc(cl, &dq_in, (size_t)n)) != TB_OK) return s;
+    if ((s = dalloc(cl, &dq_next, (size_t)n)) != TB_OK) return s;
+    if ((s = dalloc(cl, &V, (size_t)n)) != TB_OK) return s;
+    if ((s = dalloc(cl, &q, (size_t)n)) != TB_OK) return s;
+    if ((s = dalloc(cl, &res_bits, 1)) != TB_OK) return s;
+    if (dq_init) {
+        TB_CK(cudaMemcpyAsync(dq_in, dq_init, sizeof(double) * n, cudaMemcpyDefault, st));
+    } else {
+        TB_CK(cudaMemsetAsync(dq_in, 0, sizeof(double) * n, st));
+    }
+    tb_csc_stats cs{};
+    bool cocg_unconverged = false;
+    double res = 0.0;
+    int m = 0;
+    for (m = 1; m <= copts->max_scf; ++m) {
+        launch_csc_potential(gd, dq_in, n, V, st);
+        launch_csc_hamiltonian(h->ds, h->H0, V, st);
+        TB_CK(cudaGetLastError());
+        tb_stats ts{};
+        const tb_status run = mulliken_atoms_device(h, K, z, w, g_s, opts, q, &ts, st);
+        if (run != TB_OK && run != TB_ERR_NOT_CONVERGED) return run;
+        if (run == TB_ERR_NOT_CONVERGED) cocg_unconverged = true;
+        cs.outer_iterations += ts.outer_iterations;
+        cs.inner_iterations += ts.inner_iterations;
+        TB_CK(cudaMemsetAsync(res_bits, 0, sizeof(unsigned long long), st));
+        launch_csc_mix(q, qrd, dq_in, dq_next, copts->mix, n, res_bits, st);
+        TB_CK(cudaGetLastError());
+        unsigned long long bits = 0;
+        TB_CK(cudaMemcpyAsync(&bits, res_bits, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaStreamSynchronize(st));
+        std::memcpy(&res, &bits, sizeof(res));
+        if (!std::isfinite(res)) return TB_ERR_BREAKDOWN;
+        if (res <= copts->scf_tol || m == copts->max_scf) break;
+        std::swap(dq_in, dq_next);
+    }
+    cs.iterations = std::min(m, copts->max_scf);
+    cs.residual = res;
+    TB_CK(cudaMemcpyAsync(dq_out, dq_in, sizeof(double) * n, cudaMemcpyDefault, st));
+    TB_CK(cudaMemcpyAsync(q_out, q, sizeof(double) * n, cudaMemcpyDefault, st));
+    TB_CK(cudaStreamSynchronize(st));
+    cs.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = cs;
+    return (res <= copts->scf_tol && !cocg_unconverged) ? TB_OK : TB_ERR_NOT_CONVERGED;
 }
 
 tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, double inner_tol, double* a,

@@ -124,7 +124,7 @@ struct PanelDev {
 // kernel classes for launch accounting (same order as the TB_K_* constants
 // of the public header)
 enum { K_INNER_SPMV = 0, K_INNER_UPDATE, K_OUTER_SPMM, K_OUTER_UPDATE, K_FINISH, K_SHIFT_STEP,
-       K_FULL_UPDATE, K_OTHER, K_INNER32_SPMV, K_INNER32_UPDATE, K_REFINE_RESIDUAL, K_REFINE_AUX, K_COUNT };
+       K_FULL_UPDATE, K_OTHER, K_INNER32_SPMV, K_INNER32_UPDATE, K_REFINE_RESIDUAL, K_REFINE_AUX, K_CSC, K_COUNT };
 void profile_enable(bool on);
 void prof_harvest();
 void profile_read(int id, int64_t* launches, double* ms);
@@ -155,6 +155,13 @@ void launch_green_output(const PanelDev& p, int ncols, const int64_t* out_off, d
                          cudaStream_t st);
 void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
                             cudaStream_t st);
+
+// charge self-consistency (Eq. Hap-CSC)
+void launch_csc_potential(const double* gamma, const double* dq, int n, double* V, cudaStream_t st);
+void launch_csc_hamiltonian(const DevSystem& s, const double* H0, const double* V, cudaStream_t st);
+void launch_atom_sum(const double* q_orb, const int64_t* orb_off, int n_atoms, double* q_atom, cudaStream_t st);
+void launch_csc_mix(const double* q, const double* q_ref, const double* dq_in, double* dq_next, double mix, int n,
+                    unsigned long long* res_bits, cudaStream_t st);
 
 // generalized Lanczos helpers (single real column carried in a P = 1 panel)
 void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, cudaStream_t st);

@@ -1390,6 +1390,90 @@ __global__ void k_lz_scale(PanelDev p, const double2* __restrict__ w, double2* _
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Charge self-consistency (Section 2.2, Eq. Hap-CSC)
+// ---------------------------------------------------------------------------
+
+// V_i = sum_k gamma_ik dq_k: one warp per row of gamma (coalesced), lanes
+// add strided terms, then a fixed-order shuffle tree.
+__global__ void k_csc_potential(const double* __restrict__ gamma, const double* __restrict__ dq, int n,
+                                double* __restrict__ V) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < n; i += nwarps) {
+        const double* row = gamma + i * (long long)n;
+        double acc = 0.0;
+        for (int k = lane; k < n; k += 32) acc = fma(row[k], dq[k], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) V[i] = acc;
+    }
+}
+
+// H_IJ = H0_IJ + 1/2 S_IJ (V_I + V_J) for every stored block, with the FP32
+// split (hi, lo) of the new H for the double-float products of the mixed
+// path.  One warp per block row: the row's blocks are contiguous.  Padded
+// orbital slots have S = 1 on the diagonal and no coupling; they only get
+// V_I on their (decoupled) diagonal.
+__global__ void k_csc_hamiltonian(DevSystem s, const double* __restrict__ H0, const double* __restrict__ V) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long I = warp; I < s.n_atoms; I += nwarps) {
+        const double vI = V[I];
+        const long long e0 = 16LL * s.brow[I], e1 = 16LL * s.brow[I + 1];
+        for (long long e = e0 + lane; e < e1; e += 32) {
+            const int J = s.bcol[e >> 4];
+            const double h = H0[e] + 0.5 * s.S[e] * (vI + V[J]);
+            s.H[e] = h;
+            const float hi = (float)h;
+            s.H32hi[e] = hi;
+            s.H32lo[e] = (float)(h - (double)hi);
+        }
+    }
+}
+
+// q_atom[i] = sum of q_orb over the orbitals [orb_off[i], orb_off[i+1]) of atom i
+__global__ void k_atom_sum(const double* __restrict__ q_orb, const int64_t* __restrict__ orb_off, int n_atoms,
+                           double* __restrict__ q_atom) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_atoms;
+         i += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int64_t o = orb_off[i]; o < orb_off[i + 1]; ++o) acc += q_orb[o];
+        q_atom[i] = acc;
+    }
+}
+
+// dq_out = q - q_ref, res = max_i |dq_out_i - dq_in_i| (as the bit pattern of
+// a non-negative double: unsigned order is numeric order, and a NaN compares
+// above +inf), dq_next = dq_in + mix (dq_out - dq_in).
+__global__ void k_csc_mix(const double* __restrict__ q, const double* __restrict__ q_ref,
+                          const double* __restrict__ dq_in, double* __restrict__ dq_next, double mix, int n,
+                          unsigned long long* res_bits) {
+    __shared__ unsigned long long smax[THREADS / 32];
+    unsigned long long m = 0ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double d = (q[i] - q_ref[i]) - dq_in[i];
+        dq_next[i] = dq_in[i] + mix * d;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(d));
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
+        m = other > m ? other : m;
+    }
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = smax[w] > m ? smax[w] : m;
+        atomicMax(res_bits, m);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1663,6 +1747,28 @@ void launch_lz_start(const PanelDev& p, const double2* v, int row, double2* u, d
         LaunchScope ls_(K_OTHER, st);
         k_lz_start<<<grid_for(p.npad), THREADS, 0, st>>>(p, v, row, u, nrm2);
     }
+}
+
+
+void launch_csc_potential(const double* gamma, const double* dq, int n, double* V, cudaStream_t st) {
+    LaunchScope ls_(K_CSC, st);
+    k_csc_potential<<<grid_for((long long)n * 32), THREADS, 0, st>>>(gamma, dq, n, V);
+}
+
+void launch_csc_hamiltonian(const DevSystem& s, const double* H0, const double* V, cudaStream_t st) {
+    LaunchScope ls_(K_CSC, st);
+    k_csc_hamiltonian<<<grid_for((long long)s.n_atoms * 32), THREADS, 0, st>>>(s, H0, V);
+}
+
+void launch_atom_sum(const double* q_orb, const int64_t* orb_off, int n_atoms, double* q_atom, cudaStream_t st) {
+    LaunchScope ls_(K_CSC, st);
+    k_atom_sum<<<grid_for(n_atoms), THREADS, 0, st>>>(q_orb, orb_off, n_atoms, q_atom);
+}
+
+void launch_csc_mix(const double* q, const double* q_ref, const double* dq_in, double* dq_next, double mix, int n,
+                    unsigned long long* res_bits, cudaStream_t st) {
+    LaunchScope ls_(K_CSC, st);
+    k_csc_mix<<<grid_for(n), THREADS, 0, st>>>(q, q_ref, dq_in, dq_next, mix, n, res_bits);
 }
 
 }  // namespace tb

@@ -76,6 +76,24 @@ class Stats(C.Structure):
     ]
 
 
+class CscOpts(C.Structure):
+    _fields_ = [
+        ("max_scf", C.c_int32),
+        ("scf_tol", C.c_double),
+        ("mix", C.c_double),
+    ]
+
+
+class CscStats(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int32),
+        ("residual", C.c_double),
+        ("outer_iterations", C.c_int64),
+        ("inner_iterations", C.c_int64),
+        ("seconds", C.c_double),
+    ]
+
+
 # (name, restype, argtypes) of every entry point declared in include/tbcocg.h
 _VP = C.c_void_p
 _DP = C.POINTER(C.c_double)
@@ -96,6 +114,10 @@ SIGNATURES = [
                                       C.POINTER(SolveOpts), _VP, C.POINTER(Stats), _VP]),
     ("tb_mulliken_charges", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP,
                                       C.POINTER(Stats), _VP]),
+    ("tb_default_csc_opts", None, [C.POINTER(CscOpts)]),
+    ("tb_csc_hamiltonian", C.c_int, [_VP, _VP, _VP, _VP]),
+    ("tb_csc_loop", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, _VP, _VP, C.POINTER(CscOpts),
+                              C.POINTER(SolveOpts), _VP, _VP, C.POINTER(CscStats), _VP]),
     ("tb_generalized_lanczos", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_generalized_lanczos_noalloc", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
@@ -106,7 +128,7 @@ SIGNATURES = [
 
 KERNELS = {"inner_spmv": 0, "inner_update": 1, "outer_spmm": 2, "outer_update": 3, "finish": 4,
            "shift_step": 5, "full_update": 6, "other": 7, "inner32_spmv": 8, "inner32_update": 9,
-           "refine_residual": 10, "refine_aux": 11}
+           "refine_residual": 10, "refine_aux": 11, "csc": 12}
 
 _lib = None
 
@@ -316,6 +338,70 @@ def tb_mulliken_charges(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None,
                                            C.byref(opts), _out_ptr(out), C.byref(st), _stream(stream))
     _check(s, "tb_mulliken_charges", allow_unconverged)
     return out, _stats_dict(st, None, h.n_orb, K, s)
+
+
+def tb_default_csc_opts(**kw) -> CscOpts:
+    """tb_csc_opts with the library defaults, fields overridden by keyword."""
+    o = CscOpts()
+    load_library().tb_default_csc_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _in_ptr(a, n: int, keep: list):
+    """Pointer to n doubles: a CUDA tensor in place, anything else as a
+    contiguous float64 host copy (kept alive in ``keep``)."""
+    if a is None:
+        return C.c_void_p(0)
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        if a.dtype.itemsize != 8 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError("expected a contiguous float64 CUDA tensor of %d elements" % n)
+        return C.c_void_p(a.data_ptr())
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if arr.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, arr.size))
+    keep.append(arr)
+    return C.c_void_p(arr.ctypes.data)
+
+
+def tb_csc_hamiltonian(h: Handle, gamma, dq, stream=None) -> None:
+    """Set the handle's Hamiltonian to H0 + H^CSC(dq) (dq None: back to H0)."""
+    keep = []
+    n = h.n_atoms
+    g = _in_ptr(gamma, n * n, keep) if dq is not None else C.c_void_p(0)
+    s = load_library().tb_csc_hamiltonian(h.ptr, g, _in_ptr(dq, n, keep), _stream(stream))
+    _check(s, "tb_csc_hamiltonian", False)
+
+
+def tb_csc_loop(h: Handle, z, w, gamma, q_ref, g_s=2.0, dq_init=None, copts: CscOpts | None = None,
+                opts: SolveOpts | None = None, q_out=None, dq_out=None, stream=None, allow_unconverged=False):
+    """Self-consistent Mulliken charges (Eq. Hap-CSC, linear mixing); returns
+    (q, dq, stats dict)."""
+    import torch
+    keep = []
+    n = h.n_atoms
+    zz = _complex_host(z)
+    ww = _complex_host(w)
+    K = len(zz) // 2
+    if q_out is None:
+        q_out = torch.empty((n,), dtype=torch.float64, device="cuda")
+    if dq_out is None:
+        dq_out = torch.empty((n,), dtype=torch.float64, device="cuda")
+    copts = copts or tb_default_csc_opts()
+    opts = opts or tb_default_opts()
+    st = CscStats()
+    s = load_library().tb_csc_loop(h.ptr, K, _ptr(zz, C.c_double), _ptr(ww, C.c_double), float(g_s),
+                                   _in_ptr(gamma, n * n, keep), _in_ptr(q_ref, n, keep), _in_ptr(dq_init, n, keep),
+                                   C.byref(copts), C.byref(opts), _out_ptr(q_out), _out_ptr(dq_out),
+                                   C.byref(st), _stream(stream))
+    _check(s, "tb_csc_loop", allow_unconverged)
+    stats = {"status": tb_status_string(s), "iterations": st.iterations, "residual": st.residual,
+             "outer_iterations": st.outer_iterations, "inner_iterations": st.inner_iterations,
+             "seconds": st.seconds}
+    return q_out, dq_out, stats
 
 
 def tb_generalized_lanczos(h: Handle, j: int, n_steps: int, inner_tol=1e-13, stream=None):

@@ -129,3 +129,20 @@ def test_create_without_device_reports_no_device(lib, si):
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     assert _status(lambda: _create(si)) == 9
+
+
+def test_csc_defaults_and_null_arguments(lib):
+    import ctypes as C
+    from paper_1002_1202_gb300 import tb
+    o = tb.CscOpts()
+    lib.tb_default_csc_opts(C.byref(o))
+    assert (o.max_scf, o.scf_tol, o.mix) == (50, 1e-6, 0.3)
+    so = tb.SolveOpts()
+    lib.tb_default_opts(C.byref(so))
+    st = tb.CscStats()
+    z = np.array([0.0, 1.0])
+    zp = z.ctypes.data_as(C.POINTER(C.c_double))
+    # a NULL handle is rejected before any device work
+    assert lib.tb_csc_hamiltonian(None, None, None, None) == 1
+    assert lib.tb_csc_loop(None, 1, zp, zp, 2.0, None, None, None, C.byref(o), C.byref(so), None, None,
+                           C.byref(st), None) == 1
