@@ -59,6 +59,8 @@ def parse():
                     help="mixed: FP32 inner CG inside FP64 refinement (FP64-accurate); fp64: every product in FP64")
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the other precision, reported beside the headline (0: skip)")
+    ap.add_argument("--csc-scf", type=int, default=1,
+                    help="timed SCF iterations of the charge-self-consistency measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -67,6 +69,47 @@ def workload():
     s = si_system(CELLS, sigma=0.05, seed=SEED, cutoff=4.0)
     z, w = gauss_legendre_grid(K_SHIFTS, -20.0, 5.0, 0.01)
     return s, z, w
+
+
+def csc_measure(P, prec, n_scf, panel):
+    """Charge self-consistency (Eq. Hap-CSC) on liquid water, 256 neutral
+    molecules (768 atoms, N = 1536 orbitals), Klopman-Ohno gamma, 64
+    Gauss-Legendre nodes on [-60, -8] eV at a broadening of 2 eV, all 1536
+    columns per SCF iteration, linear mixing 0.3: one untimed SCF iteration,
+    then n_scf iterations timed with CUDA events (the loop is not run to
+    self-consistency here)."""
+    import torch
+    from tbinputs import water_system, gauss_legendre_grid, klopman_ohno_gamma, valence_populations
+    s = water_system(256, seed=4, excess_proton=False)
+    z, w = gauss_legendre_grid(64, -60.0, -8.0, 2.0)
+    gamma = torch.tensor(klopman_ohno_gamma(s), device="cuda")
+    q_ref = torch.tensor(valence_populations(s), device="cuda")
+    h = P.tb_create_system(s)
+    opts = P.tb_default_opts(tol=1e-8, precision=prec, panel=panel)
+    copts = P.tb_default_csc_opts(max_scf=1, mix=0.3, scf_tol=1e-12)
+    P.tb_csc_loop(h, z, w, gamma, q_ref, copts=copts, opts=opts, allow_unconverged=True)   # warm-up
+    copts = P.tb_default_csc_opts(max_scf=n_scf, mix=0.3, scf_tol=1e-12)
+    P.tb_profile_enable(True)
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    q, dq, st = P.tb_csc_loop(h, z, w, gamma, q_ref, copts=copts, opts=opts, allow_unconverged=True)
+    ev1.record(stream)
+    ev1.synchronize()
+    n_csc, ms_csc = P.tb_profile_read("csc")
+    P.tb_profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    return {"workload": "liquid water, 256 H2O (768 atoms, N=1536 sp/s orbitals), Klopman-Ohno gamma, "
+                        "64 GL shifts on [-60,-8] eV + 2i eV, all 1536 columns per SCF iteration, mixing 0.3",
+            "panel": panel,
+            "n_atoms": s.n_atoms, "N": s.n_orb, "blocks": s.nb, "scf_iterations": st["iterations"],
+            "ms_per_scf_iteration": ms / max(1, st["iterations"]),
+            "csc_kernels_ms_per_iteration": ms_csc / max(1, st["iterations"]),
+            "csc_kernel_launches": n_csc,
+            "shift_rhs_iterations_per_s": 64 * st["outer_iterations"] / (ms / 1e3),
+            "dq_residual": st["residual"]}
 
 
 def rank_columns(n_orb, panel, rank, seed=100):
@@ -444,6 +487,8 @@ def run_ours(args):
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
                                        / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),
     }
+    if world == 1 and args.csc_scf > 0:
+        line["csc"] = csc_measure(P, prec, args.csc_scf, args.panel)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, z, w, args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -259,6 +259,18 @@ tb_status tb_generalized_lanczos(tb_handle *h, int32_t j, int32_t n_steps, doubl
                                  double *a, double *b, double *norm, void *stream);
 
 /*
+ * Diagonal Green's function element from Lanczos coefficients (Section 3.2:
+ * G in the generalized Krylov subspace), the continued fraction
+ *     G_jj(z_k) = norm / (z_k - a_0 - b_1^2 / (z_k - a_1 - ... - b_{n-1}^2 / (z_k - a_{n-1})))
+ * evaluated bottom-up on the device for K points; the local density of
+ * states is -Im G_jj(E + i eta) / pi.  a [n_steps], b [n_steps + 1] as
+ * written by tb_generalized_lanczos (host or device); z: host, complex
+ * (interleaved re, im) [K]; G_out: complex [K], host or device.
+ */
+tb_status tb_lanczos_green(const double *a, const double *b, double norm, int32_t n_steps, int32_t K,
+                           const double *z, double *G_out, void *stream);
+
+/*
  * Allocation-free generalized Lanczos.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate GPU memory while they
  * call the library -- for example code that runs with the whole device

@@ -533,10 +533,12 @@ tb_status merge(tb_status run, tb_status fin) { return run != TB_OK && run != TB
 
 // Groups of consecutive atoms for the grouped FP32 SpMV: for each group the
 // ascending list of its distinct block columns and, per block, the position
-// of its column in that list.  G is the largest of 16, 8, 4, 2 whose shared
-// memory (neighbour-union panel rows of a 32-column slice plus the group's
-// S blocks) lets two CTAs share an SM; TB_SPMV_GROUP=G overrides the choice
-// (0 turns the grouped SpMV off).
+// of its column in that list.  G is 16 or 8 (CTAs of 256 or 128 threads),
+// the larger whose shared memory (neighbour-union panel rows of a 32-column
+// slice plus the group's S blocks) lets two CTAs share an SM; with neither
+// (dense neighbourhoods, e.g. ~39 neighbour atoms in liquid water) the
+// register-gather form is faster and no groups are built.
+// TB_SPMV_GROUP=G forces G (any of 16, 8, 4, 2; 0 turns the form off).
 struct SpmvGroups {
     int G = 0, n_groups = 0, max_union = 0, max_gblocks = 0;
     std::vector<int> ptr, cols, loc;
@@ -549,7 +551,7 @@ SpmvGroups build_spmv_groups(const std::vector<int>& brow, const std::vector<int
     SpmvGroups out;
     if (forced == 0) return out;
     for (int G : {16, 8, 4, 2}) {
-        if (forced > 0 && G != forced) continue;
+        if (forced > 0 ? G != forced : G < 8) continue;
         SpmvGroups g;
         g.G = G;
         g.n_groups = (n + G - 1) / G;
@@ -1073,6 +1075,27 @@ tb_status tb_csc_loop(tb_handle* h, int32_t K, const double* z, const double* w,
     cs.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = cs;
     return (res <= copts->scf_tol && !cocg_unconverged) ? TB_OK : TB_ERR_NOT_CONVERGED;
+}
+
+tb_status tb_lanczos_green(const double* a, const double* b, double norm, int32_t n_steps, int32_t K,
+                           const double* z, double* G_out, void* stream) {
+    if (!a || !b || !z || !G_out || n_steps < 1 || K < 1 || !std::isfinite(norm)) return TB_ERR_INVALID_ARG;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(z[k])) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    tb_status s;
+    const double *ad = nullptr, *bd = nullptr, *zd = nullptr;
+    if ((s = device_view(cl, a, (size_t)n_steps, &ad, st)) != TB_OK) return s;
+    if ((s = device_view(cl, b, (size_t)n_steps + 1, &bd, st)) != TB_OK) return s;
+    if ((s = device_view(cl, z, (size_t)2 * K, &zd, st)) != TB_OK) return s;
+    OutBuf ob;
+    if ((s = out_prepare(cl, ob, G_out, sizeof(double2) * (size_t)K)) != TB_OK) return s;
+    launch_lanczos_green(ad, bd, norm, n_steps, K, reinterpret_cast<const double2*>(zd),
+                         static_cast<double2*>(ob.dev), st);
+    TB_CK(cudaGetLastError());
+    return out_finish(ob, st);
 }
 
 tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, double inner_tol, double* a,

@@ -1474,6 +1474,23 @@ __global__ void k_csc_mix(const double* __restrict__ q, const double* __restrict
     }
 }
 
+
+// G(z_k) = norm / (z_k - a_0 - b_1^2 / (z_k - a_1 - ...)), one thread per
+// point, bottom-up (Section 3.2).
+__global__ void k_lanczos_green(const double* __restrict__ a, const double* __restrict__ b, double norm,
+                                int n_steps, int K, const double2* __restrict__ z, double2* __restrict__ G) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+        const double2 zk = z[k];
+        double2 g = cmk(0.0, 0.0);
+        for (int m = n_steps - 1; m >= 0; --m) {
+            const double2 tail = (m + 1 < n_steps) ? cmk(b[m + 1] * b[m + 1] * g.x, b[m + 1] * b[m + 1] * g.y)
+                                                   : cmk(0.0, 0.0);
+            g = cdiv(cmk(1.0, 0.0), csub(cmk(zk.x - a[m], zk.y), tail));
+        }
+        G[k] = cmk(norm * g.x, norm * g.y);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1769,6 +1786,13 @@ void launch_csc_mix(const double* q, const double* q_ref, const double* dq_in, d
                     unsigned long long* res_bits, cudaStream_t st) {
     LaunchScope ls_(K_CSC, st);
     k_csc_mix<<<grid_for(n), THREADS, 0, st>>>(q, q_ref, dq_in, dq_next, mix, n, res_bits);
+}
+
+
+void launch_lanczos_green(const double* a, const double* b, double norm, int n_steps, int K, const double2* z,
+                          double2* G, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_lanczos_green<<<grid_for(K), THREADS, 0, st>>>(a, b, norm, n_steps, K, z, G);
 }
 
 }  // namespace tb

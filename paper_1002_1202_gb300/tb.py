@@ -119,6 +119,7 @@ SIGNATURES = [
     ("tb_csc_loop", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, _VP, _VP, C.POINTER(CscOpts),
                               C.POINTER(SolveOpts), _VP, _VP, C.POINTER(CscStats), _VP]),
     ("tb_generalized_lanczos", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
+    ("tb_lanczos_green", C.c_int, [_VP, _VP, C.c_double, C.c_int32, C.c_int32, _DP, _VP, _VP]),
     ("tb_generalized_lanczos_noalloc", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
     ("tb_launch_count", C.c_int64, []),
@@ -414,6 +415,21 @@ def tb_generalized_lanczos(h: Handle, j: int, n_steps: int, inner_tol=1e-13, str
                                               C.c_void_p(nrm.ctypes.data), _stream(stream))
     _check(s, "tb_generalized_lanczos", False)
     return a, b, float(nrm[0])
+
+
+def tb_lanczos_green(a, b, norm: float, z, out=None, stream=None):
+    """G_jj(z_k) from Lanczos coefficients (continued fraction on the
+    device); returns a complex128 array (numpy unless ``out`` is given)."""
+    keep = []
+    n = len(a)
+    zz = _complex_host(z)
+    K = len(zz) // 2
+    if out is None:
+        out = np.zeros(K, dtype=np.complex128)
+    s = load_library().tb_lanczos_green(_in_ptr(a, n, keep), _in_ptr(b, n + 1, keep), float(norm), n, K,
+                                        _ptr(zz, C.c_double), _out_ptr(out), _stream(stream))
+    _check(s, "tb_lanczos_green", False)
+    return out
 
 
 def tb_generalized_lanczos_noalloc(h: Handle, j: int, n_steps: int, inner_tol=1e-13, stream=None, out=None):

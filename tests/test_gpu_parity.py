@@ -222,6 +222,16 @@ def test_lanczos(P, c1, h1):
     g = method.lanczos_green(a, b, nrm, zz)
     ref = dense.green_columns(H, S, zz, [j])[:, j, 0]
     assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max()
+    # the continued fraction on the device: the oracle's on the same
+    # coefficients, and the dense G_jj (local density of states)
+    zl = np.linspace(-25.0, 10.0, 301) + 2.0j
+    gd = P.tb_lanczos_green(a, b, nrm, zl)
+    go = method.lanczos_green(a, b, nrm, zl)
+    assert np.abs(gd - go).max() <= 1e-12 * np.abs(go).max()
+    gref = dense.green_columns(H, S, zl[::30], [j])[:, j, 0]
+    assert np.abs(gd[::30] - gref).max() <= 1e-8 * np.abs(gref).max()
+    with pytest.raises(P.TBError):
+        P.tb_lanczos_green(a, b, float("nan"), zl)
 
 
 def test_not_converged_status(P, c1, h1):
