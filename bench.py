@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -252,9 +253,28 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def kernel_source_sha256(kernel_file, kernel_name):
+    """sha256 of the text of one kernel's definition (from ``__global__`` to
+    its closing brace) in a file of the CUDA sources; None if not found."""
+    src = open(os.path.join(ROOT, "paper_1002_1202_gb300", "csrc", kernel_file)).read()
+    m = re.search(r"__global__[^;{]*?\b%s\s*\(" % re.escape(kernel_name), src)
+    if not m:
+        return None
+    i = src.index("{", m.end())
+    depth = 0
+    for j in range(i, len(src)):
+        if src[j] == "{":
+            depth += 1
+        elif src[j] == "}":
+            depth -= 1
+            if depth == 0:
+                return hashlib.sha256(src[m.start():j + 1].encode()).hexdigest()
+    return None
+
+
 def stored_traffic(kernel_file, kernel_name):
     """DRAM bytes per launch from a committed ncu summary, valid only while
-    the kernel source it was taken from is unchanged."""
+    the text of the kernel it was taken from is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -264,8 +284,7 @@ def stored_traffic(kernel_file, kernel_name):
         return None
     if not rec:
         return None
-    src = open(os.path.join(ROOT, "paper_1002_1202_gb300", "csrc", kernel_file), "rb").read()
-    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+    if kernel_source_sha256(kernel_file, kernel_name) != rec.get("kernel_sha256"):
         return None
     return rec.get("dram_bytes_per_launch")
 

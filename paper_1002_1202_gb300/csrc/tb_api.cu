@@ -340,6 +340,8 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         if ((s = dalloc(cl, &p.acc32, 8 * P)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.cgs, 4 * P)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.cgu, 2 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.ticket32, 1)) != TB_OK) return s;
+        TB_CK(cudaMemsetAsync(p.ticket32, 0, sizeof(unsigned), st));
         if ((s = dalloc(cl, &p.dbg, 8)) != TB_OK) return s;
         if (std::getenv("TB_TRACE")) {
             if ((s = dalloc(cl, &p.hist, (size_t)HIST_IT * 2 * P * 4)) != TB_OK) return s;
@@ -573,7 +575,7 @@ SpmvGroups build_spmv_groups(const std::vector<int>& brow, const std::vector<int
         const size_t xregion = (size_t)g.max_union * 4 * 32 * 8;
         const size_t red = (size_t)(G / 2) * 16 * 8 * 8;
         const size_t smem = 128 + std::max(xregion, red) + (size_t)g.max_gblocks * 64;
-        if (smem <= budget || (forced > 0 && smem <= 227 * 1024)) return g;
+        if (smem <= budget || (forced > 0 && smem <= 226 * 1024)) return g;
     }
     return out;
 }

@@ -100,6 +100,7 @@ struct PanelDev {
     double* acc32 = nullptr;       // [2][4][P]: FP32 CG sums (gamma, delta per real column), two slots
     double* cgs = nullptr;         // [2][2P]: alpha, beta of the current FP32 CG iteration
     unsigned char* cgu = nullptr;  // [2P]: real column updated in the current FP32 CG iteration
+    unsigned* ticket32 = nullptr;  // [1]: completion ticket of the FP32 SpMV (0 between launches)
     ColState* col = nullptr;       // [P]
     InnerState* inner = nullptr;   // [2P]
     double2* z = nullptr;          // [K]

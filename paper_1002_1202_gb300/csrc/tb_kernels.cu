@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <vector>
 
@@ -674,6 +675,96 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
+// CG scalars of iteration it, once, by the last CTA of the SpMV to finish
+// (every thread of that CTA calls this): FP64 alpha, beta and the
+// convergence of every real column from the accumulated sums; the update
+// kernel that follows only reads them (cgs[0..2P) alpha, [2P..4P) beta,
+// upd flags in cgu[0..2P)).  The sums are read through L2 (__ldcg): other
+// CTAs added them with device-scope atomics before their fence and ticket.
+__device__ void inner32_scalars_cta(const PanelDev& p, int it) {
+    __shared__ int s_cnt, s_err;
+    const int P = p.P;
+    const InnerState* base = p.inner32;
+    const InnerState* prev = p.inner32 + (size_t)(1 + (it & 1)) * 2 * P;
+    InnerState* next = p.inner32 + (size_t)(1 + ((it + 1) & 1)) * 2 * P;
+    const double* acc_slot = p.acc32 + (size_t)(it & 1) * 4 * P;
+    if (threadIdx.x == 0) { s_cnt = 0; s_err = 0; }
+    __syncthreads();
+    for (int rc = threadIdx.x; rc < 2 * P; rc += blockDim.x) {
+        const int c = rc >> 1, part = rc & 1;
+        const bool cact = p.col[c].active != 0;
+        InnerState st = prev[rc];
+        const double gam = __ldcg(acc_slot + (size_t)part * P + c);
+        const double del = __ldcg(acc_slot + (size_t)(2 + part) * P + c);
+        if (it == 0) {
+            st.bnorm2 = gam;
+            st.conv = (!cact || base[rc].skip || gam == 0.0) ? 1 : 0;
+        }
+        if (!st.conv) {
+            if (gam <= p.inner_lo_tol * p.inner_lo_tol * st.bnorm2) {
+                st.conv = 1;
+            } else {
+                const double beta = (it == 0) ? 0.0 : gam / st.gamma_prev;
+                const double den = del - ((it == 0) ? 0.0 : beta * gam / st.alpha);
+                // In exact arithmetic p^T S p >= r^T S r / cond(S); p^T S p <= 0 at
+                // the first iteration (r^T S r <= 0), or while the residual is above
+                // 1 % of its start, means S is not positive definite.  Otherwise a
+                // non-positive or collapsed value is cancellation in the FP32
+                // recurrences: the round stops and the FP64 refinement residual
+                // decides what is left (counted in flags[5]).
+                if (!(den > 0.0) || (it > 0 && den < 1e-4 * del)) {
+                    if (it == 0 || (!(den > 0.0) && gam > 1e-4 * st.bnorm2)) s_err = 1;
+                    else s_err = 2;
+                    if (p.dbg) {
+                        p.dbg[0] = it; p.dbg[1] = rc; p.dbg[2] = gam; p.dbg[3] = del;
+                        p.dbg[4] = den; p.dbg[5] = st.bnorm2; p.dbg[6] = st.gamma_prev; p.dbg[7] = st.alpha;
+                    }
+                    st.conv = 1;
+                } else {
+                    st.alpha = gam / den;
+                    st.beta = beta;
+                    st.gamma_prev = gam;
+                }
+            }
+        }
+        p.cgs[rc] = st.alpha;
+        p.cgs[2 * P + rc] = st.beta;
+        p.cgu[rc] = st.conv ? 0 : 1;
+        if (!st.conv) atomicAdd(&s_cnt, 1);
+        next[rc] = st;
+        if (p.hist && it < HIST_IT) {
+            double* hh = p.hist + ((size_t)it * 2 * P + rc) * 4;
+            hh[0] = gam; hh[1] = del; hh[2] = st.conv ? 0.0 : st.alpha; hh[3] = st.conv ? 0.0 : st.beta;
+        }
+    }
+    double* acc_next = p.acc32 + (size_t)((it + 1) & 1) * 4 * P;
+    for (int q = threadIdx.x; q < 4 * P; q += blockDim.x) acc_next[q] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        p.flags[1] = s_cnt;
+        if (s_cnt == 0) p.flags[3] = it;
+        if (s_err == 1) atomicOr(&p.flags[0], ERR_NOT_SPD);
+        if (s_err == 2) atomicAdd(&p.flags[5], 1);
+        p.flags[7] = it;            // iteration whose scalars cgs/cgu hold
+        *p.ticket32 = 0u;           // the next SpMV counts from zero
+    }
+}
+
+// Completion ticket of the FP32 SpMV kernels: every CTA fences its atomic
+// sums and takes a ticket; the CTA with the last one derives the CG scalars.
+// No CTA waits for another.
+__device__ void inner32_ticket_tail(const PanelDev& p, int it) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(p.ticket32, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        inner32_scalars_cta(p, it);
+    }
+}
+
 // w = S r (FP32) and the sums gamma = r.r, delta = w.r of every real column.
 // CPT complex columns per thread (2: one float4 per orbital row), P / CPT
 // threads per block row; the block-column index of the next block is loaded
@@ -773,6 +864,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_spmv(DevSystem s, PanelD
             }
         }
     }
+    inner32_ticket_tail(p, it);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
@@ -821,7 +913,7 @@ __global__ void __launch_bounds__(256) k_inner32_spmv_grp(DevSystem s, PanelDev 
                                                 : !(cgp[2 * c].conv && cgp[2 * c + 1].conv));
         }
     }
-    if (!__syncthreads_or(live)) return;
+    const bool any_live = __syncthreads_or(live);
     const size_t xregion = (size_t)s.max_union * 4 * PC * sizeof(float2);
     const size_t red_bytes = (size_t)(blockDim.x / 32) * TPA * 8 * sizeof(double);
     float4* xs = reinterpret_cast<float4*>(gsm + GRP_HDR);                       // [U][4][PC/2]
@@ -829,7 +921,7 @@ __global__ void __launch_bounds__(256) k_inner32_spmv_grp(DevSystem s, PanelDev 
     const float4* ss = reinterpret_cast<const float4*>(gsm + GRP_HDR + (xregion > red_bytes ? xregion : red_bytes));
     // stage the union's panel rows (16 float4 per row of the slice) and the
     // group's S blocks with 16-byte asynchronous copies by every thread
-    {
+    if (any_live) {
         const int nx = U * 4 * TPA;               // float4 of the union rows
         const uint32_t xs_a = smem_u32(xs);
         for (int k = t; k < nx; k += blockDim.x) {
@@ -921,117 +1013,76 @@ __global__ void __launch_bounds__(256) k_inner32_spmv_grp(DevSystem s, PanelDev 
         const int c = slice * PC + 2 * tcol + q / 4;
         if (sum != 0.0) atomicAdd(p.acc32 + (size_t)(it & 1) * 4 * P + (size_t)(q % 4) * P + c, sum);
     }
+    inner32_ticket_tail(p, it);
 }
 
-
-// CG scalars of iteration it, once, in one CTA: FP64 alpha, beta and the
-// convergence of every real column from the accumulated sums; the update
-// kernel that follows only reads them (cgs[0..2P) alpha, [2P..4P) beta,
-// upd flags in cgu[0..2P)).
-__global__ void __launch_bounds__(THREADS) k_inner32_scalars(PanelDev p, int it) {
-    __shared__ int s_cnt, s_err;
-    if (*(volatile int*)&p.flags[1] == 0) return;
-    const int P = p.P;
-    const InnerState* base = p.inner32;
-    const InnerState* prev = p.inner32 + (size_t)(1 + (it & 1)) * 2 * P;
-    InnerState* next = p.inner32 + (size_t)(1 + ((it + 1) & 1)) * 2 * P;
-    const double* acc_slot = p.acc32 + (size_t)(it & 1) * 4 * P;
-    if (threadIdx.x == 0) { s_cnt = 0; s_err = 0; }
-    __syncthreads();
-    for (int rc = threadIdx.x; rc < 2 * P; rc += THREADS) {
-        const int c = rc >> 1, part = rc & 1;
-        const bool cact = p.col[c].active != 0;
-        InnerState st = prev[rc];
-        const double gam = acc_slot[(size_t)part * P + c];
-        const double del = acc_slot[(size_t)(2 + part) * P + c];
-        if (it == 0) {
-            st.bnorm2 = gam;
-            st.conv = (!cact || base[rc].skip || gam == 0.0) ? 1 : 0;
-        }
-        if (!st.conv) {
-            if (gam <= p.inner_lo_tol * p.inner_lo_tol * st.bnorm2) {
-                st.conv = 1;
-            } else {
-                const double beta = (it == 0) ? 0.0 : gam / st.gamma_prev;
-                const double den = del - ((it == 0) ? 0.0 : beta * gam / st.alpha);
-                // In exact arithmetic p^T S p >= r^T S r / cond(S); p^T S p <= 0 at
-                // the first iteration (r^T S r <= 0), or while the residual is above
-                // 1 % of its start, means S is not positive definite.  Otherwise a
-                // non-positive or collapsed value is cancellation in the FP32
-                // recurrences: the round stops and the FP64 refinement residual
-                // decides what is left (counted in flags[5]).
-                if (!(den > 0.0) || (it > 0 && den < 1e-4 * del)) {
-                    if (it == 0 || (!(den > 0.0) && gam > 1e-4 * st.bnorm2)) s_err = 1;
-                    else s_err = 2;
-                    if (p.dbg) {
-                        p.dbg[0] = it; p.dbg[1] = rc; p.dbg[2] = gam; p.dbg[3] = del;
-                        p.dbg[4] = den; p.dbg[5] = st.bnorm2; p.dbg[6] = st.gamma_prev; p.dbg[7] = st.alpha;
-                    }
-                    st.conv = 1;
-                } else {
-                    st.alpha = gam / den;
-                    st.beta = beta;
-                    st.gamma_prev = gam;
-                }
-            }
-        }
-        p.cgs[rc] = st.alpha;
-        p.cgs[2 * P + rc] = st.beta;
-        p.cgu[rc] = st.conv ? 0 : 1;
-        if (!st.conv) atomicAdd(&s_cnt, 1);
-        next[rc] = st;
-        if (p.hist && it < HIST_IT) {
-            double* hh = p.hist + ((size_t)it * 2 * P + rc) * 4;
-            hh[0] = gam; hh[1] = del; hh[2] = st.conv ? 0.0 : st.alpha; hh[3] = st.conv ? 0.0 : st.beta;
-        }
-    }
-    double* acc_next = p.acc32 + (size_t)((it + 1) & 1) * 4 * P;
-    for (int q = threadIdx.x; q < 4 * P; q += THREADS) acc_next[q] = 0.0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        p.flags[1] = s_cnt;
-        if (s_cnt == 0) p.flags[3] = it;
-        if (s_err == 1) atomicOr(&p.flags[0], ERR_NOT_SPD);
-        if (s_err == 2) atomicAdd(&p.flags[5], 1);
-        p.flags[7] = it;            // iteration whose scalars cgs/cgu hold
-    }
-}
 
 // p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s (FP32) with the
-// scalars of k_inner32_scalars.  At it == 0 every vector is initialised.
+// scalars that the last CTA of the SpMV derived.  At it == 0 every vector
+// is initialised.
+template <int V>
 __global__ void k_inner32_update(PanelDev p, int it) {
+    // V complex columns per thread (V = 2: one float4 of each vector)
+    using vec = typename std::conditional<V == 2, float4, float2>::type;
     const int P = p.P;
-    if (*(volatile int*)&p.flags[7] != it) return;      // the scalar kernel of this iteration did not run
-    const int c = threadIdx.x % P;
-    if (!p.col[c].active) return;
-    const bool u0 = p.cgu[2 * c] != 0, u1 = p.cgu[2 * c + 1] != 0;
-    if (!u0 && !u1 && it > 0) return;
-    const float a0 = (float)p.cgs[2 * c], a1 = (float)p.cgs[2 * c + 1];
-    const float b0 = (float)p.cgs[2 * P + 2 * c], b1 = (float)p.cgs[2 * P + 2 * c + 1];
-    const long long items = (long long)p.npad * P;
+    if (*(volatile int*)&p.flags[7] != it) return;      // no scalars for this iteration (the SpMV exited early)
+    const int c0 = (V * threadIdx.x) % P;
+    // per real column q: act (the complex column is active: at it == 0 its
+    // p, s, x start at zero) and upd (this iteration updates it); inactive
+    // columns keep their vectors
+    float a[2 * V], b[2 * V];
+    bool act[2 * V], upd[2 * V];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const int c = c0 + j;
+        const bool ac = p.col[c].active != 0;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const int q = 2 * j + part, rc = 2 * c + part;
+            act[q] = ac;
+            upd[q] = ac && p.cgu[rc] != 0;
+            a[q] = upd[q] ? (float)p.cgs[rc] : 0.f;
+            b[q] = upd[q] ? (float)p.cgs[2 * P + rc] : 0.f;
+            any |= (it == 0) ? act[q] : upd[q];
+        }
+    }
+    if (!any) return;
+    const long long items = (long long)p.npad * P / V;
+    vec* r32 = reinterpret_cast<vec*>(p.r32);
+    vec* w32 = reinterpret_cast<vec*>(p.w32);
+    vec* p32 = reinterpret_cast<vec*>(p.p32);
+    vec* s32 = reinterpret_cast<vec*>(p.s32);
+    vec* x32 = reinterpret_cast<vec*>(p.x32);
     for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
          idx += (long long)gridDim.x * THREADS) {
-        const float2 r = p.r32[idx], w = p.w32[idx];
-        float2 pv = (it == 0) ? make_float2(0.f, 0.f) : p.p32[idx];
-        float2 sv = (it == 0) ? make_float2(0.f, 0.f) : p.s32[idx];
-        float2 x = (it == 0) ? make_float2(0.f, 0.f) : p.x32[idx];
-        float2 rn = r;
-        if (u0) {
-            pv.x = r.x + b0 * pv.x;
-            sv.x = w.x + b0 * sv.x;
-            x.x += a0 * pv.x;
-            rn.x = r.x - a0 * sv.x;
+        const vec rv = r32[idx], wv = w32[idx];
+        vec pv = p32[idx], sv = s32[idx], xv = x32[idx];
+        vec rn = rv;
+        const float* r = reinterpret_cast<const float*>(&rv);
+        const float* w = reinterpret_cast<const float*>(&wv);
+        float* pp = reinterpret_cast<float*>(&pv);
+        float* ss = reinterpret_cast<float*>(&sv);
+        float* xx = reinterpret_cast<float*>(&xv);
+        float* rr = reinterpret_cast<float*>(&rn);
+#pragma unroll
+        for (int q = 0; q < 2 * V; ++q) {
+            if (it == 0 && act[q]) {
+                pp[q] = 0.f;
+                ss[q] = 0.f;
+                xx[q] = 0.f;
+            }
+            if (upd[q]) {
+                pp[q] = r[q] + b[q] * pp[q];
+                ss[q] = w[q] + b[q] * ss[q];
+                xx[q] += a[q] * pp[q];
+                rr[q] = r[q] - a[q] * ss[q];
+            }
         }
-        if (u1) {
-            pv.y = r.y + b1 * pv.y;
-            sv.y = w.y + b1 * sv.y;
-            x.y += a1 * pv.y;
-            rn.y = r.y - a1 * sv.y;
-        }
-        p.p32[idx] = pv;
-        p.s32[idx] = sv;
-        p.x32[idx] = x;
-        p.r32[idx] = rn;
+        p32[idx] = pv;
+        s32[idx] = sv;
+        x32[idx] = xv;
+        r32[idx] = rn;
     }
 }
 
@@ -1668,9 +1719,14 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
         const size_t sm = inner32_grp_smem(s);
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-            attr = true;
+            // the dynamic limit leaves room for the kernel's static shared memory
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, k_inner32_spmv_grp) == cudaSuccess &&
+                cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024 - (int)fa.sharedSizeBytes) == cudaSuccess &&
+                cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+                    cudaSuccess)
+                attr = true;
         }
         k_inner32_spmv_grp<<<s.n_groups * (p.P / PC), s.grpG * (PC / 2), sm, st>>>(s, p, it);
     } else if (p.P >= 2)
@@ -1679,12 +1735,11 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
 }
 void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
-    {
-        LaunchScope ls_(K_INNER32_UPDATE, st);
-        k_inner32_scalars<<<1, THREADS, 0, st>>>(p, it);
-    }
     LaunchScope ls_(K_INNER32_UPDATE, st);
-    k_inner32_update<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
+    if (p.P >= 2)
+        k_inner32_update<2><<<grid_for((long long)p.npad * p.P / 2), THREADS, 0, st>>>(p, it);
+    else
+        k_inner32_update<1><<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
 }
 static size_t shift_smem(const PanelDev& p) { return sizeof(double2) * ((size_t)(p.M > 0 ? p.M : 1) + 3 * (size_t)p.K); }
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
