@@ -60,6 +60,7 @@ def parse():
                     help="mixed: FP32 inner CG inside FP64 refinement (FP64-accurate); fp64: every product in FP64")
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the other precision, reported beside the headline (0: skip)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--csc-scf", type=int, default=1,
                     help="timed SCF iterations of the charge-self-consistency measurement (0: skip)")
     return ap.parse_args()
@@ -111,6 +112,48 @@ def csc_measure(P, prec, n_scf, panel):
             "csc_kernel_launches": n_csc,
             "shift_rhs_iterations_per_s": 64 * st["outer_iterations"] / (ms / 1e3),
             "dq_residual": st["residual"]}
+
+
+def batch_measure(P, prec, panel):
+    """Ragged batch: 8 liquid-water boxes of 64-192 molecules (one H3O+ each,
+    seeded sizes), 64 seeded columns per box, 64 Gauss-Legendre shifts on
+    [-60, -8] eV + 2i eV, solved to 1e-8 as one block-diagonal batch handle
+    and, for comparison, box by box (one handle and solve per box); both
+    timed with CUDA events."""
+    import torch
+    from tbinputs import water_system, gauss_legendre_grid
+    rng = np.random.default_rng(4)
+    sizes = [int(n) for n in rng.integers(64, 193, size=8)]
+    boxes = [water_system(n, seed=10 + i) for i, n in enumerate(sizes)]
+    cols = [np.sort(np.random.default_rng(5 + i).choice(b.n_orb, 64, replace=False)).astype(np.int32)
+            for i, b in enumerate(boxes)]
+    z, w = gauss_legendre_grid(64, -60.0, -8.0, 2.0)
+    opts = P.tb_default_opts(tol=1e-8, precision=prec, panel=panel)
+    hb = P.tb_create_batch(boxes)
+    hs = [P.tb_create_system(b) for b in boxes]
+    all_cols = np.concatenate([c + hb.orb_off[i] for i, c in enumerate(cols)]).astype(np.int32)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()                                   # warm-up
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        its = fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3, its
+
+    t_b, it_b = timed(lambda: P.tb_mulliken_orbital(hb, z, w, all_cols, 2.0, opts=opts)[1]["outer_iterations"])
+    t_s, it_s = timed(lambda: sum(P.tb_mulliken_orbital(h, z, w, c, 2.0, opts=opts)[1]["outer_iterations"]
+                                  for h, c in zip(hs, cols)))
+    return {"workload": "ragged batch: 8 water boxes of %s molecules (+H3O+), 64 columns each, 64 GL shifts "
+                        "on [-60,-8] eV + 2i eV, tol 1e-8" % sizes,
+            "n_atoms": int(hb.n_atoms), "N": int(hb.n_orb), "panel": panel,
+            "batched_shift_rhs_iterations_per_s": 64 * it_b / t_b,
+            "per_box_shift_rhs_iterations_per_s": 64 * it_s / t_s,
+            "batched_s": t_b, "per_box_s": t_s, "speedup": t_s / t_b}
 
 
 def rank_columns(n_orb, panel, rank, seed=100):
@@ -506,6 +549,8 @@ def run_ours(args):
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
                                        / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),
     }
+    if world == 1 and not args.no_batch:
+        line["batch"] = batch_measure(P, prec, args.panel)
     if world == 1 and args.csc_scf > 0:
         line["csc"] = csc_measure(P, prec, args.csc_scf, args.panel)
     if world == 1 and not args.no_cpu_baseline:

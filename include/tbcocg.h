@@ -94,6 +94,24 @@ typedef struct {
  * TB_ERR_NO_DEVICE.  On error *out is NULL and nothing is allocated. */
 tb_status tb_create(tb_handle **out, const tb_system_desc *desc, void *stream);
 
+/*
+ * Ragged batch: n_systems independent systems (for example liquid-water
+ * boxes of different sizes) in one handle.  They are placed block-diagonally
+ * -- atoms and orbitals numbered system after system, no block couples two
+ * systems -- so the Krylov space of a column e_j never leaves its system,
+ * and every solve, Mulliken, CSC and Lanczos call takes columns of any
+ * system of the batch in one launch sequence, with the results of separate
+ * per-system solves (up to rounding order).  Every desc is validated as by
+ * tb_create; H_vals must be given for all systems or for none, and with
+ * none (Eq. Hap-1 on the device) all K must be equal.  Errors as tb_create.
+ */
+tb_status tb_create_batch(tb_handle **out, const tb_system_desc *descs, int32_t n_systems, void *stream);
+
+/* Systems of a handle (1 for tb_create) and their first atom / orbital:
+ * atom_off, orb_off: host int64 [n_systems + 1] (either may be NULL). */
+int32_t tb_num_systems(const tb_handle *h);
+tb_status tb_batch_offsets(const tb_handle *h, int64_t *atom_off, int64_t *orb_off);
+
 /* Release all device memory of the handle (NULL is allowed). */
 tb_status tb_destroy(tb_handle *h);
 

@@ -4,12 +4,14 @@
 #include "tb_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 using namespace tb;
@@ -37,6 +39,15 @@ struct tb_handle {
     int64_t* atom_orb_off = nullptr;  // device [n_atoms + 1]: first caller orbital of every atom
     double* H0 = nullptr;             // device [nb][16]: the Hamiltonian of tb_create, kept once
                                       // the charge-self-consistent term first replaces H
+    std::vector<int64_t> sys_atom_off;  // batch: first atom of every system, [n_systems + 1]
+    std::vector<int64_t> sys_orb_off;   // batch: first orbital of every system
+    // batch only: one solve view per system (block rows offset to the
+    // system's first atom, block columns local to it)
+    std::vector<DevSystem> sys_ds;
+    std::vector<int32_t> orb2pad_local_h;  // [N]: padded slot within the orbital's own system
+    int32_t* orb2pad_local = nullptr;      // device copy
+    int32_t* bcol_local = nullptr;         // device [nb]: block column local to its system
+    int* flags_host_sys = nullptr;         // pinned [n_systems][NFLAGS]
 };
 
 namespace {
@@ -106,6 +117,18 @@ struct Solve {
     double* q_out = nullptr;            // srow, per column
 };
 
+// What one solve sees of a system: the device arrays (a whole handle, or one
+// system of a batch with block-row pointers offset to its first atom and
+// block columns local to it), the caller-orbital -> padded-slot map of its
+// orbitals, and a pinned word array for the device status flags.
+struct View {
+    DevSystem ds;
+    const int32_t* o2p_h = nullptr;   // host [n_orb]
+    const int32_t* o2p_d = nullptr;   // device [n_orb]
+    int64_t n_orb = 0;
+    int* flags_host = nullptr;        // pinned [NFLAGS]
+};
+
 tb_status check_opts(const tb_solve_opts* o) {
     if (!o) return TB_ERR_INVALID_ARG;
     if (!(o->tol > 0.0) || !(o->inner_tol > 0.0) || o->max_iter < 1 || o->inner_max_iter < 1) return TB_ERR_INVALID_ARG;
@@ -119,22 +142,22 @@ tb_status check_opts(const tb_solve_opts* o) {
 // Inner CG for S r' = r on the current panel; one host synchronisation in the
 // common case (the number of iterations is predicted from the previous call
 // and the surplus launches exit at once).
-tb_status inner_cg(tb_handle* h, const PanelDev& p, int inner_max, int& pred, int64_t& inner_total, cudaStream_t st) {
+tb_status inner_cg(View& v, const PanelDev& p, int inner_max, int& pred, int64_t& inner_total, cudaStream_t st) {
     int launched = 0;
     int target = std::min(std::max(pred, 1), inner_max);
     while (true) {
         for (int i = launched; i < target; ++i) {
-            launch_inner_spmv(h->ds, p, i, st);
-            launch_inner_update(h->ds, p, i, st);
+            launch_inner_spmv(v.ds, p, i, st);
+            launch_inner_update(v.ds, p, i, st);
         }
         launched = target;
         TB_CK(cudaGetLastError());
-        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
         TB_CK(cudaStreamSynchronize(st));
         prof_harvest();
-        if (h->flags_host[1] == 0) {
-            inner_total += h->flags_host[3];
-            pred = h->flags_host[3] + 1;
+        if (v.flags_host[1] == 0) {
+            inner_total += v.flags_host[3];
+            pred = v.flags_host[3] + 1;
             return TB_OK;
         }
         if (launched >= inner_max) return TB_ERR_NOT_CONVERGED;
@@ -143,24 +166,24 @@ tb_status inner_cg(tb_handle* h, const PanelDev& p, int inner_max, int& pred, in
 }
 
 // FP32 CG of one refinement round (same prediction scheme as inner_cg).
-tb_status inner_cg32(tb_handle* h, const PanelDev& p, int inner_max, int& pred, int64_t& inner_total,
+tb_status inner_cg32(View& v, const PanelDev& p, int inner_max, int& pred, int64_t& inner_total,
                      cudaStream_t st) {
     int launched = 0;
     int target = std::min(std::max(pred, 1), inner_max);
     while (true) {
         for (int i = launched; i < target; ++i) {
-            launch_inner32_spmv(h->ds, p, i, st);
-            launch_inner32_update(h->ds, p, i, st);
+            launch_inner32_spmv(v.ds, p, i, st);
+            launch_inner32_update(v.ds, p, i, st);
         }
         launched = target;
         TB_CK(cudaGetLastError());
-        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
         TB_CK(cudaStreamSynchronize(st));
         prof_harvest();
-        if (h->flags_host[1] == 0) {
-            if (h->flags_host[4] > 0) {      // the round had work (flags[3] is this round's count)
-                inner_total += h->flags_host[3];
-                pred = h->flags_host[3] + 1;
+        if (v.flags_host[1] == 0) {
+            if (v.flags_host[4] > 0) {      // the round had work (flags[3] is this round's count)
+                inner_total += v.flags_host[3];
+                pred = v.flags_host[3] + 1;
             }
             return TB_OK;
         }
@@ -172,13 +195,13 @@ tb_status inner_cg32(tb_handle* h, const PanelDev& p, int inner_max, int& pred, 
 // r' = S^-1 b by FP32 CG corrections inside FP64 iterative refinement
 // (TB_MIXED).  The expected number of rounds is carried between calls so
 // that the common case costs one host synchronisation per round.
-void debug_inner32(tb_handle* h, const PanelDev& p, int round, cudaStream_t st) {
+void debug_inner32(View& v, const PanelDev& p, int round, cudaStream_t st) {
     if (!std::getenv("TB_DEBUG")) return;
     std::vector<InnerState> is(2 * p.P);
     cudaMemcpyAsync(is.data(), p.inner32, sizeof(InnerState) * 2 * p.P, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
-    std::fprintf(stderr, "[tb] round %d flags %d %d %d %d %d\n", round, h->flags_host[0], h->flags_host[1],
-                 h->flags_host[2], h->flags_host[3], h->flags_host[4]);
+    std::fprintf(stderr, "[tb] round %d flags %d %d %d %d %d\n", round, v.flags_host[0], v.flags_host[1],
+                 v.flags_host[2], v.flags_host[3], v.flags_host[4]);
     double dbg[8] = {0};
     if (p.dbg) {
         cudaMemcpyAsync(dbg, p.dbg, sizeof(dbg), cudaMemcpyDeviceToHost, st);
@@ -195,12 +218,12 @@ void debug_inner32(tb_handle* h, const PanelDev& p, int round, cudaStream_t st) 
 // TB_TRACE=1 in the environment prints the progress of every refinement round
 static const bool g_trace = std::getenv("TB_TRACE") != nullptr;
 
-tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inner_max, int& pred32,
+tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_max, int& pred32,
                       int& rounds_pred, int64_t& inner_total, cudaStream_t st) {
-    launch_refine_start(h->ds, p, b, st);
-    launch_refine_scale(h->ds, p, b, st);
+    launch_refine_start(v.ds, p, b, st);
+    launch_refine_scale(v.ds, p, b, st);
     for (int round = 0;; ++round) {
-        tb_status s = inner_cg32(h, p, inner_max, pred32, inner_total, st);
+        tb_status s = inner_cg32(v, p, inner_max, pred32, inner_total, st);
         if (s != TB_OK) return s;
         if (g_trace && p.hist) {
             const size_t nh = (size_t)HIST_IT * 2 * p.P * 4;
@@ -227,19 +250,19 @@ tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inn
             }
             cudaMemsetAsync(p.hist, 0, sizeof(double) * nh, st);
         }
-        if (h->flags_host[0] & (ERR_NOT_SPD | ERR_BREAKDOWN)) {
-            debug_inner32(h, p, round, st);
-            return (h->flags_host[0] & ERR_NOT_SPD) ? TB_ERR_S_NOT_SPD : TB_ERR_BREAKDOWN;
+        if (v.flags_host[0] & (ERR_NOT_SPD | ERR_BREAKDOWN)) {
+            debug_inner32(v, p, round, st);
+            return (v.flags_host[0] & ERR_NOT_SPD) ? TB_ERR_S_NOT_SPD : TB_ERR_BREAKDOWN;
         }
-        if (round > 0 && h->flags_host[4] == 0) {   // the last residual was already within tolerance
+        if (round > 0 && v.flags_host[4] == 0) {   // the last residual was already within tolerance
             rounds_pred = round;
             return TB_OK;
         }
-        launch_refine_add(h->ds, p, st);
-        launch_refine_residual(h->ds, p, b, st);
-        launch_refine_scale(h->ds, p, p.Rin, st);
+        launch_refine_add(v.ds, p, st);
+        launch_refine_residual(v.ds, p, b, st);
+        launch_refine_scale(v.ds, p, p.Rin, st);
         if (g_trace) {
-            cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st);
             cudaStreamSynchronize(st);
             std::vector<InnerState> is(2 * p.P);
             cudaMemcpyAsync(is.data(), p.inner32, sizeof(InnerState) * 2 * p.P, cudaMemcpyDeviceToHost, st);
@@ -248,15 +271,15 @@ tb_status mixed_inner(tb_handle* h, const PanelDev& p, const double2* b, int inn
             for (auto& x : is)
                 if (!x.skip) { smin = std::min(smin, x.scale); smax = std::max(smax, x.scale); }
             std::fprintf(stderr, "[tb] round %d: cg iters %d, unconverged real columns %d, early stops %d, "
-                         "scale range %.3e .. %.3e\n", round, h->flags_host[3], h->flags_host[4],
-                         h->flags_host[5], smin, smax);
+                         "scale range %.3e .. %.3e\n", round, v.flags_host[3], v.flags_host[4],
+                         v.flags_host[5], smin, smax);
         }
         if (round + 1 >= rounds_pred) {
             TB_CK(cudaGetLastError());
-            TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
+            TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
             TB_CK(cudaStreamSynchronize(st));
             prof_harvest();
-            if (h->flags_host[4] == 0) {
+            if (v.flags_host[4] == 0) {
                 rounds_pred = round + 1;
                 return TB_OK;
             }
@@ -271,10 +294,10 @@ struct InnerCtx {
     int redo = 0;
 };
 
-tb_status inner_solve(tb_handle* h, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic,
+tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic,
                       cudaStream_t st) {
-    if (!p.mixed) return inner_cg(h, p, inner_max, ic.pred, ic.total, st);
-    tb_status s = mixed_inner(h, p, b, inner_max, ic.pred32, ic.rounds, ic.total, st);
+    if (!p.mixed) return inner_cg(v, p, inner_max, ic.pred, ic.total, st);
+    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, st);
     if (s != TB_ERR_BREAKDOWN && s != TB_ERR_NOT_CONVERGED) return s;
     // The FP32 corrections failed to converge (or produced a non-finite
     // residual): redo this inner solve with the FP64 CG, on the device.
@@ -282,7 +305,7 @@ tb_status inner_solve(tb_handle* h, const PanelDev& p, const double2* b, int inn
     int zero = 0;
     TB_CK(cudaMemcpyAsync(p.flags, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
     TB_CK(cudaMemcpyAsync(p.Rin, b, sizeof(double2) * (size_t)p.npad * p.P, cudaMemcpyDeviceToDevice, st));
-    s = inner_cg(h, p, inner_max, ic.pred, ic.total, st);
+    s = inner_cg(v, p, inner_max, ic.pred, ic.total, st);
     if (s != TB_OK) return s;
     launch_split_panel(p, st);
     TB_CK(cudaGetLastError());
@@ -290,10 +313,10 @@ tb_status inner_solve(tb_handle* h, const PanelDev& p, const double2* b, int inn
     return TB_OK;
 }
 
-tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
+tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
     const auto t0 = std::chrono::steady_clock::now();
     const int K = q.K, R = q.R;
-    const int npad = h->ds.npad;
+    const int npad = v.ds.npad;
     int P = o->panel ? o->panel : 64;
     P = std::min(P, next_pow2(R));
     if (q.proj == PROJ_NONE) {
@@ -403,15 +426,15 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
             cs.sc_prev = make_double2(1.0, 0.0);
             cs.seed = o->seed;
             cs.active = c < ncols ? 1 : 0;
-            cs.row = c < ncols ? h->orb2pad_h[q.cols[c0 + c]] : -1;
+            cs.row = c < ncols ? v.o2p_h[q.cols[c0 + c]] : -1;
             cs.nfun = q.proj == PROJ_ROWS && c < ncols ? (int)(q.row_ptr[c0 + c + 1] - q.row_ptr[c0 + c])
                                                        : (q.proj == PROJ_SROW ? 1 : 0);
             colh[c] = cs;
             if (q.proj == PROJ_ROWS) {
                 for (int m = 0; m < M; ++m) {
-                    int v = 0;
-                    if (c < ncols && m < cs.nfun) v = h->orb2pad_h[q.rows[q.row_ptr[c0 + c] + m]];
-                    frowh[(size_t)c * M + m] = v;
+                    int slot = 0;
+                    if (c < ncols && m < cs.nfun) slot = v.o2p_h[q.rows[q.row_ptr[c0 + c] + m]];
+                    frowh[(size_t)c * M + m] = slot;
                 }
             }
         }
@@ -426,31 +449,31 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
             TB_CK(cudaMemcpyAsync(p.frow, frowh.data(), sizeof(int32_t) * P * M, cudaMemcpyHostToDevice, st));
 
         // r_0 = e_j, r'_0 = S^-1 r_0, rho_0, pi = 1, x^k = 0, p^k = r'_0
-        launch_panel_init(h->ds, p, st);
-        if ((s = inner_solve(h, p, p.Rcur, o->inner_max_iter, ic, st)) != TB_OK) return s;
-        if (h->flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
-        launch_finish(h->ds, p, st);
-        launch_shift_init(h->ds, p, st);
+        launch_panel_init(v.ds, p, st);
+        if ((s = inner_solve(v, p, p.Rcur, o->inner_max_iter, ic, st)) != TB_OK) return s;
+        if (v.flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
+        launch_finish(v.ds, p, st);
+        launch_shift_init(v.ds, p, st);
         TB_CK(cudaGetLastError());
 
         int active = ncols;
         for (int n = 0; n < o->max_iter && active > 0; ++n) {
-            launch_outer_spmm(h->ds, p, st);
-            launch_outer_update(h->ds, p, st);
-            s = inner_solve(h, p, p.Rcur, o->inner_max_iter, ic, st);
+            launch_outer_spmm(v.ds, p, st);
+            launch_outer_update(v.ds, p, st);
+            s = inner_solve(v, p, p.Rcur, o->inner_max_iter, ic, st);
             if (s != TB_OK) return s;
-            active = h->flags_host[2];     // columns still active after step n-1
-            errbits |= h->flags_host[0];
+            active = v.flags_host[2];     // columns still active after step n-1
+            errbits |= v.flags_host[0];
             if (errbits & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
             if (active == 0) break;
-            launch_finish(h->ds, p, st);
-            launch_shift_step(h->ds, p, st);
-            if (q.proj == PROJ_NONE) launch_full_update(h->ds, p, st);
+            launch_finish(v.ds, p, st);
+            launch_shift_step(v.ds, p, st);
+            if (q.proj == PROJ_NONE) launch_full_update(v.ds, p, st);
             TB_CK(cudaGetLastError());
         }
         // outputs of this panel
         if (q.proj == PROJ_NONE)
-            launch_full_output(p, h->orb2pad, (int)h->n_orb, R, ncols, c0, q.x_out, st);
+            launch_full_output(p, v.o2p_d, (int)v.n_orb, R, ncols, c0, q.x_out, st);
         else if (q.proj == PROJ_ROWS)
             launch_green_output(p, ncols, off_dev + c0, q.g_out, st);
         else
@@ -458,9 +481,9 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         TB_CK(cudaGetLastError());
         TB_CK(cudaMemcpyAsync(colh.data(), p.col, sizeof(ColState) * P, cudaMemcpyDeviceToHost, st));
         TB_CK(cudaMemcpyAsync(convh.data(), p.conv_iter, sizeof(int32_t) * P * K, cudaMemcpyDeviceToHost, st));
-        TB_CK(cudaMemcpyAsync(h->flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
         TB_CK(cudaStreamSynchronize(st));
-        errbits |= h->flags_host[0];
+        errbits |= v.flags_host[0];
         for (int c = 0; c < ncols; ++c) {
             outer_total += colh[c].iters;
             max_col_iters = std::max<int64_t>(max_col_iters, colh[c].iters);
@@ -485,6 +508,176 @@ tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_sta
         stats->inner_redos = ic.redo;
     }
     return final_status;
+}
+
+// The whole handle as one view (a single system, or a batch seen as one
+// block-diagonal system).
+View whole_view(tb_handle* h) {
+    View v;
+    v.ds = h->ds;
+    v.o2p_h = h->orb2pad_h.data();
+    v.o2p_d = h->orb2pad;
+    v.n_orb = h->n_orb;
+    v.flags_host = h->flags_host;
+    return v;
+}
+
+// A ragged batch: the columns are grouped by system and every system is
+// solved on its own view (no work on the rows of the other systems), by up
+// to 8 host threads, each on its own stream, so that the systems' kernels
+// run concurrently.  Results land in temporary buffers and are scattered
+// into the caller's layout; entries that couple two systems are zero.
+tb_status run_batch(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int ns = (int)h->sys_ds.size();
+    const int K = q.K, R = q.R;
+    std::vector<std::vector<int>> members(ns);
+    for (int c = 0; c < R; ++c) {
+        const int sys = (int)(std::upper_bound(h->sys_orb_off.begin(), h->sys_orb_off.end(), (int64_t)q.cols[c]) -
+                              h->sys_orb_off.begin()) - 1;
+        members[sys].push_back(c);
+    }
+    if (q.proj == PROJ_NONE)
+        TB_CK(cudaMemsetAsync(q.x_out, 0, sizeof(double2) * (size_t)K * R * h->n_orb, st));
+    if (q.proj == PROJ_ROWS)
+        TB_CK(cudaMemsetAsync(q.g_out, 0, sizeof(double2) * (size_t)q.row_ptr[R] * K, st));
+    cudaEvent_t ev_in;
+    TB_CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    TB_CK(cudaEventRecord(ev_in, st));
+    std::vector<int> jobs;
+    for (int sys = 0; sys < ns; ++sys)
+        if (!members[sys].empty()) jobs.push_back(sys);
+    const int nw = std::min<int>((int)jobs.size(), 8);
+    std::atomic<int> next{0};
+    std::mutex mu;
+    tb_status worst = TB_OK;
+    bool unconverged = false;
+    tb_stats agg{};
+    auto worker = [&]() {
+        cudaSetDevice(h->device);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            std::lock_guard<std::mutex> lk(mu);
+            if (worst == TB_OK) worst = TB_ERR_CUDA;
+            return;
+        }
+        cudaStreamWaitEvent(ws, ev_in, 0);
+        for (int j = next++; j < (int)jobs.size(); j = next++) {
+            const int sys = jobs[j];
+            const std::vector<int>& mem = members[sys];
+            const int Rq = (int)mem.size();
+            const int64_t orb0 = h->sys_orb_off[sys], Nq = h->sys_orb_off[sys + 1] - orb0;
+            tb_status s = TB_OK;
+            {
+                Cleanup cl;
+                cl.st = ws;
+                View v;
+                v.ds = h->sys_ds[sys];
+                v.o2p_h = h->orb2pad_local_h.data() + orb0;
+                v.o2p_d = h->orb2pad_local + orb0;
+                v.n_orb = Nq;
+                v.flags_host = h->flags_host_sys + (size_t)NFLAGS * sys;
+                std::vector<int32_t> cols(Rq), pos(Rq);
+                for (int i = 0; i < Rq; ++i) {
+                    pos[i] = mem[i];
+                    cols[i] = (int32_t)(q.cols[mem[i]] - orb0);
+                }
+                Solve q2 = q;
+                q2.R = Rq;
+                q2.cols = cols.data();
+                std::vector<int64_t> rp2, gidx;
+                std::vector<int32_t> rows2;
+                int32_t* pos_d = nullptr;
+                if ((s = dalloc(cl, &pos_d, (size_t)Rq)) == TB_OK &&
+                    cudaMemcpyAsync(pos_d, pos.data(), sizeof(int32_t) * Rq, cudaMemcpyHostToDevice, ws) != cudaSuccess)
+                    s = TB_ERR_CUDA;
+                double2* xt = nullptr;
+                double2* gt = nullptr;
+                double* qt = nullptr;
+                int64_t* gidx_d = nullptr;
+                if (s == TB_OK && q.proj == PROJ_NONE) {
+                    s = dalloc(cl, &xt, (size_t)K * Rq * Nq);
+                    q2.x_out = xt;
+                } else if (s == TB_OK && q.proj == PROJ_ROWS) {
+                    // rows inside the column's system only; the others stay zero
+                    rp2.push_back(0);
+                    for (int i = 0; i < Rq; ++i) {
+                        const int c = mem[i];
+                        for (int64_t m = q.row_ptr[c]; m < q.row_ptr[c + 1]; ++m) {
+                            const int64_t r = q.rows[m];
+                            if (r >= orb0 && r < orb0 + Nq) {
+                                rows2.push_back((int32_t)(r - orb0));
+                                gidx.push_back(m);
+                            }
+                        }
+                        rp2.push_back((int64_t)rows2.size());
+                    }
+                    if (rows2.empty()) rows2.push_back(0);   // keep the arrays non-empty
+                    q2.row_ptr = rp2.data();
+                    q2.rows = rows2.data();
+                    if ((s = dalloc(cl, &gt, (size_t)std::max<int64_t>(1, rp2.back()) * K)) == TB_OK &&
+                        (s = dalloc(cl, &gidx_d, std::max<size_t>(1, gidx.size()))) == TB_OK && !gidx.empty() &&
+                        cudaMemcpyAsync(gidx_d, gidx.data(), sizeof(int64_t) * gidx.size(), cudaMemcpyHostToDevice,
+                                        ws) != cudaSuccess)
+                        s = TB_ERR_CUDA;
+                    q2.g_out = gt;
+                } else if (s == TB_OK) {
+                    s = dalloc(cl, &qt, (size_t)Rq);
+                    q2.q_out = qt;
+                }
+                tb_stats st2{};
+                std::vector<int32_t> conv;
+                if (stats && stats->conv_iter) {
+                    conv.assign((size_t)Rq * K, -1);
+                    st2.conv_iter = conv.data();
+                }
+                if (s == TB_OK) s = run_view(v, q2, o, &st2, ws);
+                if (s == TB_OK || s == TB_ERR_NOT_CONVERGED) {
+                    if (q.proj == PROJ_NONE)
+                        launch_scatter_full(xt, pos_d, K, Rq, Nq, R, h->n_orb, orb0, q.x_out, ws);
+                    else if (q.proj == PROJ_ROWS && !gidx.empty())
+                        launch_scatter_rows(gt, gidx_d, (int64_t)gidx.size(), K, q.g_out, ws);
+                    else if (q.proj == PROJ_SROW)
+                        launch_scatter_cols(qt, pos_d, Rq, q.q_out, ws);
+                    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ws) != cudaSuccess) s = TB_ERR_CUDA;
+                }
+                std::lock_guard<std::mutex> lk(mu);
+                if (s == TB_ERR_NOT_CONVERGED) unconverged = true;
+                else if (s != TB_OK && worst == TB_OK) worst = s;
+                agg.outer_iterations += st2.outer_iterations;
+                agg.inner_iterations += st2.inner_iterations;
+                agg.max_column_iterations = std::max(agg.max_column_iterations, st2.max_column_iterations);
+                agg.switches += st2.switches;
+                agg.unconverged += st2.unconverged;
+                agg.inner_redos += st2.inner_redos;
+                if (stats && stats->conv_iter)
+                    for (int i = 0; i < Rq; ++i)
+                        for (int k = 0; k < K; ++k) stats->conv_iter[(size_t)pos[i] * K + k] = conv[(size_t)i * K + k];
+            }
+            cudaStreamSynchronize(ws);   // the view's temporaries are freed in stream order
+        }
+        cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+    cudaEventDestroy(ev_in);
+    if (stats) {
+        int32_t* ci = stats->conv_iter;
+        *stats = agg;
+        stats->conv_iter = ci;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (worst != TB_OK) return worst;
+    return unconverged ? TB_ERR_NOT_CONVERGED : TB_OK;
+}
+
+tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
+    if (!h->sys_ds.empty()) return run_batch(h, q, o, stats, st);
+    View v = whole_view(h);
+    return run_view(v, q, o, stats, st);
 }
 
 tb_status check_cols(const tb_handle* h, int R, const int32_t* cols) {
@@ -711,6 +904,9 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->eps_pad);
     cudaFree(h->atom_orb_off);
     cudaFree(h->H0);
+    cudaFree(h->orb2pad_local);
+    cudaFree(h->bcol_local);
+    if (h->flags_host_sys) cudaFreeHost(h->flags_host_sys);
     if (h->flags_host) cudaFreeHost(h->flags_host);
     delete h;
     return TB_OK;
@@ -885,7 +1081,113 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     launch_split_f64(h->ds.H, h->ds.H32hi, h->ds.H32lo, 16 * (long long)nb, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    h->sys_atom_off = {0, (int64_t)n};
+    h->sys_orb_off = {0, N};
     *out = h;
+    return TB_OK;
+}
+
+tb_status tb_create_batch(tb_handle** out, const tb_system_desc* descs, int32_t n_systems, void* stream) {
+    if (!out) return TB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!descs || n_systems < 1) return TB_ERR_INVALID_ARG;
+    const bool h_given = descs[0].H_vals != nullptr;
+    std::vector<int32_t> opa;
+    std::vector<int64_t> brow{0};
+    std::vector<int32_t> bcol;
+    std::vector<double> S, H, eps;
+    std::vector<int64_t> aoff{0}, ooff{0};
+    for (int q = 0; q < n_systems; ++q) {
+        const tb_system_desc& d = descs[q];
+        if (d.n_atoms < 1 || !d.orb_per_atom || !d.brow_ptr || !d.bcol || !d.S_vals) return TB_ERR_INVALID_ARG;
+        if ((d.H_vals != nullptr) != h_given || d.precision != TB_FP64) return TB_ERR_INVALID_ARG;
+        if (!h_given && (!d.eps || !(d.K == descs[0].K))) return TB_ERR_INVALID_ARG;
+        const int n = d.n_atoms;
+        const int64_t a0 = aoff.back();
+        if (a0 + n > (int64_t)1 << 28) return TB_ERR_INVALID_ARG;
+        // structure checks needed to size the value arrays; tb_create checks the rest
+        if (d.brow_ptr[0] != 0) return TB_ERR_INVALID_ARG;
+        int64_t N = 0;
+        for (int i = 0; i < n; ++i) {
+            if (d.orb_per_atom[i] != 1 && d.orb_per_atom[i] != 4) return TB_ERR_INVALID_ARG;
+            if (d.brow_ptr[i + 1] < d.brow_ptr[i]) return TB_ERR_INVALID_ARG;
+            N += d.orb_per_atom[i];
+        }
+        int64_t nval = 0;
+        for (int i = 0; i < n; ++i)
+            for (int64_t b = d.brow_ptr[i]; b < d.brow_ptr[i + 1]; ++b) {
+                const int j = d.bcol[b];
+                if (j < 0 || j >= n) return TB_ERR_INVALID_ARG;
+                nval += (int64_t)d.orb_per_atom[i] * d.orb_per_atom[j];
+            }
+        opa.insert(opa.end(), d.orb_per_atom, d.orb_per_atom + n);
+        const int64_t b0 = brow.back();
+        for (int i = 1; i <= n; ++i) brow.push_back(b0 + d.brow_ptr[i]);
+        for (int64_t b = 0; b < d.brow_ptr[n]; ++b) bcol.push_back((int32_t)(a0 + d.bcol[b]));
+        S.insert(S.end(), d.S_vals, d.S_vals + nval);
+        if (h_given) H.insert(H.end(), d.H_vals, d.H_vals + nval);
+        else eps.insert(eps.end(), d.eps, d.eps + N);
+        aoff.push_back(a0 + n);
+        ooff.push_back(ooff.back() + N);
+    }
+    tb_system_desc m{};
+    m.n_atoms = (int32_t)aoff.back();
+    m.orb_per_atom = opa.data();
+    m.brow_ptr = brow.data();
+    m.bcol = bcol.data();
+    m.S_vals = S.data();
+    m.H_vals = h_given ? H.data() : nullptr;
+    m.eps = h_given ? nullptr : eps.data();
+    m.K = descs[0].K;
+    m.precision = TB_FP64;
+    const tb_status s = tb_create(out, &m, stream);
+    if (s != TB_OK) return s;
+    tb_handle* h = *out;
+    h->sys_atom_off = aoff;
+    h->sys_orb_off = ooff;
+    if (n_systems == 1) return TB_OK;
+    // per-system views: local block columns and padded slots
+    std::vector<int32_t> bl(bcol.size());
+    for (int q = 0; q < n_systems; ++q)
+        for (int64_t b = brow[aoff[q]]; b < brow[aoff[q + 1]]; ++b) bl[b] = bcol[b] - (int32_t)aoff[q];
+    h->orb2pad_local_h.resize(ooff.back());
+    for (int q = 0; q < n_systems; ++q)
+        for (int64_t o = ooff[q]; o < ooff[q + 1]; ++o)
+            h->orb2pad_local_h[o] = h->orb2pad_h[o] - 4 * (int32_t)aoff[q];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto fail = [&](cudaError_t e) {
+        cudaGetLastError();
+        tb_destroy(h);
+        *out = nullptr;
+        return e == cudaErrorMemoryAllocation ? TB_ERR_OOM : TB_ERR_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->bcol_local, sizeof(int32_t) * bl.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->orb2pad_local, sizeof(int32_t) * ooff.back())) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost(&h->flags_host_sys, sizeof(int) * NFLAGS * n_systems)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->bcol_local, bl.data(), sizeof(int32_t) * bl.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h->orb2pad_local, h->orb2pad_local_h.data(), sizeof(int32_t) * ooff.back(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    for (int q = 0; q < n_systems; ++q) {
+        DevSystem v = h->ds;
+        v.n_atoms = (int)(aoff[q + 1] - aoff[q]);
+        v.npad = 4 * v.n_atoms;
+        v.nb = brow[aoff[q + 1]] - brow[aoff[q]];
+        v.brow = h->ds.brow + aoff[q];
+        v.bcol = h->bcol_local;
+        v.grpG = 0;                 // the grouped SpMV's atom groups are built for the whole handle
+        h->sys_ds.push_back(v);
+    }
+    return TB_OK;
+}
+
+int32_t tb_num_systems(const tb_handle* h) { return h ? (int32_t)h->sys_atom_off.size() - 1 : 0; }
+
+tb_status tb_batch_offsets(const tb_handle* h, int64_t* atom_off, int64_t* orb_off) {
+    if (!h) return TB_ERR_INVALID_ARG;
+    if (atom_off) std::memcpy(atom_off, h->sys_atom_off.data(), sizeof(int64_t) * h->sys_atom_off.size());
+    if (orb_off) std::memcpy(orb_off, h->sys_orb_off.data(), sizeof(int64_t) * h->sys_orb_off.size());
     return TB_OK;
 }
 
@@ -1145,14 +1447,15 @@ tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, doubl
     int pred = 64;
     int64_t inner_total = 0;
     const int inner_max = 1000;
+    View hv = whole_view(h);
     launch_panel_init(h->ds, p, st);
-    if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
+    if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
     launch_lz_start(p, p.Rp, cs.row, U, nd, st);
     for (int n = 0; n < n_steps; ++n) {
         launch_lz_spmv(h->ds, h->ds.H, U, p.W, st);                  // H u^n
         launch_lz_dot(p, U, p.W, ad + n, 0, st);                     // a_n = u^T H u
         TB_CK(cudaMemcpyAsync(p.Rin, p.W, sizeof(double2) * npad, cudaMemcpyDeviceToDevice, st));
-        if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;   // S^-1 H u^n
+        if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;   // S^-1 H u^n
         launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, st);  // w = S^-1 H u - a u - b u_prev
         launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, st);                 // S w
         launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, st);                // b_{n+1} = ||w||_S
@@ -1273,14 +1576,15 @@ tb_status tb_generalized_lanczos_noalloc(tb_handle* h, int32_t j, int32_t n_step
     int pred = 64;
     int64_t inner_total = 0;
     const int inner_max = 1000;
+    View hv = whole_view(h);
     launch_panel_init(h->ds, p, st);
-    if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
+    if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
     launch_lz_start(p, p.Rp, cs.row, U, nd, st);
     for (int n = 0; n < n_steps; ++n) {
         launch_lz_spmv(h->ds, h->ds.H, U, p.W, st);
         launch_lz_dot(p, U, p.W, ad + n, 0, st);
         TB_CK(cudaMemcpyAsync(p.Rin, p.W, sizeof(double2) * npad, cudaMemcpyDeviceToDevice, st));
-        if ((s = inner_cg(h, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
+        if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
         launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, st);
         launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, st);
         launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, st);

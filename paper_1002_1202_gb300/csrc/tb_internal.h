@@ -157,6 +157,12 @@ void launch_green_output(const PanelDev& p, int ncols, const int64_t* out_off, d
 void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
                             cudaStream_t st);
 
+// ragged batches: results of one system's solve into the caller's layout
+void launch_scatter_full(const double2* tmp, const int32_t* pos, int K, int Rq, int64_t Nq, int R, int64_t N,
+                         int64_t orb0, double2* out, cudaStream_t st);
+void launch_scatter_rows(const double2* tmp, const int64_t* gidx, int64_t n, int K, double2* out, cudaStream_t st);
+void launch_scatter_cols(const double* tmp, const int32_t* pos, int Rq, double* out, cudaStream_t st);
+
 // charge self-consistency (Eq. Hap-CSC)
 void launch_csc_potential(const double* gamma, const double* dq, int n, double* V, cudaStream_t st);
 void launch_csc_hamiltonian(const DevSystem& s, const double* H0, const double* V, cudaStream_t st);

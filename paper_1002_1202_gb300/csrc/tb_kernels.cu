@@ -17,6 +17,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 #include <cstdlib>
 #include <vector>
@@ -1542,6 +1544,41 @@ __global__ void k_lanczos_green(const double* __restrict__ a, const double* __re
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Ragged batches: scatter one system's results into the caller's layout
+// ---------------------------------------------------------------------------
+
+// out[k][pos[c]][orb0 + o] = tmp[k][c][o]   (full solutions, [K][R][N])
+__global__ void k_scatter_full(const double2* __restrict__ tmp, const int32_t* __restrict__ pos, int K, int Rq,
+                               int64_t Nq, int R, int64_t N, int64_t orb0, double2* __restrict__ out) {
+    const long long total = (long long)K * Rq * Nq;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long o = i % Nq;
+        const long long kc = i / Nq;
+        const int c = (int)(kc % Rq), k = (int)(kc / Rq);
+        out[((long long)k * R + pos[c]) * N + orb0 + o] = tmp[i];
+    }
+}
+
+// out[gidx[e] * K + k] = tmp[e * K + k]   (Green's function elements)
+__global__ void k_scatter_rows(const double2* __restrict__ tmp, const int64_t* __restrict__ gidx, int64_t n, int K,
+                               double2* __restrict__ out) {
+    const long long total = n * (long long)K;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long e = i / K;
+        out[gidx[e] * K + (i - e * K)] = tmp[i];
+    }
+}
+
+// out[pos[c]] = tmp[c]   (one value per column)
+__global__ void k_scatter_cols(const double* __restrict__ tmp, const int32_t* __restrict__ pos, int Rq,
+                               double* __restrict__ out) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < Rq; c += gridDim.x * blockDim.x) out[pos[c]] = tmp[c];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1550,13 +1587,17 @@ __global__ void k_lanczos_green(const double* __restrict__ a, const double* __re
 // ---------------------------------------------------------------------------
 namespace {
 struct Profiler {
+    // launch counts are atomics; the event pairs of the profiling mode and
+    // the accumulated times are guarded by mu (host threads of a ragged
+    // batch launch concurrently)
+    std::mutex mu;
     bool on = false;
     std::vector<cudaEvent_t> ev;      // start/stop pairs
     std::vector<int> kid;             // kernel id of each pair in use
     size_t used = 0;
-    int64_t launches[K_COUNT] = {};
+    std::atomic<int64_t> launches[K_COUNT] = {};
     double ms[K_COUNT] = {};
-    int64_t total = 0;
+    std::atomic<int64_t> total{0};
 };
 Profiler g_prof;
 
@@ -1564,9 +1605,10 @@ struct LaunchScope {
     cudaStream_t st;
     size_t pair = (size_t)-1;
     LaunchScope(int id, cudaStream_t s) : st(s) {
-        ++g_prof.total;
-        ++g_prof.launches[id];
+        g_prof.total.fetch_add(1, std::memory_order_relaxed);
+        g_prof.launches[id].fetch_add(1, std::memory_order_relaxed);
         if (!g_prof.on) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
         if (2 * g_prof.used + 2 > g_prof.ev.size()) {
             for (int i = 0; i < 2; ++i) {
                 cudaEvent_t e;
@@ -1580,21 +1622,13 @@ struct LaunchScope {
         cudaEventRecord(g_prof.ev[2 * pair], st);
     }
     ~LaunchScope() {
-        if (pair != (size_t)-1) cudaEventRecord(g_prof.ev[2 * pair + 1], st);
+        if (pair == (size_t)-1) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        cudaEventRecord(g_prof.ev[2 * pair + 1], st);
     }
 };
-}  // namespace
 
-void profile_enable(bool on) {
-    prof_harvest();
-    g_prof.on = on;
-    for (int i = 0; i < K_COUNT; ++i) {
-        g_prof.launches[i] = 0;
-        g_prof.ms[i] = 0.0;
-    }
-}
-
-void prof_harvest() {
+void harvest_locked() {
     for (size_t i = 0; i < g_prof.used; ++i) {
         float t = 0.f;
         cudaEventSynchronize(g_prof.ev[2 * i + 1]);
@@ -1605,9 +1639,27 @@ void prof_harvest() {
     }
     g_prof.used = 0;
 }
+}  // namespace
+
+void profile_enable(bool on) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    harvest_locked();
+    g_prof.on = on;
+    for (int i = 0; i < K_COUNT; ++i) {
+        g_prof.launches[i] = 0;
+        g_prof.ms[i] = 0.0;
+    }
+}
+
+void prof_harvest() {
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    harvest_locked();
+}
 
 void profile_read(int id, int64_t* launches, double* ms) {
-    prof_harvest();
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    harvest_locked();
     *launches = g_prof.launches[id];
     *ms = g_prof.ms[id];
 }
@@ -1617,15 +1669,26 @@ int64_t launch_count() { return g_prof.total; }
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static int g_gmax = 0;
 static int gmax() {
-    if (g_gmax == 0) {
+    static const int g = [] {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g_gmax = 4 * (sms > 0 ? sms : 1);
-    }
-    return g_gmax;
+        return 4 * (sms > 0 ? sms : 1);
+    }();
+    return g;
+}
+
+// Raise (never lower) a kernel's dynamic shared-memory limit: threads of a
+// ragged batch may launch the same kernel with different sizes at once.
+static bool ensure_dyn_smem(const void* kernel, size_t bytes, size_t& current) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (bytes <= current) return true;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return false;
+    current = bytes;
+    return true;
 }
 int max_grid() { return gmax(); }
 
@@ -1717,17 +1780,16 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
     // register-gather form with its higher occupancy is faster
     if (s.grpG > 0 && p.P >= PC && p.P <= 64) {
         const size_t sm = inner32_grp_smem(s);
-        static bool attr = false;
-        if (!attr) {
+        static const bool attr = [] {
             // the dynamic limit leaves room for the kernel's static shared memory
             cudaFuncAttributes fa;
-            if (cudaFuncGetAttributes(&fa, k_inner32_spmv_grp) == cudaSuccess &&
-                cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     227 * 1024 - (int)fa.sharedSizeBytes) == cudaSuccess &&
-                cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
-                    cudaSuccess)
-                attr = true;
-        }
+            return cudaFuncGetAttributes(&fa, k_inner32_spmv_grp) == cudaSuccess &&
+                   cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024 - (int)fa.sharedSizeBytes) == cudaSuccess &&
+                   cudaFuncSetAttribute(k_inner32_spmv_grp, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+                       cudaSuccess;
+        }();
+        (void)attr;
         k_inner32_spmv_grp<<<s.n_groups * (p.P / PC), s.grpG * (PC / 2), sm, st>>>(s, p, it);
     } else if (p.P >= 2)
         k_inner32_spmv<2><<<grid_for((long long)s.n_atoms * (p.P / 2)), THREADS, 0, st>>>(s, p, it);
@@ -1744,7 +1806,8 @@ void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStre
 static size_t shift_smem(const PanelDev& p) { return sizeof(double2) * ((size_t)(p.M > 0 ? p.M : 1) + 3 * (size_t)p.K); }
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     const size_t sm = shift_smem(p);
-    cudaFuncSetAttribute(k_shift_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static size_t lim_init = 48 * 1024;
+    ensure_dyn_smem((const void*)k_shift_init, sm, lim_init);
     {
         LaunchScope ls_(K_OTHER, st);
         k_shift_init<<<p.P, THREADS, sm, st>>>(s, p);
@@ -1756,7 +1819,8 @@ void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
 }
 void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     const size_t sm = shift_smem(p);
-    cudaFuncSetAttribute(k_shift_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static size_t lim_step = 48 * 1024;
+    ensure_dyn_smem((const void*)k_shift_step, sm, lim_step);
     {
         LaunchScope ls_(K_SHIFT_STEP, st);
         k_shift_step<<<p.P, THREADS, sm, st>>>(s, p);
@@ -1848,6 +1912,23 @@ void launch_lanczos_green(const double* a, const double* b, double norm, int n_s
                           double2* G, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
     k_lanczos_green<<<grid_for(K), THREADS, 0, st>>>(a, b, norm, n_steps, K, z, G);
+}
+
+
+void launch_scatter_full(const double2* tmp, const int32_t* pos, int K, int Rq, int64_t Nq, int R, int64_t N,
+                         int64_t orb0, double2* out, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_scatter_full<<<grid_for((long long)K * Rq * Nq), THREADS, 0, st>>>(tmp, pos, K, Rq, Nq, R, N, orb0, out);
+}
+
+void launch_scatter_rows(const double2* tmp, const int64_t* gidx, int64_t n, int K, double2* out, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_scatter_rows<<<grid_for(n * (long long)K), THREADS, 0, st>>>(tmp, gidx, n, K, out);
+}
+
+void launch_scatter_cols(const double* tmp, const int32_t* pos, int Rq, double* out, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_scatter_cols<<<grid_for(Rq), THREADS, 0, st>>>(tmp, pos, Rq, out);
 }
 
 }  // namespace tb

@@ -102,6 +102,9 @@ _I64P = C.POINTER(C.c_int64)
 SIGNATURES = [
     ("tb_create", C.c_int, [C.POINTER(_VP), C.POINTER(SystemDesc), _VP]),
     ("tb_destroy", C.c_int, [_VP]),
+    ("tb_create_batch", C.c_int, [C.POINTER(_VP), C.POINTER(SystemDesc), C.c_int32, _VP]),
+    ("tb_num_systems", C.c_int32, [_VP]),
+    ("tb_batch_offsets", C.c_int, [_VP, _I64P, _I64P]),
     ("tb_num_orbitals", C.c_int64, [_VP]),
     ("tb_num_atoms", C.c_int64, [_VP]),
     ("tb_num_blocks", C.c_int64, [_VP]),
@@ -243,6 +246,40 @@ def tb_create(orb_per_atom, brow_ptr, bcol, S_vals, H_vals=None, eps=None, K=1.7
     h = C.c_void_p()
     _check(lib.tb_create(C.byref(h), C.byref(d), _stream(stream)), "tb_create", False)
     return Handle(h, int(lib.tb_num_orbitals(h)), int(lib.tb_num_atoms(h)), int(lib.tb_num_blocks(h)))
+
+
+def tb_create_batch(systems, stream=None) -> Handle:
+    """tb_create_batch from a list of ``tbinputs.TBSystem`` (H by Eq. Hap-1;
+    all K equal).  The handle gets ``atom_off`` and ``orb_off`` (numpy int64
+    [n_systems + 1]): the first atom and orbital of every system."""
+    lib = load_library()
+    keep = []
+    descs = (SystemDesc * len(systems))()
+    for d, so in zip(descs, systems):
+        arrs = [np.ascontiguousarray(so.orb_per_atom, dtype=np.int32),
+                np.ascontiguousarray(so.brow_ptr, dtype=np.int64),
+                np.ascontiguousarray(so.bcol, dtype=np.int32),
+                np.ascontiguousarray(so.S_vals, dtype=np.float64),
+                np.ascontiguousarray(so.eps, dtype=np.float64)]
+        keep.append(arrs)
+        d.n_atoms = len(arrs[0])
+        d.orb_per_atom = _ptr(arrs[0], C.c_int32)
+        d.brow_ptr = _ptr(arrs[1], C.c_int64)
+        d.bcol = _ptr(arrs[2], C.c_int32)
+        d.S_vals = _ptr(arrs[3], C.c_double)
+        d.H_vals = None
+        d.eps = _ptr(arrs[4], C.c_double)
+        d.K = float(so.K)
+        d.precision = TB_FP64
+    h = C.c_void_p()
+    _check(lib.tb_create_batch(C.byref(h), descs, len(systems), _stream(stream)), "tb_create_batch", False)
+    out = Handle(h, int(lib.tb_num_orbitals(h)), int(lib.tb_num_atoms(h)), int(lib.tb_num_blocks(h)))
+    ns = int(lib.tb_num_systems(h))
+    out.atom_off = np.zeros(ns + 1, dtype=np.int64)
+    out.orb_off = np.zeros(ns + 1, dtype=np.int64)
+    _check(lib.tb_batch_offsets(h, _ptr(out.atom_off, C.c_int64), _ptr(out.orb_off, C.c_int64)),
+           "tb_batch_offsets", False)
+    return out
 
 
 def tb_create_system(sysobj, explicit_H=None, stream=None) -> Handle:

@@ -146,3 +146,19 @@ def test_csc_defaults_and_null_arguments(lib):
     assert lib.tb_csc_hamiltonian(None, None, None, None) == 1
     assert lib.tb_csc_loop(None, 1, zp, zp, 2.0, None, None, None, C.byref(o), C.byref(so), None, None,
                            C.byref(st), None) == 1
+
+
+def test_batch_validation(lib, si):
+    """tb_create_batch checks every system as tb_create does and rejects
+    batches that mix explicit and ASED Hamiltonians or ASED constants."""
+    import dataclasses
+    import torch
+    from paper_1002_1202_gb300 import tb
+    other_K = dataclasses.replace(si, K=si.K + 0.5)
+    assert _status(lambda: tb.tb_create_batch([si, other_K], stream=0)) == 1
+    bad = dataclasses.replace(si, bcol=si.bcol.copy())
+    bad.bcol[3] = si.n_atoms + 1
+    assert _status(lambda: tb.tb_create_batch([si, bad], stream=0)) == 1
+    assert _status(lambda: tb.tb_create_batch([], stream=0)) == 1
+    if not torch.cuda.is_available():
+        assert _status(lambda: tb.tb_create_batch([si, si], stream=0)) == 9

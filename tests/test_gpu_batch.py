@@ -1,0 +1,109 @@
+"""Ragged batches (block-diagonal handle of independent systems) on the GPU:
+a batch solve gives the per-system solves, columns of different systems
+share panels, and nothing leaks across systems."""
+import numpy as np
+import pytest
+
+from tbinputs import water_system, si_system, gauss_legendre_grid
+from oracle import dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_1202_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def systems():
+    return [water_system(8, seed=4, cutoff=3.0, excess_proton=False),
+            si_system((2, 2, 2), sigma=0.05, seed=1),
+            water_system(16, seed=7, cutoff=3.0)]
+
+
+@pytest.fixture(scope="module")
+def grid():
+    return gauss_legendre_grid(32, -40.0, 0.0, 1.0)
+
+
+def test_batch_offsets(P, systems):
+    h = P.tb_create_batch(systems)
+    assert list(h.atom_off) == list(np.cumsum([0] + [s.n_atoms for s in systems]))
+    assert list(h.orb_off) == list(np.cumsum([0] + [s.n_orb for s in systems]))
+    assert h.n_orb == sum(s.n_orb for s in systems)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_batch_charges_equal_per_system(P, systems, grid, prec):
+    z, w = grid
+    opts = P.tb_default_opts(precision=prec)
+    hb = P.tb_create_batch(systems)
+    qb, st = P.tb_mulliken_charges(hb, z, w, opts=opts)
+    qb = qb.cpu().numpy()
+    for i, s in enumerate(systems):
+        q, _ = P.tb_mulliken_charges(P.tb_create_system(s), z, w, opts=opts)
+        assert np.abs(qb[hb.atom_off[i]:hb.atom_off[i + 1]] - q.cpu().numpy()).max() <= 1e-9
+    # one system against the dense definition
+    s = systems[0]
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    ref = dense.mulliken_atom(dense.mulliken_orbital(H, S, z, w), s.orbital_atom(), s.n_atoms)
+    assert np.abs(qb[:s.n_atoms] - ref).max() <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_batch_columns_stay_in_their_system(P, systems, grid, prec):
+    z, w = grid
+    z = z[::4]
+    hb = P.tb_create_batch(systems)
+    picks = [(0, 3), (1, 0), (1, 200), (2, 5), (0, 40)]
+    cols = [int(hb.orb_off[i] + j) for i, j in picks]
+    opts = P.tb_default_opts(precision=prec)
+    x, st = P.tb_shifted_cocg(hb, z, cols, opts=opts)
+    X = x.cpu().numpy()
+    for c, (i, j) in enumerate(picks):
+        lo, hi = hb.orb_off[i], hb.orb_off[i + 1]
+        outside = np.concatenate([X[:, c, :lo], X[:, c, hi:]], axis=1)
+        assert np.all(outside == 0)
+        xs, _ = P.tb_shifted_cocg(P.tb_create_system(systems[i]), z, [j], opts=opts)
+        ref = xs.cpu().numpy()[:, 0]
+        assert np.abs(X[:, c, lo:hi] - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_batch_green_elements_and_stats(P, systems, grid):
+    z, w = grid
+    z = z[::4]
+    hb = P.tb_create_batch(systems)
+    o1 = int(hb.orb_off[1])
+    cols = [2, o1 + 7, o1 + 100]
+    # rows of the column's own system and of another system (those are zero)
+    rows_per_col = [[2, 5, o1 + 3], [o1 + 7, o1 + 9, 4], [o1 + 100, int(hb.orb_off[2]) + 1]]
+    row_ptr = np.cumsum([0] + [len(r) for r in rows_per_col])
+    rows = [r for rr in rows_per_col for r in rr]
+    G, st = P.tb_green_elements(hb, z, cols, row_ptr, rows)
+    G = G.cpu().numpy()
+    x, st2 = P.tb_shifted_cocg(hb, z, cols)
+    X = x.cpu().numpy()
+    for c in range(len(cols)):
+        for m in range(row_ptr[c], row_ptr[c + 1]):
+            r = rows[m]
+            same = np.searchsorted(hb.orb_off, r, side="right") == np.searchsorted(hb.orb_off, cols[c], side="right")
+            if same:
+                assert np.abs(G[m] - X[:, c, r]).max() <= 1e-10 * np.abs(X[:, c]).max()
+            else:
+                assert np.all(G[m] == 0)
+    assert st["outer_iterations"] > 0 and st["status"] == "TB_OK"
+    # per-(column, shift) convergence steps come back in the caller's column order
+    conv = np.asarray(st2["conv_iter"]).reshape(len(cols), len(z))
+    assert np.all(conv >= 0)
+    for c, j in enumerate(cols):
+        sys = int(np.searchsorted(hb.orb_off, j, side="right")) - 1
+        _, sts = P.tb_shifted_cocg(P.tb_create_system(systems[sys]), z, [j - int(hb.orb_off[sys])])
+        # same recurrences; rounding order differs with the panel width (+-1 step)
+        assert np.abs(conv[c] - np.asarray(sts["conv_iter"]).reshape(1, len(z))[0]).max() <= 1
