@@ -328,8 +328,8 @@ tb_status tb_generalized_lanczos_noalloc(tb_handle *h, int32_t j, int32_t n_step
  * tb_profile_enable(0) stops it.  tb_profile_read waits for the recorded
  * events and returns, for one kernel class TB_K_*, the launches counted since
  * the last reset and their summed device time in milliseconds (0 ms while
- * profiling is off).  Not thread-safe; intended for a single benchmarking
- * thread.
+ * profiling is off).  Counting is thread-safe (the library's own worker
+ * threads launch concurrently); enable, read and reset from one thread.
  */
 enum {
     TB_K_INNER_SPMV = 0,   /* w = S r and the inner-CG dot products        */
@@ -351,6 +351,10 @@ enum {
 int64_t tb_launch_count(void);
 void tb_profile_enable(int32_t enable);
 tb_status tb_profile_read(int32_t kernel, int64_t *launches, double *total_ms);
+/* Busy time (ms) of a kernel class since profiling was enabled: the union
+ * of its launch intervals, so overlapping launches on several streams (two
+ * panels in flight, ragged batches) count once.  0 without profiling. */
+tb_status tb_profile_busy(int32_t kernel, double *busy_ms);
 
 /* Static string naming a status code. */
 const char *tb_status_string(tb_status s);

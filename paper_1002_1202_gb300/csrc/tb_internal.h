@@ -13,6 +13,7 @@ constexpr int MAX_K = 1024;    // shifts per call
 constexpr int MAX_M = 1024;    // projected rows per column
 
 constexpr int NFLAGS = 8;      // device status words of a panel (see PanelDev::flags)
+constexpr int NPOOL = 8;       // host worker threads of one call, at most
 constexpr int RED_GROUP = 32;  // CTAs per first-level group of the grid reductions
 constexpr int MAX_GROUPS = 64; // upper bound on first-level groups (grids <= 2048 CTAs)
 constexpr int HIST_IT = 64;    // FP32 CG iterations kept by the trace history
@@ -129,6 +130,7 @@ enum { K_INNER_SPMV = 0, K_INNER_UPDATE, K_OUTER_SPMM, K_OUTER_UPDATE, K_FINISH,
 void profile_enable(bool on);
 void prof_harvest();
 void profile_read(int id, int64_t* launches, double* ms);
+double profile_busy(int id);
 int64_t launch_count();
 
 // ---- launchers (tb_kernels.cu) -------------------------------------------

@@ -1598,6 +1598,11 @@ struct Profiler {
     std::atomic<int64_t> launches[K_COUNT] = {};
     double ms[K_COUNT] = {};
     std::atomic<int64_t> total{0};
+    // launch intervals (ms after the reference event) per kernel class, for
+    // the busy time when launches of several streams overlap
+    cudaEvent_t ref = nullptr;
+    bool ref_set = false;
+    std::vector<std::pair<double, double>> iv[K_COUNT];
 };
 Profiler g_prof;
 
@@ -1630,10 +1635,15 @@ struct LaunchScope {
 
 void harvest_locked() {
     for (size_t i = 0; i < g_prof.used; ++i) {
-        float t = 0.f;
+        float t = 0.f, a = 0.f, b = 0.f;
         cudaEventSynchronize(g_prof.ev[2 * i + 1]);
         if (cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) == cudaSuccess)
             g_prof.ms[g_prof.kid[i]] += t;
+        else
+            cudaGetLastError();
+        if (g_prof.ref_set && cudaEventElapsedTime(&a, g_prof.ref, g_prof.ev[2 * i]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, g_prof.ref, g_prof.ev[2 * i + 1]) == cudaSuccess)
+            g_prof.iv[g_prof.kid[i]].push_back({(double)a, (double)b});
         else
             cudaGetLastError();
     }
@@ -1648,7 +1658,36 @@ void profile_enable(bool on) {
     for (int i = 0; i < K_COUNT; ++i) {
         g_prof.launches[i] = 0;
         g_prof.ms[i] = 0.0;
+        g_prof.iv[i].clear();
     }
+    g_prof.ref_set = false;
+    if (on) {
+        if (!g_prof.ref && cudaEventCreate(&g_prof.ref) != cudaSuccess) {
+            cudaGetLastError();
+            g_prof.ref = nullptr;
+        }
+        if (g_prof.ref && cudaEventRecord(g_prof.ref, 0) == cudaSuccess) g_prof.ref_set = true;
+        else cudaGetLastError();
+    }
+}
+
+double profile_busy(int id) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    harvest_locked();
+    std::vector<std::pair<double, double>> v = g_prof.iv[id];
+    std::sort(v.begin(), v.end());
+    double busy = 0.0, lo = 0.0, hi = -1.0;
+    for (const auto& x : v) {
+        if (x.first > hi) {
+            if (hi > lo) busy += hi - lo;
+            lo = x.first;
+            hi = x.second;
+        } else if (x.second > hi) {
+            hi = x.second;
+        }
+    }
+    if (hi > lo) busy += hi - lo;
+    return busy;
 }
 
 void prof_harvest() {

@@ -128,6 +128,7 @@ SIGNATURES = [
     ("tb_launch_count", C.c_int64, []),
     ("tb_profile_enable", None, [C.c_int32]),
     ("tb_profile_read", C.c_int, [C.c_int32, _I64P, _DP]),
+    ("tb_profile_busy", C.c_int, [C.c_int32, _DP]),
 ]
 
 KERNELS = {"inner_spmv": 0, "inner_update": 1, "outer_spmm": 2, "outer_update": 3, "finish": 4,
@@ -493,6 +494,15 @@ def tb_launch_count() -> int:
 
 def tb_profile_enable(enable: bool = True) -> None:
     load_library().tb_profile_enable(1 if enable else 0)
+
+
+def tb_profile_busy(kernel) -> float:
+    """Busy milliseconds of a kernel class: the union of its launch
+    intervals over all streams since profiling was enabled."""
+    kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    ms = C.c_double()
+    _check(load_library().tb_profile_busy(kid, C.byref(ms)), "tb_profile_busy", False)
+    return ms.value
 
 
 def tb_profile_read(kernel) -> tuple:
