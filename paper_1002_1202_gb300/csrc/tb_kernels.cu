@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <thread>
 #include <type_traits>
 #include <cstdlib>
 #include <vector>
@@ -1588,13 +1589,18 @@ __global__ void k_scatter_cols(const double* __restrict__ tmp, const int32_t* __
 namespace {
 struct Profiler {
     // launch counts are atomics; the event pairs of the profiling mode and
-    // the accumulated times are guarded by mu (host threads of a ragged
-    // batch launch concurrently)
+    // the accumulated times are guarded by mu (host threads of one call
+    // launch concurrently).  A pair is reused only after its stop event was
+    // recorded and harvested; a thread's own harvest (after it synchronised
+    // its stream) takes only the pairs it recorded, so it never waits for or
+    // reads another thread's pairs in flight.
     std::mutex mu;
     bool on = false;
-    std::vector<cudaEvent_t> ev;      // start/stop pairs
-    std::vector<int> kid;             // kernel id of each pair in use
-    size_t used = 0;
+    std::vector<cudaEvent_t> ev;          // start/stop pairs
+    std::vector<int> kid;                 // kernel id of each pair
+    std::vector<std::thread::id> owner;   // thread that recorded the pair
+    std::vector<size_t> free_pairs;
+    std::vector<size_t> stopped;          // recorded, not yet harvested
     std::atomic<int64_t> launches[K_COUNT] = {};
     double ms[K_COUNT] = {};
     std::atomic<int64_t> total{0};
@@ -1614,27 +1620,43 @@ struct LaunchScope {
         g_prof.launches[id].fetch_add(1, std::memory_order_relaxed);
         if (!g_prof.on) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
-        if (2 * g_prof.used + 2 > g_prof.ev.size()) {
-            for (int i = 0; i < 2; ++i) {
-                cudaEvent_t e;
-                cudaEventCreate(&e);
-                g_prof.ev.push_back(e);
+        if (g_prof.free_pairs.empty()) {
+            cudaEvent_t e[2];
+            if (cudaEventCreate(&e[0]) != cudaSuccess || cudaEventCreate(&e[1]) != cudaSuccess) {
+                cudaGetLastError();
+                return;
             }
+            g_prof.ev.push_back(e[0]);
+            g_prof.ev.push_back(e[1]);
+            g_prof.kid.push_back(0);
+            g_prof.owner.push_back(std::thread::id());
+            g_prof.free_pairs.push_back(g_prof.kid.size() - 1);
         }
-        pair = g_prof.used++;
-        if (g_prof.kid.size() < g_prof.used) g_prof.kid.resize(g_prof.used);
+        pair = g_prof.free_pairs.back();
+        g_prof.free_pairs.pop_back();
         g_prof.kid[pair] = id;
+        g_prof.owner[pair] = std::this_thread::get_id();
         cudaEventRecord(g_prof.ev[2 * pair], st);
     }
     ~LaunchScope() {
         if (pair == (size_t)-1) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
         cudaEventRecord(g_prof.ev[2 * pair + 1], st);
+        g_prof.stopped.push_back(pair);
     }
 };
 
-void harvest_locked() {
-    for (size_t i = 0; i < g_prof.used; ++i) {
+// all: every recorded pair (waits for them; call when no launch is in
+// flight); else only the calling thread's pairs (complete after it
+// synchronised its stream)
+void harvest_locked(bool all) {
+    std::vector<size_t> keep;
+    const std::thread::id me = std::this_thread::get_id();
+    for (size_t i : g_prof.stopped) {
+        if (!all && g_prof.owner[i] != me) {
+            keep.push_back(i);
+            continue;
+        }
         float t = 0.f, a = 0.f, b = 0.f;
         cudaEventSynchronize(g_prof.ev[2 * i + 1]);
         if (cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) == cudaSuccess)
@@ -1646,14 +1668,15 @@ void harvest_locked() {
             g_prof.iv[g_prof.kid[i]].push_back({(double)a, (double)b});
         else
             cudaGetLastError();
+        g_prof.free_pairs.push_back(i);
     }
-    g_prof.used = 0;
+    g_prof.stopped.swap(keep);
 }
 }  // namespace
 
 void profile_enable(bool on) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    harvest_locked();
+    harvest_locked(true);
     g_prof.on = on;
     for (int i = 0; i < K_COUNT; ++i) {
         g_prof.launches[i] = 0;
@@ -1671,9 +1694,24 @@ void profile_enable(bool on) {
     }
 }
 
+void prof_harvest() {
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    harvest_locked(false);
+}
+
+void profile_read(int id, int64_t* launches, double* ms) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    harvest_locked(true);
+    *launches = g_prof.launches[id];
+    *ms = g_prof.ms[id];
+}
+
+int64_t launch_count() { return g_prof.total; }
+
 double profile_busy(int id) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    harvest_locked();
+    harvest_locked(true);
     std::vector<std::pair<double, double>> v = g_prof.iv[id];
     std::sort(v.begin(), v.end());
     double busy = 0.0, lo = 0.0, hi = -1.0;
@@ -1689,21 +1727,6 @@ double profile_busy(int id) {
     if (hi > lo) busy += hi - lo;
     return busy;
 }
-
-void prof_harvest() {
-    if (!g_prof.on) return;
-    std::lock_guard<std::mutex> lk(g_prof.mu);
-    harvest_locked();
-}
-
-void profile_read(int id, int64_t* launches, double* ms) {
-    std::lock_guard<std::mutex> lk(g_prof.mu);
-    harvest_locked();
-    *launches = g_prof.launches[id];
-    *ms = g_prof.ms[id];
-}
-
-int64_t launch_count() { return g_prof.total; }
 
 // ---------------------------------------------------------------------------
 // launchers
