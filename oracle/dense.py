@@ -231,3 +231,46 @@ def electron_count_closed_form(eigs: np.ndarray, z, w, g_s=2.0) -> float:
     for zk, wk in zip(z, w):
         tot += wk * np.sum(1.0 / (zk - eigs))
     return -(g_s / math.pi) * tot.imag
+
+
+# --------------------------------------------------------------------------
+# z-derivatives and the band energy with its gradients (adjoint quantities)
+# --------------------------------------------------------------------------
+def green_derivative_columns(H, S, z, cols) -> np.ndarray:
+    """dG/dz e_j = -G S G e_j for every shift (G = (zS - H)^-1, so
+    dG/dz = -G (dA/dz) G with dA/dz = S); (K, N, R) complex."""
+    N = S.shape[0]
+    out = np.zeros((len(z), N, len(cols)), dtype=np.complex128)
+    B = np.zeros((N, len(cols)), dtype=np.complex128)
+    for c, j in enumerate(cols):
+        B[j, c] = 1.0
+    for k, zk in enumerate(z):
+        A = shifted_matrix(H, S, zk)
+        X = gauss_solve(A, B)
+        out[k] = -gauss_solve(A, S @ X)
+    return out
+
+
+def band_energy(H, S, z, w, g_s=2.0) -> float:
+    """Band-structure energy E = Tr(rho H) = sum_ab rho_ab H_ba with the
+    energy-integrated density matrix rho of ``density_matrix``."""
+    rho = density_matrix(H, S, z, w, g_s)
+    return float(np.sum(rho * H.T))
+
+
+def band_energy_gradients(H, S, z, w, g_s=2.0):
+    """dE/dH_ab and dE/dS_ab, H_ab and S_ab taken as independent entries.
+    With real weights E = -(g_s/pi) Im sum_k w_k z_k Tr[G_k S] for every H
+    and S (because G (zS - H) = 1), and dG = G (dH - z dS) G, so
+      dE/dH_ab = -(g_s/pi) Im sum_k w_k z_k [G S G]_ba,
+      dE/dS_ab = -(g_s/pi) Im sum_k w_k (z_k G_ba - z_k^2 [G S G]_ba).
+    Returns the two (N, N) real matrices."""
+    N = S.shape[0]
+    gH = np.zeros((N, N), dtype=np.complex128)
+    gS = np.zeros((N, N), dtype=np.complex128)
+    for zk, wk in zip(z, w):
+        G = green_matrix(H, S, zk)
+        GSG = G @ S @ G
+        gH += wk * zk * GSG.T
+        gS += wk * (zk * G.T - zk * zk * GSG.T)
+    return -(g_s / math.pi) * gH.imag, -(g_s / math.pi) * gS.imag

@@ -70,7 +70,8 @@ def apply_S_inverse(S, r: np.ndarray, tol: float, max_iter: int):
 
 def generalized_shifted_cocg(H, S, z, j: int, *, tol=1e-10, inner_tol=1e-13, inner_max_iter=1000,
                              max_iter=100000, seed=0, switching=True, functionals=None,
-                             keep_full=True, force_switch_every=0, pi_sign=1.0, record=False):
+                             keep_full=True, force_switch_every=0, pi_sign=1.0, record=False,
+                             derivative=False):
     """Generalized shifted COCG for (z_k S - H) x_k = e_j, k = 0..K-1.
 
     Seed system (Eq. shift-E) solved by the recurrences Eq. (CGp:p),
@@ -108,6 +109,20 @@ def generalized_shifted_cocg(H, S, z, j: int, *, tol=1e-10, inner_tol=1e-13, inn
     ``force_switch_every``: if > 0, switch to the worst unconverged shift
     every that many steps as well (used to exercise the switch).
 
+    ``derivative``: also carry d/dz_k of every shift's iterates by
+    differentiating the shift recurrences in z_k with the seed quantities
+    (r_n, r'_n, alpha_n, beta_n and the switch rescalings) held fixed: only
+    Delta_k = z_k - z_s depends on z_k, so
+      dpi_{n+1} = alpha_n pi_n + (1 + alpha_n Delta) dpi_n
+                  + (beta_{n-1} alpha_n / alpha_{n-1}) (dpi_n - dpi_{n-1}),
+      d alpha^k = alpha_n (dpi_n pi_{n+1} - pi_n dpi_{n+1}) / pi_{n+1}^2,
+      d beta^k  = 2 beta_n (pi_n / pi_{n+1}) (dpi_n pi_{n+1} - pi_n dpi_{n+1}) / pi_{n+1}^2,
+      dx^k += d alpha^k p^k + alpha^k dp^k,
+      dp^k  = -r'_{n+1} dpi_{n+1} / pi_{n+1}^2 + d beta^k p^k + beta^k dp^k,
+    and a seed switch divides dpi, dpi_prev by the same constants as pi.  No
+    extra matrix products: the derivative lives in the same Krylov sequence.
+    The result then carries dx (K, N) and/or dt (K, M).
+
     Returns a dict with x (K, N) if keep_full, t (K, M) if functionals,
     conv_iter (K,), iterations, switches, and (if record) per-step histories.
     """
@@ -134,6 +149,13 @@ def generalized_shifted_cocg(H, S, z, j: int, *, tol=1e-10, inner_tol=1e-13, inn
     t = np.zeros((K, F.shape[0]), dtype=np.complex128) if F is not None else None
     u = np.tile(F @ rp, (K, 1)) if F is not None else None
     hist = {"alpha": [], "beta": [], "rnorm": [], "seed": [], "pi": [], "inner": []} if record else None
+    if derivative:
+        dpi = np.zeros(K, dtype=np.complex128)
+        dpi_prev = np.zeros(K, dtype=np.complex128)
+        dx = np.zeros((K, N), dtype=np.complex128) if keep_full else None
+        dp = np.zeros((K, N), dtype=np.complex128) if keep_full else None
+        dt = np.zeros((K, F.shape[0]), dtype=np.complex128) if F is not None else None
+        du = np.zeros((K, F.shape[0]), dtype=np.complex128) if F is not None else None
     switches = 0
     n = 0
     for n in range(max_iter):
@@ -159,6 +181,24 @@ def generalized_shifted_cocg(H, S, z, j: int, *, tol=1e-10, inner_tol=1e-13, inn
         bk = np.zeros(K, dtype=np.complex128)
         ak[act] = alpha * pi[act] / pi_new[act]
         bk[act] = beta * (pi[act] / pi_new[act]) ** 2
+        if derivative:
+            dpi_new = dpi.copy()
+            dpi_new[act] = alpha * pi[act] + (1.0 + alpha * d[act]) * dpi[act] + \
+                pi_sign * (beta_prev * alpha / alpha_prev) * (dpi[act] - dpi_prev[act])
+            num = np.zeros(K, dtype=np.complex128)
+            num[act] = (dpi[act] * pi_new[act] - pi[act] * dpi_new[act]) / pi_new[act] ** 2
+            dak = alpha * num
+            dbk = np.zeros(K, dtype=np.complex128)
+            dbk[act] = 2.0 * beta * (pi[act] / pi_new[act]) * num[act]
+            dip = np.zeros(K, dtype=np.complex128)
+            dip[act] = -dpi_new[act] / pi_new[act] ** 2
+            if keep_full:
+                dx[act] += dak[act, None] * p[act] + ak[act, None] * dp[act]
+                dp[act] = rp_new[None, :] * dip[act, None] + dbk[act, None] * p[act] + bk[act, None] * dp[act]
+            if F is not None:
+                fr_d = F @ rp_new
+                dt[act] += dak[act, None] * u[act] + ak[act, None] * du[act]
+                du[act] = fr_d[None, :] * dip[act, None] + dbk[act, None] * u[act] + bk[act, None] * du[act]
         if keep_full:
             x[act] += ak[act, None] * p[act]
             p[act] = rp_new[None, :] / pi_new[act, None] + bk[act, None] * p[act]
@@ -180,6 +220,8 @@ def generalized_shifted_cocg(H, S, z, j: int, *, tol=1e-10, inner_tol=1e-13, inn
             hist["inner"].append(m_in)
         # advance n -> n+1
         pi_prev, pi = pi, pi_new
+        if derivative:
+            dpi_prev, dpi = dpi, dpi_new
         r_prev, r, rp, rho = r, r_new, rp_new, rho_new
         alpha_prev, beta_prev = alpha, beta
         if conv.all():
@@ -197,6 +239,9 @@ def generalized_shifted_cocg(H, S, z, j: int, *, tol=1e-10, inner_tol=1e-13, inn
                 alpha_prev, beta_prev = ak[s_new], bk[s_new]
                 pi = pi / c1
                 pi_prev = pi_prev / c0
+                if derivative:
+                    dpi = dpi / c1
+                    dpi_prev = dpi_prev / c0
                 zs = z[s_new]
                 s = s_new
                 switches += 1
@@ -206,6 +251,11 @@ def generalized_shifted_cocg(H, S, z, j: int, *, tol=1e-10, inner_tol=1e-13, inn
         out["x"] = x
     if F is not None:
         out["t"] = t
+    if derivative:
+        if keep_full:
+            out["dx"] = dx
+        if F is not None:
+            out["dt"] = dt
     if record:
         out["history"] = hist
     return out
