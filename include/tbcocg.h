@@ -182,6 +182,36 @@ tb_status tb_green_elements(tb_handle *h, int32_t K, const double *z, int32_t R,
                             double *G_out, tb_stats *stats, void *stream);
 
 /*
+ * As tb_green_elements, and also dG_ij/dz at the same elements (the
+ * adjoint building block; dG/dz = -G S G).  The derivative is carried
+ * through the same Krylov sequence by differentiating the shift recurrences
+ * (Eq. shift:pi and the alpha^k, beta^k relations) with respect to z_k with
+ * the seed quantities fixed: no extra matrix products, 2x the per-shift
+ * state.  dG_out: complex [row_ptr[R]][K] like G_out, host or device.
+ */
+tb_status tb_green_elements_dz(tb_handle *h, int32_t K, const double *z, int32_t R, const int32_t *cols,
+                               const int64_t *row_ptr, const int32_t *rows, const tb_solve_opts *opts,
+                               double *G_out, double *dG_out, tb_stats *stats, void *stream);
+
+/*
+ * Band-structure energy and its gradients (adjoint; the quadrature z_k,
+ * w_k must have real weights):
+ *     E = Tr(rho H) = -(g_s/pi) Im sum_k w_k z_k Tr[G(z_k) S],
+ *     dE/dH_ab = -(g_s/pi) Im sum_k w_k z_k [G S G]_ba,
+ *     dE/dS_ab = -(g_s/pi) Im sum_k w_k (z_k G_ba - z_k^2 [G S G]_ba),
+ * H_ab, S_ab taken as independent entries of the stored pattern.  All N
+ * columns are solved with their pattern rows projected (values and z-
+ * derivatives, as tb_green_elements_dz).  E_out: one double; dE_dH, dE_dS:
+ * double arrays in the caller's block layout of S_vals (one value per
+ * stored entry); host or device.  Chain rule to forces (dS/dR, dH/dR) is the
+ * caller's.  Status as tb_shifted_cocg; TB_ERR_INVALID_ARG if a block
+ * column holds more than 1024 orbitals.
+ */
+tb_status tb_band_energy(tb_handle *h, int32_t K, const double *z, const double *w, double g_s,
+                         const tb_solve_opts *opts, double *E_out, double *dE_dH, double *dE_dS, tb_stats *stats,
+                         void *stream);
+
+/*
  * Gross Mulliken populations of selected orbitals (Section 2.2, the
  * Mulliken partition of the charge density), from the energy integral of
  * the Green's function with the quadrature (z_k, w_k) (host, complex):

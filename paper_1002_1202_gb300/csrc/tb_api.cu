@@ -39,6 +39,13 @@ struct tb_handle {
     int64_t* atom_orb_off = nullptr;  // device [n_atoms + 1]: first caller orbital of every atom
     double* H0 = nullptr;             // device [nb][16]: the Hamiltonian of tb_create, kept once
                                       // the charge-self-consistent term first replaces H
+    // host copies of the caller's pattern and S values (gradient outputs
+    // use the caller's block layout)
+    std::vector<int64_t> brow_h;       // [n_atoms + 1]
+    std::vector<int32_t> bcol_h;       // [nb]
+    std::vector<int64_t> boff_h;       // [nb + 1]: first value of every block
+    std::vector<int64_t> btrans_h;     // [nb]: index of the transposed block
+    std::vector<double> S_h;           // [boff_h[nb]]
     std::vector<int64_t> sys_atom_off;  // batch: first atom of every system, [n_systems + 1]
     std::vector<int64_t> sys_orb_off;   // batch: first orbital of every system
     // batch only: one solve view per system (block rows offset to the
@@ -114,6 +121,7 @@ struct Solve {
     // device outputs
     double2* x_out = nullptr;           // full
     double2* g_out = nullptr;           // rows
+    double2* dg_out = nullptr;          // rows: d/dz of the elements (optional)
     double* q_out = nullptr;            // srow, per column
 };
 
@@ -392,6 +400,13 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
         if ((s = dalloc(cl, &p.t, (size_t)P * K * M)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.u, (size_t)P * K * M)) != TB_OK) return s;
         if (q.proj == PROJ_ROWS && (s = dalloc(cl, &p.frow, (size_t)P * M)) != TB_OK) return s;
+        if (q.proj == PROJ_ROWS && q.dg_out) {
+            p.deriv = 1;
+            if ((s = dalloc(cl, &p.dt, (size_t)P * K * M)) != TB_OK) return s;
+            if ((s = dalloc(cl, &p.du, (size_t)P * K * M)) != TB_OK) return s;
+            if ((s = dalloc(cl, &p.dpi, (size_t)P * K)) != TB_OK) return s;
+            if ((s = dalloc(cl, &p.dpi_prev, (size_t)P * K)) != TB_OK) return s;
+        }
     }
     double2* w_dev = nullptr;
     if (q.proj == PROJ_SROW) {
@@ -474,8 +489,10 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
         // outputs of this panel
         if (q.proj == PROJ_NONE)
             launch_full_output(p, v.o2p_d, (int)v.n_orb, R, ncols, c0, q.x_out, st);
-        else if (q.proj == PROJ_ROWS)
+        else if (q.proj == PROJ_ROWS) {
             launch_green_output(p, ncols, off_dev + c0, q.g_out, st);
+            if (p.deriv) launch_green_deriv_output(p, ncols, off_dev + c0, q.dg_out, st);
+        }
         else
             launch_mulliken_output(p, ncols, w_dev, q.g_s, q.q_out + c0, st);
         TB_CK(cudaGetLastError());
@@ -544,8 +561,10 @@ tb_status run_jobs(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stat
     }
     if (q.proj == PROJ_NONE)
         TB_CK(cudaMemsetAsync(q.x_out, 0, sizeof(double2) * (size_t)K * R * h->n_orb, st));
-    if (q.proj == PROJ_ROWS)
+    if (q.proj == PROJ_ROWS) {
         TB_CK(cudaMemsetAsync(q.g_out, 0, sizeof(double2) * (size_t)q.row_ptr[R] * K, st));
+        if (q.dg_out) TB_CK(cudaMemsetAsync(q.dg_out, 0, sizeof(double2) * (size_t)q.row_ptr[R] * K, st));
+    }
     cudaEvent_t ev_in;
     TB_CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
     TB_CK(cudaEventRecord(ev_in, st));
@@ -614,6 +633,7 @@ tb_status run_jobs(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stat
                     s = TB_ERR_CUDA;
                 double2* xt = nullptr;
                 double2* gt = nullptr;
+                double2* dgt = nullptr;
                 double* qt = nullptr;
                 int64_t* gidx_d = nullptr;
                 if (s == TB_OK && q.proj == PROJ_NONE) {
@@ -642,6 +662,8 @@ tb_status run_jobs(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stat
                                         ws) != cudaSuccess)
                         s = TB_ERR_CUDA;
                     q2.g_out = gt;
+                    if (s == TB_OK && q.dg_out) s = dalloc(cl, &dgt, (size_t)std::max<int64_t>(1, rp2.back()) * K);
+                    q2.dg_out = q.dg_out ? dgt : nullptr;
                 } else if (s == TB_OK) {
                     s = dalloc(cl, &qt, (size_t)Rq);
                     q2.q_out = qt;
@@ -656,8 +678,10 @@ tb_status run_jobs(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stat
                 if (s == TB_OK || s == TB_ERR_NOT_CONVERGED) {
                     if (q.proj == PROJ_NONE)
                         launch_scatter_full(xt, pos_d, K, Rq, Nq, R, h->n_orb, orb0, q.x_out, ws);
-                    else if (q.proj == PROJ_ROWS && !gidx.empty())
+                    else if (q.proj == PROJ_ROWS && !gidx.empty()) {
                         launch_scatter_rows(gt, gidx_d, (int64_t)gidx.size(), K, q.g_out, ws);
+                        if (q.dg_out) launch_scatter_rows(dgt, gidx_d, (int64_t)gidx.size(), K, q.dg_out, ws);
+                    }
                     else if (q.proj == PROJ_SROW)
                         launch_scatter_cols(qt, pos_d, Rq, q.q_out, ws);
                     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ws) != cudaSuccess) s = TB_ERR_CUDA;
@@ -1000,6 +1024,7 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
             hmax = std::max(hmax, std::fabs(d->H_vals[e]));
         }
     }
+    std::vector<int64_t> btrans(nb);
     for (int i = 0; i < n; ++i) {
         const int ni = d->orb_per_atom[i];
         for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
@@ -1010,6 +1035,7 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
             const int32_t* f = std::lower_bound(beg, end, (int32_t)i);
             if (f == end || *f != i) return TB_ERR_NOT_SYMMETRIC;
             const int64_t bt = d->brow_ptr[j] + (f - beg);
+            btrans[b] = bt;
             for (int a = 0; a < ni; ++a)
                 for (int c = 0; c < nj; ++c) {
                     const double s1 = d->S_vals[boff[b] + (int64_t)a * nj + c];
@@ -1067,6 +1093,11 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     h->n_atoms = n;
     h->n_orb = N;
     h->orb_per_atom.assign(d->orb_per_atom, d->orb_per_atom + n);
+    h->brow_h.assign(d->brow_ptr, d->brow_ptr + n + 1);
+    h->bcol_h.assign(d->bcol, d->bcol + nb);
+    h->boff_h = boff;
+    h->btrans_h = btrans;
+    h->S_h.assign(d->S_vals, d->S_vals + boff[nb]);
     h->orb2pad_h = o2p;
     h->ds.n_atoms = n;
     h->ds.nb = nb;
@@ -1258,6 +1289,12 @@ tb_status tb_shifted_cocg(tb_handle* h, int32_t K, const double* z, int32_t R, c
 tb_status tb_green_elements(tb_handle* h, int32_t K, const double* z, int32_t R, const int32_t* cols,
                             const int64_t* row_ptr, const int32_t* rows, const tb_solve_opts* opts,
                             double* G_out, tb_stats* stats, void* stream) {
+    return tb_green_elements_dz(h, K, z, R, cols, row_ptr, rows, opts, G_out, nullptr, stats, stream);
+}
+
+tb_status tb_green_elements_dz(tb_handle* h, int32_t K, const double* z, int32_t R, const int32_t* cols,
+                               const int64_t* row_ptr, const int32_t* rows, const tb_solve_opts* opts,
+                               double* G_out, double* dG_out, tb_stats* stats, void* stream) {
     if (!h || !G_out || !row_ptr || !rows) return TB_ERR_INVALID_ARG;
     tb_status s;
     if ((s = check_opts(opts)) != TB_OK) return s;
@@ -1273,13 +1310,102 @@ tb_status tb_green_elements(tb_handle* h, int32_t K, const double* z, int32_t R,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Cleanup cl;
     cl.st = st;
-    OutBuf ob;
-    if ((s = out_prepare(cl, ob, G_out, sizeof(double2) * (size_t)row_ptr[R] * K)) != TB_OK) return s;
+    OutBuf ob, obd;
+    const size_t bytes = sizeof(double2) * (size_t)row_ptr[R] * K;
+    if ((s = out_prepare(cl, ob, G_out, bytes)) != TB_OK) return s;
+    if (dG_out && (s = out_prepare(cl, obd, dG_out, bytes)) != TB_OK) return s;
     Solve q;
     q.K = K; q.z = z; q.R = R; q.cols = cols; q.proj = PROJ_ROWS; q.row_ptr = row_ptr; q.rows = rows;
     q.g_out = static_cast<double2*>(ob.dev);
+    q.dg_out = dG_out ? static_cast<double2*>(obd.dev) : nullptr;
     const tb_status run = run_solve(h, q, opts, stats, st);
-    return merge(run, out_finish(ob, st));
+    tb_status fin = out_finish(ob, st);
+    if (dG_out && fin == TB_OK) fin = out_finish(obd, st);
+    return merge(run, fin);
+}
+
+tb_status tb_band_energy(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,
+                         const tb_solve_opts* opts, double* E_out, double* dE_dH, double* dE_dS, tb_stats* stats,
+                         void* stream) {
+    if (!h || !E_out || !dE_dH || !dE_dS || !w || !std::isfinite(g_s)) return TB_ERR_INVALID_ARG;
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(w[k])) return TB_ERR_INVALID_ARG;
+    // every column b with the rows a of its block column (the H/S pattern),
+    // in caller orbital order; element e = (a, b) also names value
+    // index val[e] of H_ab / S_ab in the caller's block layout
+    const int n = h->n_atoms;
+    const int64_t N = h->n_orb;
+    std::vector<int64_t> ooff(n + 1, 0);
+    for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + h->orb_per_atom[i];
+    std::vector<int32_t> cols(N), rows;
+    std::vector<int64_t> row_ptr(N + 1, 0), val;
+    std::vector<double> S_el;
+    for (int J = 0; J < n; ++J) {
+        const int nj = h->orb_per_atom[J];
+        for (int bo = 0; bo < nj; ++bo) {
+            const int64_t b = ooff[J] + bo;
+            cols[b] = (int32_t)b;
+            // block column J = block row J by symmetry of the pattern
+            for (int64_t blk = h->brow_h[J]; blk < h->brow_h[J + 1]; ++blk) {
+                const int I = h->bcol_h[blk];
+                const int ni = h->orb_per_atom[I];
+                const int64_t bt = h->btrans_h[blk];       // block (I, J)
+                for (int ao = 0; ao < ni; ++ao) {
+                    rows.push_back((int32_t)(ooff[I] + ao));
+                    const int64_t v = h->boff_h[bt] + (int64_t)ao * nj + bo;
+                    val.push_back(v);
+                    S_el.push_back(h->S_h[v]);
+                }
+            }
+            row_ptr[b + 1] = (int64_t)rows.size();
+            if (row_ptr[b + 1] - row_ptr[b] > MAX_M) return TB_ERR_INVALID_ARG;
+        }
+    }
+    const int64_t ne = (int64_t)rows.size();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    double2 *G, *dG, *zd, *wd;
+    double *Sd, *et, *gH, *gS, *Ed;
+    int64_t* vald;
+    if ((s = dalloc(cl, &G, (size_t)ne * K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &dG, (size_t)ne * K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &zd, (size_t)K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &wd, (size_t)K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &Sd, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &et, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gH, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gS, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &Ed, 1)) != TB_OK) return s;
+    if ((s = dalloc(cl, &vald, (size_t)ne)) != TB_OK) return s;
+    TB_CK(cudaMemcpyAsync(zd, z, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(wd, w, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(Sd, S_el.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(vald, val.data(), sizeof(int64_t) * ne, cudaMemcpyHostToDevice, st));
+    Solve q;
+    q.K = K; q.z = z; q.R = (int)N; q.cols = cols.data(); q.proj = PROJ_ROWS; q.row_ptr = row_ptr.data();
+    q.rows = rows.data(); q.g_out = G; q.dg_out = dG;
+    const tb_status run = run_solve(h, q, opts, stats, st);
+    if (run != TB_OK && run != TB_ERR_NOT_CONVERGED) return run;
+    launch_band_energy_terms(G, dG, Sd, ne, K, zd, wd, g_s, et, gH, gS, st);
+    launch_sum_fixed(et, ne, Ed, st);
+    // gradients into the caller's block layout (every pattern value once)
+    const size_t nval = (size_t)h->boff_h.back();
+    OutBuf oH, oS, oE;
+    if ((s = out_prepare(cl, oH, dE_dH, sizeof(double) * nval)) != TB_OK) return s;
+    if ((s = out_prepare(cl, oS, dE_dS, sizeof(double) * nval)) != TB_OK) return s;
+    if ((s = out_prepare(cl, oE, E_out, sizeof(double))) != TB_OK) return s;
+    launch_scatter_values(gH, vald, ne, static_cast<double*>(oH.dev), st);
+    launch_scatter_values(gS, vald, ne, static_cast<double*>(oS.dev), st);
+    TB_CK(cudaMemcpyAsync(oE.dev, Ed, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TB_CK(cudaGetLastError());
+    tb_status fin = out_finish(oH, st);
+    if (fin == TB_OK) fin = out_finish(oS, st);
+    if (fin == TB_OK) fin = out_finish(oE, st);
+    return merge(run, fin);
 }
 
 tb_status tb_mulliken_orbital(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,

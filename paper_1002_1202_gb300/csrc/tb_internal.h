@@ -110,6 +110,9 @@ struct PanelDev {
     double2 *ak = nullptr, *bk = nullptr, *ipi = nullptr;  // [P][K] this step (full mode)
     int32_t* frow = nullptr;       // [P][M] padded rows (PROJ_ROWS)
     double2 *t = nullptr, *u = nullptr;          // [P][K][M] projected x, p
+    int deriv = 0;                               // 1: also d/dz_k of the projections (PROJ_ROWS)
+    double2 *dpi = nullptr, *dpi_prev = nullptr; // [P][K] d pi^k / d z_k
+    double2 *dt = nullptr, *du = nullptr;        // [P][K][M] d/dz_k of t, u
     double2 *X = nullptr, *Pk = nullptr;         // [K][npad][P] full mode x, p
     double* partials = nullptr;    // [grid][4][P] per-CTA sums
     double* partials2 = nullptr;   // [MAX_GROUPS][4][P] per-group sums
@@ -156,6 +159,12 @@ void launch_full_output(const PanelDev& p, const int32_t* orb2pad, int n_orb, in
                         int c0, double2* out, cudaStream_t st);
 void launch_green_output(const PanelDev& p, int ncols, const int64_t* out_off, double2* out,
                          cudaStream_t st);
+void launch_green_deriv_output(const PanelDev& p, int ncols, const int64_t* out_off, double2* out,
+                               cudaStream_t st);
+void launch_band_energy_terms(const double2* G, const double2* dG, const double* S_el, int64_t n, int K,
+                              const double2* z, const double2* w, double g_s, double* e_terms, double* gH,
+                              double* gS, cudaStream_t st);
+void launch_sum_fixed(const double* v, int64_t n, double* out, cudaStream_t st);
 void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
                             cudaStream_t st);
 
@@ -164,6 +173,7 @@ void launch_scatter_full(const double2* tmp, const int32_t* pos, int K, int Rq, 
                          int64_t orb0, double2* out, cudaStream_t st);
 void launch_scatter_rows(const double2* tmp, const int64_t* gidx, int64_t n, int K, double2* out, cudaStream_t st);
 void launch_scatter_cols(const double* tmp, const int32_t* pos, int Rq, double* out, cudaStream_t st);
+void launch_scatter_values(const double* v, const int64_t* idx, int64_t n, double* out, cudaStream_t st);
 
 // charge self-consistency (Eq. Hap-CSC)
 void launch_csc_potential(const double* gamma, const double* dq, int n, double* V, cudaStream_t st);

@@ -1167,8 +1167,17 @@ __global__ void k_shift_init(DevSystem s, PanelDev p) {
             const size_t o = ((size_t)c * K + k) * p.M + m;
             p.t[o] = cmk(0.0, 0.0);
             p.u[o] = d[m];
+            if (p.deriv) {
+                p.dt[o] = cmk(0.0, 0.0);
+                p.du[o] = cmk(0.0, 0.0);      // u_0 = F r'_0 does not depend on z_k
+            }
         }
     }
+    if (p.deriv)
+        for (int k = threadIdx.x; k < K; k += THREADS) {
+            p.dpi[(size_t)c * K + k] = cmk(0.0, 0.0);
+            p.dpi_prev[(size_t)c * K + k] = cmk(0.0, 0.0);
+        }
     __syncthreads();
     if (threadIdx.x == 0) {
         cs.rho = cs.rho_new;
@@ -1212,6 +1221,9 @@ __global__ void __launch_bounds__(THREADS) k_shift_step(DevSystem s, PanelDev p)
     double2* sak = d + p.M;                 // [K]
     double2* sbk = sak + K;                 // [K]
     double2* sip = sbk + K;                 // [K]
+    double2* sdak = sip + K;                // [K] derivative mode: d alpha^k, d beta^k, d (1/pi^k)
+    double2* sdbk = sdak + K;
+    double2* sdip = sdbk + K;
     if (p.proj != PROJ_NONE) eval_functionals(s, p, c, nfun, d, red);
 
     const double2 one = cmk(1.0, 0.0);
@@ -1240,6 +1252,19 @@ __global__ void __launch_bounds__(THREADS) k_shift_step(DevSystem s, PanelDev p)
         const double res = rnorm / cabs2(pin);
         p.pi_prev[o] = pk;
         p.pi[o] = pin;
+        if (p.deriv) {
+            // d/dz_k with the seed quantities fixed (d Delta_k / d z_k = 1)
+            const double2 dpk = p.dpi[o], dpp = p.dpi_prev[o];
+            const double2 dpin = cadd(cadd(cmul(alpha, pk), cmul(cadd(one, cmul(alpha, dl)), dpk)),
+                                      cmul(c2, csub(dpk, dpp)));
+            const double2 ip2 = cmul(ip, ip);
+            const double2 num = cmul(csub(cmul(dpk, pin), cmul(pk, dpin)), ip2);
+            sdak[k] = cmul(alpha, num);
+            sdbk[k] = cmul(cmk(2.0 * beta.x, 2.0 * beta.y), cmul(ratio, num));
+            sdip[k] = cmk(-cmul(dpin, ip2).x, -cmul(dpin, ip2).y);
+            p.dpi_prev[o] = dpk;
+            p.dpi[o] = dpin;
+        }
         sak[k] = ak;
         sbk[k] = bk;
         sip[k] = ip;
@@ -1263,6 +1288,11 @@ __global__ void __launch_bounds__(THREADS) k_shift_step(DevSystem s, PanelDev p)
             if (ip.x == 0.0 && ip.y == 0.0) continue;
             const size_t o = ((size_t)c * K + k) * p.M + m;
             const double2 u = p.u[o];
+            if (p.deriv) {
+                const double2 du = p.du[o];
+                p.dt[o] = cadd(p.dt[o], cadd(cmul(sdak[k], u), cmul(sak[k], du)));
+                p.du[o] = cadd(cadd(cmul(d[m], sdip[k]), cmul(sdbk[k], u)), cmul(sbk[k], du));
+            }
             p.t[o] = cadd(p.t[o], cmul(sak[k], u));
             p.u[o] = cadd(cmul(d[m], ip), cmul(sbk[k], u));
         }
@@ -1326,6 +1356,10 @@ __global__ void __launch_bounds__(THREADS) k_shift_step(DevSystem s, PanelDev p)
             const size_t o = (size_t)c * K + k;
             p.pi[o] = cdiv(p.pi[o], c1);
             p.pi_prev[o] = cdiv(p.pi_prev[o], c0);
+            if (p.deriv) {
+                p.dpi[o] = cdiv(p.dpi[o], c1);
+                p.dpi_prev[o] = cdiv(p.dpi_prev[o], c0);
+            }
         }
     }
 }
@@ -1360,14 +1394,58 @@ __global__ void k_full_output(PanelDev p, const int32_t* __restrict__ orb2pad, i
     }
 }
 
-__global__ void k_green_output(PanelDev p, int ncols, const int64_t* __restrict__ off, double2* __restrict__ out) {
+// projected values src (p.t: G elements, p.dt: their z-derivatives) into the
+// caller's layout out[(off[c] + m) * K + k]
+__global__ void k_green_output(PanelDev p, int ncols, const int64_t* __restrict__ off, const double2* src,
+                               double2* __restrict__ out) {
     const int c = blockIdx.x;
     if (c >= ncols) return;
     const int nf = p.col[c].nfun;
     for (int e = threadIdx.x; e < nf * p.K; e += THREADS) {
         const int m = e / p.K, k = e % p.K;
-        out[(size_t)(off[c] + m) * p.K + k] = p.t[((size_t)c * p.K + k) * p.M + m];
+        out[(size_t)(off[c] + m) * p.K + k] = src[((size_t)c * p.K + k) * p.M + m];
     }
+}
+
+// Band energy and its gradients per projected element e = (a, b) of the
+// H/S pattern (G_e(z_k) = G_ab, dG_e = dG_ab/dz):
+//   e_terms[e] = -(g_s/pi) Im sum_k w_k z_k S_ab G_ab(z_k)   (E = sum_e e_terms)
+//   gH[e] = -(g_s/pi) Im sum_k w_k z_k (-dG_ab)  = dE/dH_ba
+//   gS[e] = -(g_s/pi) Im sum_k w_k (z_k G_ab + z_k^2 dG_ab) = dE/dS_ba
+// (dG/dz = -G S G; G and G S G are symmetric, so (a, b) and (b, a) agree)
+__global__ void k_band_energy_terms(const double2* __restrict__ G, const double2* __restrict__ dG,
+                                    const double* __restrict__ S_el, int64_t n, int K, const double2* __restrict__ z,
+                                    const double2* __restrict__ w, double g_s, double* __restrict__ e_terms,
+                                    double* __restrict__ gH, double* __restrict__ gS) {
+    const double f = -g_s / 3.14159265358979323846;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double ae = 0.0, ah = 0.0, as = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double2 wz = cmul(w[k], z[k]);
+            const double2 g = G[e * K + k], dg = dG[e * K + k];
+            ae += cmul(wz, g).y;
+            ah -= cmul(wz, dg).y;
+            as += cmul(wz, g).y + cmul(cmul(wz, z[k]), dg).y;
+        }
+        e_terms[e] = f * S_el[e] * ae;
+        gH[e] = f * ah;
+        gS[e] = f * as;
+    }
+}
+
+// out[0] = sum of v[0..n) in a fixed order (one CTA: strided partial sums,
+// then a tree): deterministic whatever the launch history
+__global__ void k_sum_fixed(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
+    __shared__ double red[THREADS];
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < n; i += THREADS) acc += v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = THREADS / 2; st >= 1; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
 }
 
 // a7: q_j = -(g_s/pi) Im sum_k w_k s_j^T x_j(z_k)
@@ -1572,6 +1650,13 @@ __global__ void k_scatter_rows(const double2* __restrict__ tmp, const int64_t* _
         const long long e = i / K;
         out[gidx[e] * K + (i - e * K)] = tmp[i];
     }
+}
+
+// out[idx[e]] = v[e]
+__global__ void k_scatter_values(const double* __restrict__ v, const int64_t* __restrict__ idx, int64_t n,
+                                 double* __restrict__ out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        out[idx[e]] = v[e];
 }
 
 // out[pos[c]] = tmp[c]   (one value per column)
@@ -1865,7 +1950,9 @@ void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStre
     else
         k_inner32_update<1><<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, it);
 }
-static size_t shift_smem(const PanelDev& p) { return sizeof(double2) * ((size_t)(p.M > 0 ? p.M : 1) + 3 * (size_t)p.K); }
+static size_t shift_smem(const PanelDev& p) {
+    return sizeof(double2) * ((size_t)(p.M > 0 ? p.M : 1) + (p.deriv ? 6 : 3) * (size_t)p.K);
+}
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     const size_t sm = shift_smem(p);
     static size_t lim_init = 48 * 1024;
@@ -1904,8 +1991,22 @@ void launch_full_output(const PanelDev& p, const int32_t* orb2pad, int n_orb, in
 void launch_green_output(const PanelDev& p, int ncols, const int64_t* off, double2* out, cudaStream_t st) {
     {
         LaunchScope ls_(K_OTHER, st);
-        k_green_output<<<p.P, THREADS, 0, st>>>(p, ncols, off, out);
+        k_green_output<<<p.P, THREADS, 0, st>>>(p, ncols, off, p.t, out);
     }
+}
+void launch_green_deriv_output(const PanelDev& p, int ncols, const int64_t* off, double2* out, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_green_output<<<p.P, THREADS, 0, st>>>(p, ncols, off, p.dt, out);
+}
+void launch_band_energy_terms(const double2* G, const double2* dG, const double* S_el, int64_t n, int K,
+                              const double2* z, const double2* w, double g_s, double* e_terms, double* gH,
+                              double* gS, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_band_energy_terms<<<grid_for(n), THREADS, 0, st>>>(G, dG, S_el, n, K, z, w, g_s, e_terms, gH, gS);
+}
+void launch_sum_fixed(const double* v, int64_t n, double* out, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_sum_fixed<<<1, THREADS, 0, st>>>(v, n, out);
 }
 void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
                             cudaStream_t st) {
@@ -1986,6 +2087,11 @@ void launch_scatter_full(const double2* tmp, const int32_t* pos, int K, int Rq, 
 void launch_scatter_rows(const double2* tmp, const int64_t* gidx, int64_t n, int K, double2* out, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
     k_scatter_rows<<<grid_for(n * (long long)K), THREADS, 0, st>>>(tmp, gidx, n, K, out);
+}
+
+void launch_scatter_values(const double* v, const int64_t* idx, int64_t n, double* out, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_scatter_values<<<grid_for(n), THREADS, 0, st>>>(v, idx, n, out);
 }
 
 void launch_scatter_cols(const double* tmp, const int32_t* pos, int Rq, double* out, cudaStream_t st) {

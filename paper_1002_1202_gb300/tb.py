@@ -113,6 +113,10 @@ SIGNATURES = [
                                   C.POINTER(Stats), _VP]),
     ("tb_green_elements", C.c_int, [_VP, C.c_int32, _DP, C.c_int32, _I32P, _I64P, _I32P,
                                     C.POINTER(SolveOpts), _VP, C.POINTER(Stats), _VP]),
+    ("tb_green_elements_dz", C.c_int, [_VP, C.c_int32, _DP, C.c_int32, _I32P, _I64P, _I32P,
+                                       C.POINTER(SolveOpts), _VP, _VP, C.POINTER(Stats), _VP]),
+    ("tb_band_energy", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP, _VP, _VP,
+                                 C.POINTER(Stats), _VP]),
     ("tb_mulliken_orbital", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.c_int32, _I32P,
                                       C.POINTER(SolveOpts), _VP, C.POINTER(Stats), _VP]),
     ("tb_mulliken_charges", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP,
@@ -341,6 +345,50 @@ def tb_green_elements(h: Handle, z, cols, row_ptr, rows, opts: SolveOpts | None 
                                          C.byref(st), _stream(stream))
     _check(s, "tb_green_elements", allow_unconverged)
     return out, _stats_dict(st, conv, R, K, s)
+
+
+def tb_green_elements_dz(h: Handle, z, cols, row_ptr, rows, opts: SolveOpts | None = None, out=None, dout=None,
+                         stream=None, allow_unconverged=False):
+    """As tb_green_elements, plus dG/dz at the same elements; returns
+    (G, dG, stats)."""
+    import torch
+    zz = _complex_host(z)
+    cc = np.ascontiguousarray(cols, dtype=np.int32)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    rr = np.ascontiguousarray(rows, dtype=np.int32)
+    K, R = len(zz) // 2, len(cc)
+    if out is None:
+        out = torch.empty((int(rp[-1]), K), dtype=torch.complex128, device="cuda")
+    if dout is None:
+        dout = torch.empty((int(rp[-1]), K), dtype=torch.complex128, device="cuda")
+    opts = opts or tb_default_opts()
+    st, conv = _stats(R, K, True)
+    s = load_library().tb_green_elements_dz(h.ptr, K, _ptr(zz, C.c_double), R, _ptr(cc, C.c_int32),
+                                            _ptr(rp, C.c_int64), _ptr(rr, C.c_int32), C.byref(opts), _out_ptr(out),
+                                            _out_ptr(dout), C.byref(st), _stream(stream))
+    _check(s, "tb_green_elements_dz", allow_unconverged)
+    return out, dout, _stats_dict(st, conv, R, K, s)
+
+
+def tb_band_energy(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None, n_values=None, stream=None,
+                   allow_unconverged=False):
+    """Band energy E and dE/dH, dE/dS in the caller's block layout (length
+    ``n_values`` = len(S_vals)); returns (E, dE_dH, dE_dS, stats) as numpy."""
+    zz = _complex_host(z)
+    ww = _complex_host(w)
+    K = len(zz) // 2
+    if n_values is None:
+        raise ValueError("n_values (the length of the S_vals array) is required")
+    E = np.zeros(1)
+    gH = np.zeros(int(n_values))
+    gS = np.zeros(int(n_values))
+    opts = opts or tb_default_opts()
+    st, _ = _stats(h.n_orb, K, False)
+    s = load_library().tb_band_energy(h.ptr, K, _ptr(zz, C.c_double), _ptr(ww, C.c_double), float(g_s),
+                                      C.byref(opts), _out_ptr(E), _out_ptr(gH), _out_ptr(gS), C.byref(st),
+                                      _stream(stream))
+    _check(s, "tb_band_energy", allow_unconverged)
+    return float(E[0]), gH, gS, _stats_dict(st, None, h.n_orb, K, s)
 
 
 def tb_mulliken_orbital(h: Handle, z, w, cols, g_s=2.0, opts: SolveOpts | None = None, out=None, stream=None,

@@ -1,0 +1,120 @@
+"""z-derivatives of Green's function elements and the band energy with its
+gradients on the GPU, against the oracle: the dense definitions
+(-G S G, Tr(rho H), dE/dH, dE/dS) at convergence, and the oracle's
+forward-differentiated recurrences after a fixed number of steps."""
+import numpy as np
+import pytest
+
+from tbinputs import si_system, water_system, linspace_grid
+from oracle import dense, method
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_1202_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def si():
+    s = si_system((2, 2, 2), sigma=0.05, seed=1)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    return s, H, S
+
+
+def _rows(cols, rng, N):
+    rows, ptr = [], [0]
+    for j in cols:
+        r = sorted(set([int(j)] + list(rng.choice(N, 6, replace=False))))
+        rows += r
+        ptr.append(len(rows))
+    return np.array(ptr), np.array(rows)
+
+
+def _dense_blocks(s, vals):
+    """Values in the block layout of S_vals -> dense (N, N) matrix."""
+    N = s.n_orb
+    oo = s.orb_offset()
+    bo = s.block_offsets()
+    M = np.zeros((N, N))
+    for i in range(s.n_atoms):
+        ni = s.orb_per_atom[i]
+        for b in range(s.brow_ptr[i], s.brow_ptr[i + 1]):
+            j = s.bcol[b]
+            nj = s.orb_per_atom[j]
+            M[oo[i]:oo[i] + ni, oo[j]:oo[j] + nj] = vals[bo[b]:bo[b + 1]].reshape(ni, nj)
+    return M
+
+
+@pytest.mark.parametrize("prec,force", [(0, 0), (1, 0), (0, 5)], ids=["fp64", "mixed", "fp64-switches"])
+def test_green_elements_dz_dense(P, si, prec, force):
+    s, H, S = si
+    z, w = linspace_grid(16, -20.0, 5.0, 1.0)
+    cols = [3, 77, 200]
+    ptr, rows = _rows(cols, np.random.default_rng(2), s.n_orb)
+    h = P.tb_create_system(s)
+    opts = P.tb_default_opts(precision=prec, force_switch_every=force)
+    G, dG, st = P.tb_green_elements_dz(h, z, cols, ptr, rows, opts=opts)
+    G, dG = G.cpu().numpy(), dG.cpu().numpy()
+    Gd = dense.green_columns(H, S, z, cols)
+    dGd = dense.green_derivative_columns(H, S, z, cols)
+    for c in range(len(cols)):
+        for m in range(ptr[c], ptr[c + 1]):
+            assert np.abs(G[m] - Gd[:, rows[m], c]).max() <= 1e-7 * np.abs(Gd[:, :, c]).max()
+            assert np.abs(dG[m] - dGd[:, rows[m], c]).max() <= 1e-6 * np.abs(dGd[:, :, c]).max()
+
+
+def test_green_elements_dz_fixed_steps_match_method(P, si):
+    s, H, S = si
+    z, w = linspace_grid(16, -20.0, 5.0, 0.5)
+    n = 25
+    cols = [5, 130]
+    ptr, rows = _rows(cols, np.random.default_rng(4), s.n_orb)
+    h = P.tb_create_system(s)
+    opts = P.tb_default_opts(max_iter=n, force_switch_every=7)
+    G, dG, st = P.tb_green_elements_dz(h, z, cols, ptr, rows, opts=opts, allow_unconverged=True)
+    dG = dG.cpu().numpy()
+    for c, j in enumerate(cols):
+        F = np.eye(s.n_orb)[rows[ptr[c]:ptr[c + 1]]]
+        ref = method.generalized_shifted_cocg(H, S, z, j, max_iter=n, force_switch_every=7, derivative=True,
+                                              functionals=F, keep_full=False)["dt"]
+        got = dG[ptr[c]:ptr[c + 1]].T
+        assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_band_energy_and_gradients(P, prec):
+    s = water_system(8, seed=4, cutoff=3.0, excess_proton=False)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(16, -40.0, -8.0, 1.0)
+    h = P.tb_create_system(s)
+    E, gH, gS, st = P.tb_band_energy(h, z, w, opts=P.tb_default_opts(precision=prec), n_values=len(s.S_vals))
+    assert st["status"] == "TB_OK"
+    Ed = dense.band_energy(H, S, z, w)
+    assert abs(E - Ed) <= 1e-8 * abs(Ed)
+    gHd, gSd = dense.band_energy_gradients(H, S, z, w)
+    mask = _dense_blocks(s, np.ones(len(s.S_vals))) > 0
+    assert np.abs(_dense_blocks(s, gH)[mask] - gHd[mask]).max() <= 1e-7 * np.abs(gHd).max()
+    assert np.abs(_dense_blocks(s, gS)[mask] - gSd[mask]).max() <= 1e-7 * np.abs(gSd).max()
+
+
+def test_band_energy_of_a_batch(P):
+    a = water_system(8, seed=4, cutoff=3.0, excess_proton=False)
+    b = si_system((2, 2, 2), sigma=0.05, seed=1)
+    z, w = linspace_grid(16, -40.0, 0.0, 1.0)
+    hb = P.tb_create_batch([a, b])
+    n_vals = len(a.S_vals) + len(b.S_vals)
+    E, gH, gS, _ = P.tb_band_energy(hb, z, w, n_values=n_vals)
+    Ea, gHa, gSa, _ = P.tb_band_energy(P.tb_create_system(a), z, w, n_values=len(a.S_vals))
+    Eb, gHb, gSb, _ = P.tb_band_energy(P.tb_create_system(b), z, w, n_values=len(b.S_vals))
+    assert abs(E - (Ea + Eb)) <= 1e-9 * abs(E)
+    assert np.abs(gH - np.concatenate([gHa, gHb])).max() <= 1e-9 * np.abs(gH).max()
+    assert np.abs(gS - np.concatenate([gSa, gSb])).max() <= 1e-9 * np.abs(gS).max()
