@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the other precision, reported beside the headline (0: skip)")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the band-energy gradient measurement")
     ap.add_argument("--csc-scf", type=int, default=1,
                     help="timed SCF iterations of the charge-self-consistency measurement (0: skip)")
     return ap.parse_args()
@@ -156,6 +157,33 @@ def batch_measure(P, prec, panel):
             "batched_shift_rhs_iterations_per_s": 64 * it_b / t_b,
             "per_box_shift_rhs_iterations_per_s": 64 * it_s / t_s,
             "batched_s": t_b, "per_box_s": t_s, "speedup": t_s / t_b}
+
+
+def adjoint_measure(P, prec, panel):
+    """Band energy with dE/dH and dE/dS (every column of the system, its
+    pattern rows projected with their z-derivatives) on Si 512 atoms (4x4x4
+    cells, N = 2048, 68 pattern rows per column), 64 Gauss-Legendre shifts on
+    [-20, 5] eV + 1i eV, tol 1e-8; timed with CUDA events."""
+    import torch
+    from tbinputs import si_system, gauss_legendre_grid
+    s = si_system((4, 4, 4), sigma=0.05, seed=3)
+    z, w = gauss_legendre_grid(64, -20.0, 5.0, 1.0)
+    h = P.tb_create_system(s)
+    opts = P.tb_default_opts(tol=1e-8, precision=prec, panel=panel)
+    P.tb_band_energy(h, z, w, opts=opts, n_values=len(s.S_vals))        # warm-up
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    E, gH, gS, st = P.tb_band_energy(h, z, w, opts=opts, n_values=len(s.S_vals))
+    ev1.record(stream)
+    ev1.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    return {"workload": "band energy + dE/dH, dE/dS: Si 512 atoms (4x4x4 cells), N=2048, all columns, pattern "
+                        "rows and z-derivatives projected, 64 GL shifts on [-20,5] eV + 1i eV, tol 1e-8",
+            "n_atoms": s.n_atoms, "N": s.n_orb, "gradient_entries": len(s.S_vals), "panel": panel, "seconds": t,
+            "shift_rhs_iterations_per_s": 64 * st["outer_iterations"] / t, "E_eV": E}
 
 
 def rank_columns(n_orb, panel, rank, seed=100):
@@ -562,6 +590,8 @@ def run_ours(args):
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
                                        / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),
     }
+    if world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_measure(P, prec, args.panel)
     if world == 1 and not args.no_batch:
         line["batch"] = batch_measure(P, prec, args.panel)
     if world == 1 and args.csc_scf > 0:
