@@ -1828,6 +1828,9 @@ static int gmax() {
 
 // Raise (never lower) a kernel's dynamic shared-memory limit: threads of a
 // ragged batch may launch the same kernel with different sizes at once.
+// The tracked limit starts at 0, so the attribute is always set explicitly:
+// the 48 KB default covers static plus dynamic shared memory, and a size
+// just under it can still be refused.
 static bool ensure_dyn_smem(const void* kernel, size_t bytes, size_t& current) {
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
@@ -1955,7 +1958,7 @@ static size_t shift_smem(const PanelDev& p) {
 }
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     const size_t sm = shift_smem(p);
-    static size_t lim_init = 48 * 1024;
+    static size_t lim_init = 0;
     ensure_dyn_smem((const void*)k_shift_init, sm, lim_init);
     {
         LaunchScope ls_(K_OTHER, st);
@@ -1968,7 +1971,7 @@ void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
 }
 void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
     const size_t sm = shift_smem(p);
-    static size_t lim_step = 48 * 1024;
+    static size_t lim_step = 0;
     ensure_dyn_smem((const void*)k_shift_step, sm, lim_step);
     {
         LaunchScope ls_(K_SHIFT_STEP, st);
