@@ -772,11 +772,14 @@ __device__ void inner32_ticket_tail(const PanelDev& p, int it) {
 // CPT complex columns per thread (2: one float4 per orbital row), P / CPT
 // threads per block row; the block-column index of the next block is loaded
 // one block ahead so the panel-row gathers do not wait on it.
-template <int CPT>
+// PW: the panel width as a compile-time constant (4 ... 256: row strides
+// fold into the load offsets; measured 4 % faster at 256 columns), 0 for
+// any width at run time.
+template <int CPT, int PW = 0>
 __global__ void __launch_bounds__(THREADS, 4) k_inner32_spmv(DevSystem s, PanelDev p, int it) {
     __shared__ double smem[4 * CPT * THREADS];
     if (*(volatile int*)&p.flags[1] == 0) return;
-    const int P = p.P;
+    const int P = PW > 0 ? PW : p.P;
     const int TPR = P / CPT;                    // threads per block row
     const int t0 = threadIdx.x % TPR;
     const int c0 = t0 * CPT;
@@ -808,9 +811,10 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_spmv(DevSystem s, PanelD
                 const int J = Jn;
                 if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
                 float xv[4][2 * CPT];
+                const float2* xb = p.r32 + (size_t)(4 * J) * P + c0;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float2* xr = p.r32 + (size_t)(4 * J + e) * P + c0;
+                    const float2* xr = xb + e * P;
                     if (CPT == 2) {
                         const float4 q4 = *reinterpret_cast<const float4*>(xr);
                         xv[e][0] = q4.x; xv[e][1] = q4.y; xv[e][2] = q4.z; xv[e][3] = q4.w;
@@ -1941,8 +1945,19 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
         }();
         (void)attr;
         k_inner32_spmv_grp<<<s.n_groups * (p.P / PC), s.grpG * (PC / 2), sm, st>>>(s, p, it);
-    } else if (p.P >= 2)
-        k_inner32_spmv<2><<<grid_for((long long)s.n_atoms * (p.P / 2)), THREADS, 0, st>>>(s, p, it);
+    } else if (p.P >= 2) {
+        const int g = grid_for((long long)s.n_atoms * (p.P / 2));
+        switch (p.P) {
+            case 256: k_inner32_spmv<2, 256><<<g, THREADS, 0, st>>>(s, p, it); break;
+            case 128: k_inner32_spmv<2, 128><<<g, THREADS, 0, st>>>(s, p, it); break;
+            case 64: k_inner32_spmv<2, 64><<<g, THREADS, 0, st>>>(s, p, it); break;
+            case 32: k_inner32_spmv<2, 32><<<g, THREADS, 0, st>>>(s, p, it); break;
+            case 16: k_inner32_spmv<2, 16><<<g, THREADS, 0, st>>>(s, p, it); break;
+            case 8: k_inner32_spmv<2, 8><<<g, THREADS, 0, st>>>(s, p, it); break;
+            case 4: k_inner32_spmv<2, 4><<<g, THREADS, 0, st>>>(s, p, it); break;
+            default: k_inner32_spmv<2><<<g, THREADS, 0, st>>>(s, p, it); break;
+        }
+    }
     else
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
 }
