@@ -274,3 +274,28 @@ def band_energy_gradients(H, S, z, w, g_s=2.0):
         gH += wk * zk * GSG.T
         gS += wk * (zk * G.T - zk * zk * GSG.T)
     return -(g_s / math.pi) * gH.imag, -(g_s / math.pi) * gS.imag
+
+
+def forces_ased(gH, gS, dS_dd, orb_per_atom, brow_ptr, bcol, eps, K) -> np.ndarray:
+    """F_I = -dE/dR_I for H built by Eq. Hap-1 from S (charge-independent):
+    every stored entry e of block (I, J), I != J, contributes
+    v_e = (dE/dS_e + K (eps_a + eps_b) / 2 dE/dH_e) dS_e/dd with
+    d = R_J - R_I, so F_I += v_e and F_J -= v_e (on-site H is eps, constant).
+    gH, gS: dense (N, N) gradients; dS_dd: (3, n_values) in the block layout.
+    Returns (n_atoms, 3)."""
+    n = len(orb_per_atom)
+    oo = np.concatenate([[0], np.cumsum(orb_per_atom)])
+    F = np.zeros((n, 3))
+    e = 0
+    for i in range(n):
+        for b in range(brow_ptr[i], brow_ptr[i + 1]):
+            j = bcol[b]
+            for a in range(orb_per_atom[i]):
+                for c in range(orb_per_atom[j]):
+                    ra, rb = oo[i] + a, oo[j] + c
+                    if i != j:
+                        wgt = gS[ra, rb] + 0.5 * K * (eps[ra] + eps[rb]) * gH[ra, rb]
+                        F[i] += wgt * dS_dd[:, e]
+                        F[j] -= wgt * dS_dd[:, e]
+                    e += 1
+    return F

@@ -215,6 +215,64 @@ def _pairs(pos, box, pbc, cutoff):
     return pairs, d
 
 
+def bond_blocks(A, B, D) -> np.ndarray:
+    """Overlap blocks <phi_A(0) | phi_B(d)> for bond vectors D (n, 3), Angstrom:
+    STO bond integrals in the bond frame, Slater-Koster rotation (s, then p
+    along x, y, z).  Returns (n, A.n_orb, B.n_orb)."""
+    D = np.atleast_2d(np.asarray(D, dtype=np.float64))
+    R = np.linalg.norm(D, axis=1)
+    bi = bond_integrals(A.n, A.zeta, B.n, B.zeta, R / BOHR_ANGSTROM)
+    u = D / R[:, None]
+    blk = np.zeros((len(D), A.n_orb, B.n_orb))
+    blk[:, 0, 0] = bi["ss"]
+    if B.l == 1:
+        blk[:, 0, 1:] = u * bi["sp"][:, None]
+    if A.l == 1:
+        blk[:, 1:, 0] = u * bi["ps"][:, None]
+    if A.l == 1 and B.l == 1:
+        uu = u[:, :, None] * u[:, None, :]
+        blk[:, 1:, 1:] = uu * bi["pp_sigma"][:, None, None] + (np.eye(3)[None] - uu) * bi["pp_pi"][:, None, None]
+    return blk
+
+
+def overlap_bond_derivatives(system, h=1e-5) -> np.ndarray:
+    """dS_e / dd for every stored entry e of S_vals, d = R_J - R_I the
+    (minimum-image) bond vector of the entry's block (I, J), by central
+    differences of ``bond_blocks`` (step h Angstrom); zero on diagonal
+    blocks.  Returns (3, len(S_vals)).  Geometry input for forces: the
+    derivative of the overlap with respect to the atom positions."""
+    s = system
+    pos = np.asarray(s.positions, dtype=np.float64)
+    box = np.asarray(s.box, dtype=np.float64)
+    bo = s.block_offsets()
+    out = np.zeros((3, len(s.S_vals)))
+    rows = np.repeat(np.arange(s.n_atoms), np.diff(s.brow_ptr))
+    for b in range(s.nb):
+        i, j = rows[b], s.bcol[b]
+        if i == j:
+            continue
+        d = pos[j] - pos[i]
+        for ax in range(3):
+            if s.pbc[ax]:
+                d[ax] -= box[ax] * np.round(d[ax] / box[ax])
+        A, B = s.species[i], s.species[j]
+        for ax in range(3):
+            e = np.zeros(3)
+            e[ax] = h
+            diff = (bond_blocks(A, B, d + e) - bond_blocks(A, B, d - e))[0] / (2 * h)
+            out[ax, bo[b]:bo[b + 1]] = diff.ravel()
+    return out
+
+
+def displaced(system, atom, axis, delta):
+    """The same system with one atom moved by delta (Angstrom) along an
+    axis, rebuilt with the original cutoff (same blocks for small moves)."""
+    s = system
+    pos = np.array(s.positions, dtype=np.float64)
+    pos[atom, axis] += delta
+    return build_system(s.species, pos, s.box, s.pbc, s.meta.get("cutoff", 4.0), s.K, meta=s.meta)
+
+
 def build_system(species, pos, box, pbc, cutoff, K=1.75, meta=None) -> TBSystem:
     """Overlap matrix in block-sparse form for atoms within ``cutoff``
     (Angstrom, minimum image along periodic axes)."""
@@ -237,7 +295,6 @@ def build_system(species, pos, box, pbc, cutoff, K=1.75, meta=None) -> TBSystem:
     np.cumsum(sizes, out=boff[1:])
     vals = np.zeros(boff[-1])
     sp_idx = np.array([list(SPECIES).index(s.name) for s in species])
-    R = np.linalg.norm(D, axis=1)
     diag = I == J
     # diagonal blocks: normalised orbitals, same-atom s-p overlap vanishes
     for b in np.nonzero(diag)[0]:
@@ -255,19 +312,8 @@ def build_system(species, pos, box, pbc, cutoff, K=1.75, meta=None) -> TBSystem:
             A, B = SPECIES[names[ta]], SPECIES[names[tb]]
             for c0 in range(0, len(sel), 4096):
                 ch = sel[c0:c0 + 4096]
-                bi = bond_integrals(A.n, A.zeta, B.n, B.zeta, R[ch] / BOHR_ANGSTROM)
-                u = D[ch] / R[ch, None]
+                blk = bond_blocks(A, B, D[ch])
                 na, nbo = A.n_orb, B.n_orb
-                blk = np.zeros((len(ch), na, nbo))
-                blk[:, 0, 0] = bi["ss"]
-                if B.l == 1:
-                    blk[:, 0, 1:] = u * bi["sp"][:, None]
-                if A.l == 1:
-                    blk[:, 1:, 0] = u * bi["ps"][:, None]
-                if A.l == 1 and B.l == 1:
-                    uu = u[:, :, None] * u[:, None, :]
-                    blk[:, 1:, 1:] = uu * bi["pp_sigma"][:, None, None] + \
-                        (np.eye(3)[None] - uu) * bi["pp_pi"][:, None, None]
                 idx = boff[ch][:, None] + np.arange(na * nbo)[None, :]
                 vals[idx] = blk.reshape(len(ch), -1)
                 tr = np.searchsorted(keys, J[ch].astype(np.int64) * n + I[ch])

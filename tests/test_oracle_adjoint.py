@@ -10,7 +10,10 @@ facts that do not come from the oracle itself:
 * E = Tr(rho H) against the eigenvalue closed form
   -(g_s/pi) Im sum_k w_k sum_m eps_m / (z_k - eps_m);
 * dE/dH and dE/dS against central differences of E under symmetric
-  perturbations of H and of S.
+  perturbations of H and of S;
+* forces (chain rule through dE/dS, dE/dH and the geometry derivative of S)
+  against central differences of E under atom displacements, and zero net
+  force.
 """
 import math
 
@@ -99,3 +102,25 @@ def test_band_energy_gradients_match_differences(small):
             fd = (dense.band_energy(H, S + h * D, z, w) - dense.band_energy(H, S - h * D, z, w)) / (2 * h)
         analytic = float(np.sum(grad * D))
         assert abs(fd - analytic) <= 1e-6 * max(1.0, abs(analytic)), which
+
+
+def test_forces_match_differences_of_energy(small):
+    """F = -dE/dR by the chain rule through dE/dS, dE/dH and the geometry
+    derivative of S, against central differences of the dense band energy
+    of displaced systems (S and the Eq. Hap-1 H rebuilt)."""
+    from tbinputs import overlap_bond_derivatives, displaced
+    s, H, S = small
+    z, w = linspace_grid(16, -40.0, -8.0, 1.0)
+    gH, gS = dense.band_energy_gradients(H, S, z, w)
+    F = dense.forces_ased(gH, gS, overlap_bond_derivatives(s), s.orb_per_atom, s.brow_ptr, s.bcol, s.eps, s.K)
+    assert np.abs(F.sum(axis=0)).max() <= 1e-8 * np.abs(F).max()      # no net force: translation invariance
+    h = 1e-4
+    for atom in (0, 5, 13):
+        for ax in range(3):
+            Es = []
+            for sgn in (1, -1):
+                sd = displaced(s, atom, ax, sgn * h)
+                Sd = sd.dense_S()
+                Es.append(dense.band_energy(dense.ased_hamiltonian(Sd, sd.eps, sd.K, sd.orbital_atom()), Sd, z, w))
+            fd = -(Es[0] - Es[1]) / (2 * h)
+            assert abs(F[atom, ax] - fd) <= 1e-5 * max(1.0, np.abs(F).max())
