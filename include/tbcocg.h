@@ -212,6 +212,22 @@ tb_status tb_band_energy(tb_handle *h, int32_t K, const double *z, const double 
                          void *stream);
 
 /*
+ * Forces F_I = -dE/dR_I from the band-energy gradients of tb_band_energy
+ * (chain rule through the geometry): every stored entry e of an off-site
+ * block (I, J) contributes v_e = dE/dS_e dS_e/dd + dE/dH_e dH_e/dd, with
+ * d = R_J - R_I the block's bond vector, as F_I += v_e, F_J -= v_e; on-site
+ * blocks do not move.  dE_dH, dE_dS: double [n_values] (tb_band_energy's
+ * outputs); dS_dd, dH_dd: double [3][n_values], the caller's geometry
+ * derivatives of every stored entry (component-major); dH_dd == NULL uses
+ * Eq. Hap-1, dH_e/dd = K (eps_a + eps_b)/2 dS_e/dd (handles whose H was
+ * built from eps and K only, else TB_ERR_INVALID_ARG).  The charge-transfer
+ * term of Eq. Hap-CSC is not included.  F_out: double [n_atoms][3]; all
+ * arrays host or device.
+ */
+tb_status tb_forces(tb_handle *h, const double *dE_dH, const double *dE_dS, const double *dS_dd,
+                    const double *dH_dd, double *F_out, void *stream);
+
+/*
  * Gross Mulliken populations of selected orbitals (Section 2.2, the
  * Mulliken partition of the charge density), from the energy integral of
  * the Green's function with the quadrature (z_k, w_k) (host, complex):

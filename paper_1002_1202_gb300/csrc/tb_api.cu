@@ -46,6 +46,9 @@ struct tb_handle {
     std::vector<int64_t> boff_h;       // [nb + 1]: first value of every block
     std::vector<int64_t> btrans_h;     // [nb]: index of the transposed block
     std::vector<double> S_h;           // [boff_h[nb]]
+    bool ased = false;                 // H built by Eq. Hap-1 from eps and K
+    double K = 0.0;
+    std::vector<double> eps_h;         // [N] caller order (Eq. Hap-1 handles)
     std::vector<int64_t> sys_atom_off;  // batch: first atom of every system, [n_systems + 1]
     std::vector<int64_t> sys_orb_off;   // batch: first orbital of every system
     // batch only: one solve view per system (block rows offset to the
@@ -1098,6 +1101,9 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     h->boff_h = boff;
     h->btrans_h = btrans;
     h->S_h.assign(d->S_vals, d->S_vals + boff[nb]);
+    h->ased = d->H_vals == nullptr;
+    h->K = d->K;
+    if (h->ased) h->eps_h.assign(d->eps, d->eps + N);
     h->orb2pad_h = o2p;
     h->ds.n_atoms = n;
     h->ds.nb = nb;
@@ -1322,6 +1328,36 @@ tb_status tb_green_elements_dz(tb_handle* h, int32_t K, const double* z, int32_t
     tb_status fin = out_finish(ob, st);
     if (dG_out && fin == TB_OK) fin = out_finish(obd, st);
     return merge(run, fin);
+}
+
+tb_status tb_forces(tb_handle* h, const double* dE_dH, const double* dE_dS, const double* dS_dd, const double* dH_dd,
+                    double* F_out, void* stream) {
+    if (!h || !dE_dH || !dE_dS || !dS_dd || !F_out) return TB_ERR_INVALID_ARG;
+    if (!dH_dd && !h->ased) return TB_ERR_INVALID_ARG;   // no rule for dH/dd of an explicit H
+    const int n = h->n_atoms;
+    const int64_t nb = (int64_t)h->bcol_h.size();
+    const int64_t nvals = h->boff_h.back();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    tb_status s;
+    const double *gH, *gS, *dS, *dH = nullptr, *eps = nullptr;
+    if ((s = device_view(cl, dE_dH, (size_t)nvals, &gH, st)) != TB_OK) return s;
+    if ((s = device_view(cl, dE_dS, (size_t)nvals, &gS, st)) != TB_OK) return s;
+    if ((s = device_view(cl, dS_dd, (size_t)3 * nvals, &dS, st)) != TB_OK) return s;
+    if (dH_dd && (s = device_view(cl, dH_dd, (size_t)3 * nvals, &dH, st)) != TB_OK) return s;
+    if (!dH_dd && (s = device_view(cl, h->eps_h.data(), h->eps_h.size(), &eps, st)) != TB_OK) return s;
+    const int64_t *boff, *btr;
+    if ((s = device_view(cl, h->boff_h.data(), h->boff_h.size(), &boff, st)) != TB_OK) return s;
+    if ((s = device_view(cl, h->btrans_h.data(), h->btrans_h.size(), &btr, st)) != TB_OK) return s;
+    double* vblk = nullptr;
+    if ((s = dalloc(cl, &vblk, (size_t)3 * nb)) != TB_OK) return s;
+    OutBuf ob;
+    if ((s = out_prepare(cl, ob, F_out, sizeof(double) * 3 * (size_t)n)) != TB_OK) return s;
+    launch_force_blocks(n, h->ds.brow, h->ds.bcol, boff, h->atom_orb_off, gH, gS, dS, dH, eps, h->K, nvals, vblk, st);
+    launch_force_atoms(n, h->ds.brow, h->ds.bcol, btr, vblk, static_cast<double*>(ob.dev), st);
+    TB_CK(cudaGetLastError());
+    return out_finish(ob, st);
 }
 
 tb_status tb_band_energy(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,

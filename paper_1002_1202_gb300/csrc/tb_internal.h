@@ -165,6 +165,11 @@ void launch_band_energy_terms(const double2* G, const double2* dG, const double*
                               const double2* z, const double2* w, double g_s, double* e_terms, double* gH,
                               double* gS, cudaStream_t st);
 void launch_sum_fixed(const double* v, int64_t n, double* out, cudaStream_t st);
+void launch_force_blocks(int n_atoms, const int* brow, const int* bcol, const int64_t* boff, const int64_t* ooff,
+                         const double* gH, const double* gS, const double* dS_dd, const double* dH_dd,
+                         const double* eps, double K, int64_t nvals, double* vblk, cudaStream_t st);
+void launch_force_atoms(int n_atoms, const int* brow, const int* bcol, const int64_t* btrans, const double* vblk,
+                        double* F, cudaStream_t st);
 void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, double g_s, double* out,
                             cudaStream_t st);
 

@@ -1669,6 +1669,73 @@ __global__ void k_scatter_cols(const double* __restrict__ tmp, const int32_t* __
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < Rq; c += gridDim.x * blockDim.x) out[pos[c]] = tmp[c];
 }
 
+
+// ---------------------------------------------------------------------------
+// Forces from the band-energy gradients (chain rule through the geometry)
+// ---------------------------------------------------------------------------
+
+// v_b = sum over the entries e of off-site block b = (I, J) of
+// dE/dS_e dS_e/dd + dE/dH_e dH_e/dd (d = R_J - R_I); dH_dd == nullptr: the
+// Eq. Hap-1 rule, dH_e/dd = K (eps_a + eps_b) / 2 dS_e/dd.  One warp per
+// block row, lanes over its blocks.
+__global__ void k_force_blocks(int n_atoms, const int* __restrict__ brow, const int* __restrict__ bcol,
+                               const int64_t* __restrict__ boff, const int64_t* __restrict__ ooff,
+                               const double* __restrict__ gH, const double* __restrict__ gS,
+                               const double* __restrict__ dS_dd, const double* __restrict__ dH_dd,
+                               const double* __restrict__ eps, double K, int64_t nvals, double* __restrict__ vblk) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long I = warp; I < n_atoms; I += nw) {
+        const int ni = (int)(ooff[I + 1] - ooff[I]);
+        for (int b = brow[I] + lane; b < brow[I + 1]; b += 32) {
+            const int J = bcol[b];
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+            if (J != I) {
+                const int nj = (int)(ooff[J + 1] - ooff[J]);
+                for (int a = 0; a < ni; ++a)
+                    for (int c = 0; c < nj; ++c) {
+                        const int64_t e = boff[b] + (int64_t)a * nj + c;
+                        double ws = gS[e], wh = gH[e];
+                        if (dH_dd) {
+                            v0 += ws * dS_dd[e] + wh * dH_dd[e];
+                            v1 += ws * dS_dd[nvals + e] + wh * dH_dd[nvals + e];
+                            v2 += ws * dS_dd[2 * nvals + e] + wh * dH_dd[2 * nvals + e];
+                        } else {
+                            const double w = ws + 0.5 * K * (eps[ooff[I] + a] + eps[ooff[J] + c]) * wh;
+                            v0 += w * dS_dd[e];
+                            v1 += w * dS_dd[nvals + e];
+                            v2 += w * dS_dd[2 * nvals + e];
+                        }
+                    }
+            }
+            vblk[3 * (size_t)b] = v0;
+            vblk[3 * (size_t)b + 1] = v1;
+            vblk[3 * (size_t)b + 2] = v2;
+        }
+    }
+}
+
+// F_I = sum over off-site blocks (I, J) of v_(I,J) - v_(J,I), in block order
+__global__ void k_force_atoms(int n_atoms, const int* __restrict__ brow, const int* __restrict__ bcol,
+                              const int64_t* __restrict__ btrans, const double* __restrict__ vblk,
+                              double* __restrict__ F) {
+    for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < n_atoms;
+         I += (long long)gridDim.x * blockDim.x) {
+        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+        for (int b = brow[I]; b < brow[I + 1]; ++b) {
+            if (bcol[b] == I) continue;
+            const int64_t t = btrans[b];
+            f0 += vblk[3 * (size_t)b] - vblk[3 * (size_t)t];
+            f1 += vblk[3 * (size_t)b + 1] - vblk[3 * (size_t)t + 1];
+            f2 += vblk[3 * (size_t)b + 2] - vblk[3 * (size_t)t + 2];
+        }
+        F[3 * I] = f0;
+        F[3 * I + 1] = f1;
+        F[3 * I + 2] = f2;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -2115,6 +2182,21 @@ void launch_scatter_values(const double* v, const int64_t* idx, int64_t n, doubl
 void launch_scatter_cols(const double* tmp, const int32_t* pos, int Rq, double* out, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
     k_scatter_cols<<<grid_for(Rq), THREADS, 0, st>>>(tmp, pos, Rq, out);
+}
+
+
+void launch_force_blocks(int n_atoms, const int* brow, const int* bcol, const int64_t* boff, const int64_t* ooff,
+                         const double* gH, const double* gS, const double* dS_dd, const double* dH_dd,
+                         const double* eps, double K, int64_t nvals, double* vblk, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_force_blocks<<<grid_for((long long)n_atoms * 32), THREADS, 0, st>>>(n_atoms, brow, bcol, boff, ooff, gH, gS,
+                                                                           dS_dd, dH_dd, eps, K, nvals, vblk);
+}
+
+void launch_force_atoms(int n_atoms, const int* brow, const int* bcol, const int64_t* btrans, const double* vblk,
+                        double* F, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_force_atoms<<<grid_for(n_atoms), THREADS, 0, st>>>(n_atoms, brow, bcol, btrans, vblk, F);
 }
 
 }  // namespace tb

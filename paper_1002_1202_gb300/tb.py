@@ -117,6 +117,7 @@ SIGNATURES = [
                                        C.POINTER(SolveOpts), _VP, _VP, C.POINTER(Stats), _VP]),
     ("tb_band_energy", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP, _VP, _VP,
                                  C.POINTER(Stats), _VP]),
+    ("tb_forces", C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("tb_mulliken_orbital", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.c_int32, _I32P,
                                       C.POINTER(SolveOpts), _VP, C.POINTER(Stats), _VP]),
     ("tb_mulliken_charges", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP,
@@ -389,6 +390,20 @@ def tb_band_energy(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None, n_va
                                       _stream(stream))
     _check(s, "tb_band_energy", allow_unconverged)
     return float(E[0]), gH, gS, _stats_dict(st, None, h.n_orb, K, s)
+
+
+def tb_forces(h: Handle, dE_dH, dE_dS, dS_dd, dH_dd=None, stream=None):
+    """Forces (n_atoms, 3) from band-energy gradients and geometry
+    derivatives (3, n_values); dH_dd None: the Eq. Hap-1 rule."""
+    keep = []
+    nv = len(dE_dH)
+    F = np.zeros((h.n_atoms, 3))
+    s = load_library().tb_forces(h.ptr, _in_ptr(dE_dH, nv, keep), _in_ptr(dE_dS, nv, keep),
+                                 _in_ptr(np.ravel(dS_dd), 3 * nv, keep),
+                                 _in_ptr(None if dH_dd is None else np.ravel(dH_dd), 3 * nv, keep),
+                                 _out_ptr(F), _stream(stream))
+    _check(s, "tb_forces", False)
+    return F
 
 
 def tb_mulliken_orbital(h: Handle, z, w, cols, g_s=2.0, opts: SolveOpts | None = None, out=None, stream=None,

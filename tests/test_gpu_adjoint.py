@@ -1,7 +1,8 @@
 """z-derivatives of Green's function elements and the band energy with its
-gradients on the GPU, against the oracle: the dense definitions
-(-G S G, Tr(rho H), dE/dH, dE/dS) at convergence, and the oracle's
-forward-differentiated recurrences after a fixed number of steps."""
+gradients and the forces they give on the GPU, against the oracle: the
+dense definitions (-G S G, Tr(rho H), dE/dH, dE/dS, the chain rule to
+forces) at convergence, the oracle's forward-differentiated recurrences after
+a fixed number of steps, and energy differences of displaced geometries."""
 import numpy as np
 import pytest
 
@@ -118,3 +119,47 @@ def test_band_energy_of_a_batch(P):
     assert abs(E - (Ea + Eb)) <= 1e-9 * abs(E)
     assert np.abs(gH - np.concatenate([gHa, gHb])).max() <= 1e-9 * np.abs(gH).max()
     assert np.abs(gS - np.concatenate([gSa, gSb])).max() <= 1e-9 * np.abs(gS).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_forces(P, prec):
+    """Forces from the device band-energy gradients and the geometry
+    derivatives of S: the oracle's chain rule on the dense gradients, the
+    explicit-dH path, zero net force, and central differences of the dense
+    band energy under atom displacements."""
+    from tbinputs import overlap_bond_derivatives, displaced
+    s = water_system(8, seed=4, cutoff=3.0, excess_proton=False)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(16, -40.0, -8.0, 1.0)
+    h = P.tb_create_system(s)
+    E, gH, gS, st = P.tb_band_energy(h, z, w, opts=P.tb_default_opts(precision=prec), n_values=len(s.S_vals))
+    dS = overlap_bond_derivatives(s)
+    F = P.tb_forces(h, gH, gS, dS)
+    gHd, gSd = dense.band_energy_gradients(H, S, z, w)
+    Fref = dense.forces_ased(gHd, gSd, dS, s.orb_per_atom, s.brow_ptr, s.bcol, s.eps, s.K)
+    scale = np.abs(Fref).max()
+    assert np.abs(F - Fref).max() <= 1e-7 * scale
+    assert np.abs(F.sum(axis=0)).max() <= 1e-8 * scale
+    # explicit dH/dd (the Eq. Hap-1 rule written out by the caller) gives the same forces
+    oo = s.orb_offset()
+    bo = s.block_offsets()
+    rows = np.repeat(np.arange(s.n_atoms), np.diff(s.brow_ptr))
+    dH = np.zeros_like(dS)
+    for b in range(s.nb):
+        i, j = rows[b], s.bcol[b]
+        if i == j:
+            continue
+        ni, nj = s.orb_per_atom[i], s.orb_per_atom[j]
+        c = 0.5 * s.K * (s.eps[oo[i]:oo[i] + ni][:, None] + s.eps[oo[j]:oo[j] + nj][None, :])
+        dH[:, bo[b]:bo[b + 1]] = dS[:, bo[b]:bo[b + 1]] * c.ravel()[None, :]
+    assert np.abs(P.tb_forces(h, gH, gS, dS, dH) - F).max() <= 1e-12 * scale
+    # against differences of the energy of displaced geometries
+    hstep = 1e-4
+    for atom, ax in ((2, 0), (11, 2)):
+        Es = []
+        for sgn in (1, -1):
+            sd = displaced(s, atom, ax, sgn * hstep)
+            Sd = sd.dense_S()
+            Es.append(dense.band_energy(dense.ased_hamiltonian(Sd, sd.eps, sd.K, sd.orbital_atom()), Sd, z, w))
+        assert abs(F[atom, ax] + (Es[0] - Es[1]) / (2 * hstep)) <= 1e-5 * scale
