@@ -163,3 +163,42 @@ def test_forces(P, prec):
             Sd = sd.dense_S()
             Es.append(dense.band_energy(dense.ased_hamiltonian(Sd, sd.eps, sd.K, sd.orbital_atom()), Sd, z, w))
         assert abs(F[atom, ax] + (Es[0] - Es[1]) / (2 * hstep)) <= 1e-5 * scale
+
+
+def test_autograd_band_energy(P):
+    """torch.autograd through the device adjoint: gradients equal
+    tb_band_energy's, and a symmetric perturbation of S moves E by their
+    contraction (central differences)."""
+    import torch
+    from paper_1002_1202_gb300.autograd import band_energy
+    s = water_system(8, seed=4, cutoff=3.0, excess_proton=False)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(16, -40.0, -8.0, 1.0)
+    # H in the block layout of S_vals
+    oo, bo = s.orb_offset(), s.block_offsets()
+    rows = np.repeat(np.arange(s.n_atoms), np.diff(s.brow_ptr))
+    Hv = np.concatenate([H[oo[rows[b]]:oo[rows[b]] + s.orb_per_atom[rows[b]],
+                           oo[s.bcol[b]]:oo[s.bcol[b]] + s.orb_per_atom[s.bcol[b]]].ravel() for b in range(s.nb)])
+    Sv = torch.tensor(s.S_vals, dtype=torch.float64, requires_grad=True)
+    Ht = torch.tensor(Hv, dtype=torch.float64, requires_grad=True)
+    structure = (s.orb_per_atom, s.brow_ptr, s.bcol)
+    E = band_energy(structure, Sv, Ht, z, w)
+    E.backward()
+    h = P.tb_create(s.orb_per_atom, s.brow_ptr, s.bcol, s.S_vals, Hv)
+    E2, gH, gS, _ = P.tb_band_energy(h, z, w, n_values=len(s.S_vals))
+    assert abs(E.item() - E2) <= 1e-12 * abs(E2)
+    assert np.array_equal(Sv.grad.numpy(), gS) and np.array_equal(Ht.grad.numpy(), gH)
+    # symmetric perturbation of S (block (i, j) and its transpose together)
+    D = np.zeros_like(s.S_vals)
+    b = int(s.brow_ptr[3]) + 1
+    i, j = rows[b], s.bcol[b]
+    t = int(np.nonzero((rows == j) & (s.bcol == i))[0][0])
+    ni, nj = s.orb_per_atom[i], s.orb_per_atom[j]
+    blk = np.random.default_rng(1).standard_normal((ni, nj))
+    D[bo[b]:bo[b + 1]] = blk.ravel()
+    D[bo[t]:bo[t + 1]] = blk.T.ravel()
+    step = 1e-5
+    Ep = band_energy(structure, torch.tensor(s.S_vals + step * D), Ht.detach(), z, w).item()
+    Em = band_energy(structure, torch.tensor(s.S_vals - step * D), Ht.detach(), z, w).item()
+    assert abs((Ep - Em) / (2 * step) - float(np.dot(gS, D))) <= 1e-5 * max(1.0, abs(float(np.dot(gS, D))))
