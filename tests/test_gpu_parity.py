@@ -285,25 +285,37 @@ def test_max_shift_count(P, c1, h1):
 # sampled columns against the oracle's method after the same number of steps
 # ---------------------------------------------------------------------------
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
-def test_full_size_sampled_columns(P, precision):
-    import torch
+@pytest.mark.parametrize("precision,ncols,panel,sample,rtol",
+                         [(0, 64, 64, (0, 37), 1e-9), (1, 1024, 256, (0, 300, 700, 1023), 1e-7)],
+                         ids=["fp64", "mixed-bench-launch"])
+def test_full_size_sampled_columns(P, precision, ncols, panel, sample, rtol):
+    """The benchmark's system and shifts (Si 4096 atoms, 256 Gauss-Legendre
+    shifts at 0.01 eV); the mixed case in the benchmark's launch
+    configuration (1024 columns as four panels of 256 in flight, tol 1e-8,
+    inner 1e-12).  Sampled columns, from every panel, after 12 outer steps,
+    against the oracle's method on the same column.  Both sides solve
+    S r' = r only to inner_tol = 1e-12, by different solvers (FP64 CG against
+    FP32 CG inside FP64 refinement); to first order the populations then
+    differ by up to n cond(A) inner_tol ~ 12 x (40 eV / 0.01 eV) x 1e-12
+    ~ 5e-8, hence 1e-7 for the mixed case (the FP64 case runs the oracle's
+    own CG steps and agrees to 1e-9)."""
     s = si_system((8, 8, 8), sigma=0.05, seed=3, cutoff=4.0)
     z, w = gauss_legendre_grid(256, -20.0, 5.0, 0.01)
-    cols = choose_columns(s.n_orb, 64, seed=5)
+    cols = choose_columns(s.n_orb, ncols, seed=5)
     n = 12
     h = P.tb_create_system(s)
-    opts = P.tb_default_opts(max_iter=n, panel=64, precision=precision)
+    opts = P.tb_default_opts(max_iter=n, panel=panel, precision=precision, tol=1e-8, inner_tol=1e-12)
     q, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts, allow_unconverged=True)
     q = q.cpu().numpy()
     Sc = s.to_csr()
     Hc = dense.ased_hamiltonian_sparse(Sc, s.eps, s.K, s.orbital_atom())
-    for c in (0, 37):
+    for c in sample:
         j = int(cols[c])
         F = Sc[j].toarray()
-        out = method.generalized_shifted_cocg(Hc, Sc, z, j, max_iter=n, keep_full=False, functionals=F)
+        out = method.generalized_shifted_cocg(Hc, Sc, z, j, max_iter=n, keep_full=False, functionals=F,
+                                              tol=1e-8, inner_tol=1e-12)
         qref = -(2.0 / math.pi) * np.imag(np.sum(w * out["t"][:, 0]))
-        assert abs(q[c] - qref) <= 1e-9 * max(1.0, abs(qref))
+        assert abs(q[c] - qref) <= rtol * max(1.0, abs(qref))
 
 
 def test_mixed_inner_tolerances(P, c1, h1):
