@@ -64,6 +64,7 @@ def parse():
                     help="timed steps of the other precision, reported beside the headline (0: skip)")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the band-energy gradient measurement")
+    ap.add_argument("--no-lanczos", action="store_true", help="skip the batched Lanczos measurement")
     ap.add_argument("--csc-scf", type=int, default=1,
                     help="timed SCF iterations of the charge-self-consistency measurement (0: skip)")
     return ap.parse_args()
@@ -184,6 +185,38 @@ def adjoint_measure(P, prec, panel):
                         "rows and z-derivatives projected, 64 GL shifts on [-20,5] eV + 1i eV, tol 1e-8",
             "n_atoms": s.n_atoms, "N": s.n_orb, "gradient_entries": len(s.S_vals), "panel": panel, "seconds": t,
             "shift_rhs_iterations_per_s": 64 * st["outer_iterations"] / t, "E_eV": E}
+
+
+def lanczos_measure(P, s, prec, panel):
+    """Generalized Lanczos (Section 3.2) for the LDOS of many orbitals: 1024
+    seeded columns of the benchmark system as panels of ``panel`` columns,
+    100 steps each, against the single-column call (FP64, as the paper's
+    one-orbital use) on one of them; timed with CUDA events."""
+    import torch
+    cols = rank_columns(s.n_orb, 1024, 0, seed=7)
+    h = P.tb_create_system(s)
+    n_steps = 100
+    opts = P.tb_default_opts(precision=prec, panel=panel, inner_tol=1e-12)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    P.tb_generalized_lanczos_batch(h, cols[:panel], 3, opts=opts)       # warm-up
+    t_b = timed(lambda: P.tb_generalized_lanczos_batch(h, cols, n_steps, opts=opts))
+    t_1 = timed(lambda: P.tb_generalized_lanczos(h, int(cols[0]), n_steps, inner_tol=1e-12))
+    return {"workload": "generalized Lanczos, Si 4096 atoms, 1024 columns x 100 steps (panels of %d), "
+                        "vs one column" % panel,
+            "batched_s": t_b, "column_steps_per_s": 1024 * n_steps / t_b,
+            "single_column_s": t_1, "single_column_steps_per_s": n_steps / t_1,
+            "speedup_per_column": (n_steps / t_1 and (1024 * n_steps / t_b) / (n_steps / t_1))}
 
 
 def rank_columns(n_orb, panel, rank, seed=100):
@@ -602,6 +635,8 @@ def run_ours(args):
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
                                        / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),
     }
+    if world == 1 and not args.no_lanczos:
+        line["lanczos"] = lanczos_measure(P, s, prec, args.panel)
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_measure(P, prec, args.panel)
     if world == 1 and not args.no_batch:

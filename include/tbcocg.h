@@ -335,6 +335,19 @@ tb_status tb_lanczos_green(const double *a, const double *b, double norm, int32_
                            const double *z, double *G_out, void *stream);
 
 /*
+ * Generalized Lanczos for R columns at once: R independent processes (one
+ * per e_{cols[c]}) run together on panels of opts->panel columns (0: 64),
+ * their S^-1 products solved as one panel (opts->precision selects the FP64
+ * CG or FP32 CG inside FP64 refinement; opts->inner_tol their accuracy).
+ * Writes a[c][0..n_steps-1], b[c][0..n_steps] (b[c][0] = 0) and norm[c], in
+ * the layout and meaning of tb_generalized_lanczos (host or device).
+ * tb_generalized_lanczos(h, j, ...) is the case R = 1 in FP64.
+ */
+tb_status tb_generalized_lanczos_batch(tb_handle *h, int32_t R, const int32_t *cols, int32_t n_steps,
+                                       const tb_solve_opts *opts, double *a, double *b, double *norm,
+                                       void *stream);
+
+/*
  * Allocation-free generalized Lanczos.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate GPU memory while they
  * call the library -- for example code that runs with the whole device

@@ -324,6 +324,47 @@ tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_ma
     return TB_OK;
 }
 
+// Device workspace of a panel's inner solves (FP64 CG; with p.mixed the FP32
+// CG and refinement buffers too) and of its grid reductions: everything but
+// the shift state.  p.P, p.npad, p.grid and p.mixed must be set.
+tb_status alloc_inner_workspace(Cleanup& cl, PanelDev& p, cudaStream_t st) {
+    const int P = p.P;
+    const size_t nv = (size_t)p.npad * P;
+    tb_status s;
+    double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
+    for (double2** v : vecs) {
+        if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
+    }
+    if (p.mixed) {
+        float2** v32[] = {&p.r32, &p.p32, &p.s32, &p.w32, &p.x32};
+        for (float2** v : v32) {
+            if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
+            TB_CK(cudaMemsetAsync(*v, 0, sizeof(float2) * nv, st));
+        }
+        if ((s = dalloc(cl, &p.RpS, nv)) != TB_OK) return s;
+        TB_CK(cudaMemsetAsync(p.RpS, 0, sizeof(float4) * nv, st));
+        if ((s = dalloc(cl, &p.inner32, 3 * 2 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.acc32, 8 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.cgs, 4 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.cgu, 2 * P)) != TB_OK) return s;
+        if ((s = dalloc(cl, &p.ticket32, 1)) != TB_OK) return s;
+        TB_CK(cudaMemsetAsync(p.ticket32, 0, sizeof(unsigned), st));
+        if ((s = dalloc(cl, &p.dbg, 8)) != TB_OK) return s;
+        if (std::getenv("TB_TRACE")) {
+            if ((s = dalloc(cl, &p.hist, (size_t)HIST_IT * 2 * P * 4)) != TB_OK) return s;
+            TB_CK(cudaMemsetAsync(p.hist, 0, sizeof(double) * HIST_IT * 2 * P * 4, st));
+        }
+        TB_CK(cudaMemsetAsync(p.dbg, 0, 8 * sizeof(double), st));
+    }
+    if ((s = dalloc(cl, &p.col, P)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.inner, 2 * P)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.partials, (size_t)p.grid * 4 * P)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.counter, 1 + MAX_GROUPS)) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.partials2, (size_t)MAX_GROUPS * 4 * std::max(p.P, 1))) != TB_OK) return s;
+    if ((s = dalloc(cl, &p.flags, NFLAGS)) != TB_OK) return s;
+    return TB_OK;
+}
+
 tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
     const auto t0 = std::chrono::steady_clock::now();
     const int K = q.K, R = q.R;
@@ -358,41 +399,11 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
     p.inner_lo_tol = o->inner_lo_tol;
     const size_t nv = (size_t)npad * P;
     tb_status s;
-    double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
-    for (double2** v : vecs) {
-        if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
-    }
-    if (p.mixed) {
-        float2** v32[] = {&p.r32, &p.p32, &p.s32, &p.w32, &p.x32};
-        for (float2** v : v32) {
-            if ((s = dalloc(cl, v, nv)) != TB_OK) return s;
-            TB_CK(cudaMemsetAsync(*v, 0, sizeof(float2) * nv, st));
-        }
-        if ((s = dalloc(cl, &p.RpS, nv)) != TB_OK) return s;
-        TB_CK(cudaMemsetAsync(p.RpS, 0, sizeof(float4) * nv, st));
-        if ((s = dalloc(cl, &p.inner32, 3 * 2 * P)) != TB_OK) return s;
-        if ((s = dalloc(cl, &p.acc32, 8 * P)) != TB_OK) return s;
-        if ((s = dalloc(cl, &p.cgs, 4 * P)) != TB_OK) return s;
-        if ((s = dalloc(cl, &p.cgu, 2 * P)) != TB_OK) return s;
-        if ((s = dalloc(cl, &p.ticket32, 1)) != TB_OK) return s;
-        TB_CK(cudaMemsetAsync(p.ticket32, 0, sizeof(unsigned), st));
-        if ((s = dalloc(cl, &p.dbg, 8)) != TB_OK) return s;
-        if (std::getenv("TB_TRACE")) {
-            if ((s = dalloc(cl, &p.hist, (size_t)HIST_IT * 2 * P * 4)) != TB_OK) return s;
-            TB_CK(cudaMemsetAsync(p.hist, 0, sizeof(double) * HIST_IT * 2 * P * 4, st));
-        }
-        TB_CK(cudaMemsetAsync(p.dbg, 0, 8 * sizeof(double), st));
-    }
-    if ((s = dalloc(cl, &p.col, P)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.inner, 2 * P)) != TB_OK) return s;
+    if ((s = alloc_inner_workspace(cl, p, st)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.z, K)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.pi, (size_t)P * K)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.pi_prev, (size_t)P * K)) != TB_OK) return s;
     if ((s = dalloc(cl, &p.conv_iter, (size_t)P * K)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.partials, (size_t)p.grid * 4 * P)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.counter, 1 + MAX_GROUPS)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.partials2, (size_t)MAX_GROUPS * 4 * std::max(p.P, 1))) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.flags, NFLAGS)) != TB_OK) return s;
     if (q.proj == PROJ_NONE) {
         if ((s = dalloc(cl, &p.ak, (size_t)P * K)) != TB_OK) return s;
         if ((s = dalloc(cl, &p.bk, (size_t)P * K)) != TB_OK) return s;
@@ -1609,73 +1620,104 @@ tb_status tb_lanczos_green(const double* a, const double* b, double norm, int32_
     return out_finish(ob, st);
 }
 
+tb_status tb_generalized_lanczos_batch(tb_handle* h, int32_t R, const int32_t* cols, int32_t n_steps,
+                                       const tb_solve_opts* opts, double* a, double* b, double* norm,
+                                       void* stream) {
+    if (!h || !a || !b || !norm || n_steps < 1) return TB_ERR_INVALID_ARG;
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_cols(h, R, cols)) != TB_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int npad = h->ds.npad;
+    const int P = std::min(opts->panel ? opts->panel : 64, next_pow2(R));
+    Cleanup cl_out;
+    cl_out.st = st;
+    OutBuf oa, ob, on;
+    if ((s = out_prepare(cl_out, oa, a, sizeof(double) * (size_t)R * n_steps)) != TB_OK) return s;
+    if ((s = out_prepare(cl_out, ob, b, sizeof(double) * (size_t)R * (n_steps + 1))) != TB_OK) return s;
+    if ((s = out_prepare(cl_out, on, norm, sizeof(double) * (size_t)R)) != TB_OK) return s;
+    View v = whole_view(h);
+    for (int c0 = 0; c0 < R; c0 += P) {
+        const int ncols = std::min(P, R - c0);
+        Cleanup cl;
+        cl.st = st;
+        PanelDev p;
+        p.P = P;
+        p.K = 1;
+        p.npad = npad;
+        p.grid = max_grid();
+        p.inner_tol = opts->inner_tol;
+        p.mixed = opts->precision == TB_MIXED ? 1 : 0;
+        p.inner_lo_tol = opts->inner_lo_tol;
+        if ((s = alloc_inner_workspace(cl, p, st)) != TB_OK) return s;
+        const size_t nv = (size_t)npad * P;
+        double2 *U, *Uprev, *Wv;
+        if ((s = dalloc(cl, &U, nv)) != TB_OK) return s;
+        if ((s = dalloc(cl, &Uprev, nv)) != TB_OK) return s;
+        if ((s = dalloc(cl, &Wv, nv)) != TB_OK) return s;
+        // this panel's rows of the outputs ([R][n_steps], [R][n_steps + 1], [R])
+        double* ad = static_cast<double*>(oa.dev) + (size_t)c0 * n_steps;
+        double* bd = static_cast<double*>(ob.dev) + (size_t)c0 * (n_steps + 1);
+        double* nd = static_cast<double*>(on.dev) + c0;
+        double *ap, *bp, *np_;
+        if ((s = dalloc(cl, &ap, (size_t)P * n_steps)) != TB_OK) return s;
+        if ((s = dalloc(cl, &bp, (size_t)P * (n_steps + 1))) != TB_OK) return s;
+        if ((s = dalloc(cl, &np_, (size_t)P)) != TB_OK) return s;
+        std::vector<ColState> colh(P);
+        for (int c = 0; c < P; ++c) {
+            std::memset(&colh[c], 0, sizeof(ColState));
+            colh[c].active = c < ncols ? 1 : 0;
+            colh[c].row = c < ncols ? h->orb2pad_h[cols[c0 + c]] : -1;
+        }
+        TB_CK(cudaMemcpyAsync(p.col, colh.data(), sizeof(ColState) * P, cudaMemcpyHostToDevice, st));
+        TB_CK(cudaMemsetAsync(p.inner, 0, 2 * P * sizeof(InnerState), st));
+        if (p.mixed) {
+            TB_CK(cudaMemsetAsync(p.inner32, 0, sizeof(InnerState) * 3 * 2 * P, st));
+            TB_CK(cudaMemsetAsync(p.acc32, 0, sizeof(double) * 8 * P, st));
+        }
+        TB_CK(cudaMemsetAsync(p.flags, 0, NFLAGS * sizeof(int), st));
+        TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned) * (1 + MAX_GROUPS), st));
+        TB_CK(cudaMemsetAsync(Uprev, 0, sizeof(double2) * nv, st));
+        TB_CK(cudaMemsetAsync(ap, 0, sizeof(double) * P * n_steps, st));
+        TB_CK(cudaMemsetAsync(bp, 0, sizeof(double) * P * (n_steps + 1), st));
+        InnerCtx ic;
+        // u^0 = S^-1 e_j / sqrt(e_j^T S^-1 e_j); inner solves take the right-hand
+        // side in Rcur (refinement) and Rin (FP64 CG), the solution in Rp
+        launch_panel_init(h->ds, p, st);
+        if ((s = inner_solve(v, p, p.Rcur, opts->inner_max_iter, ic, st)) != TB_OK) return s;
+        launch_lz_start(p, p.Rp, U, np_, st);
+        for (int n = 0; n < n_steps; ++n) {
+            launch_lz_spmv(h->ds, h->ds.H, U, p.W, P, st);                        // H u^n
+            launch_lz_dot(p, U, p.W, ap + n, n_steps, 0, st);                     // a_n = u^T H u
+            TB_CK(cudaMemcpyAsync(p.Rin, p.W, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
+            TB_CK(cudaMemcpyAsync(p.Rcur, p.W, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
+            if ((s = inner_solve(v, p, p.Rcur, opts->inner_max_iter, ic, st)) != TB_OK) return s;  // S^-1 H u^n
+            launch_lz_combine(p, p.Rp, U, Uprev, Wv, ap + n, bp + n, n_steps, n_steps + 1, st);
+            launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, P, st);                      // S w
+            launch_lz_dot(p, Wv, p.W, bp + n + 1, n_steps + 1, 1, st);            // b_{n+1} = ||w||_S
+            launch_lz_scale(p, Wv, U, Uprev, bp + n + 1, n_steps + 1, st);
+            TB_CK(cudaGetLastError());
+        }
+        if (v.flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
+        TB_CK(cudaMemcpyAsync(ad, ap, sizeof(double) * ncols * n_steps, cudaMemcpyDeviceToDevice, st));
+        TB_CK(cudaMemcpyAsync(bd, bp, sizeof(double) * ncols * (n_steps + 1), cudaMemcpyDeviceToDevice, st));
+        TB_CK(cudaMemcpyAsync(nd, np_, sizeof(double) * ncols, cudaMemcpyDeviceToDevice, st));
+        TB_CK(cudaStreamSynchronize(st));
+    }
+    tb_status fin = out_finish(oa, st);
+    if (fin == TB_OK) fin = out_finish(ob, st);
+    if (fin == TB_OK) fin = out_finish(on, st);
+    return fin;
+}
+
 tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, double inner_tol, double* a,
                                  double* b, double* norm, void* stream) {
-    if (!h || !a || !b || !norm || n_steps < 1 || j < 0 || j >= h->n_orb) return TB_ERR_INVALID_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Cleanup cl;
-    cl.st = st;
-    tb_status s;
-    const int npad = h->ds.npad;
-    PanelDev p;
-    p.P = 1;
-    p.K = 1;
-    p.npad = npad;
-    p.grid = max_grid();
-    p.inner_tol = inner_tol > 0.0 ? inner_tol : 1e-13;
-    double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
-    for (double2** v : vecs)
-        if ((s = dalloc(cl, v, npad)) != TB_OK) return s;
-    double2 *U, *Uprev, *Wv;
-    if ((s = dalloc(cl, &U, npad)) != TB_OK) return s;
-    if ((s = dalloc(cl, &Uprev, npad)) != TB_OK) return s;
-    if ((s = dalloc(cl, &Wv, npad)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.col, 1)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.inner, 2)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.partials, (size_t)p.grid * 4)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.counter, 1 + MAX_GROUPS)) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.partials2, (size_t)MAX_GROUPS * 4 * std::max(p.P, 1))) != TB_OK) return s;
-    if ((s = dalloc(cl, &p.flags, NFLAGS)) != TB_OK) return s;
-    double *ad, *bd, *nd;
-    if ((s = dalloc(cl, &ad, n_steps)) != TB_OK) return s;
-    if ((s = dalloc(cl, &bd, (size_t)n_steps + 1)) != TB_OK) return s;
-    if ((s = dalloc(cl, &nd, 1)) != TB_OK) return s;
-    ColState cs;
-    std::memset(&cs, 0, sizeof(cs));
-    cs.active = 1;
-    cs.row = h->orb2pad_h[j];
-    TB_CK(cudaMemcpyAsync(p.col, &cs, sizeof(cs), cudaMemcpyHostToDevice, st));
-    TB_CK(cudaMemsetAsync(p.inner, 0, 2 * sizeof(InnerState), st));
-    TB_CK(cudaMemsetAsync(p.flags, 0, NFLAGS * sizeof(int), st));
-    TB_CK(cudaMemsetAsync(p.counter, 0, sizeof(unsigned) * (1 + MAX_GROUPS), st));
-    TB_CK(cudaMemsetAsync(Uprev, 0, sizeof(double2) * npad, st));
-    TB_CK(cudaMemsetAsync(ad, 0, sizeof(double) * n_steps, st));
-    TB_CK(cudaMemsetAsync(bd, 0, sizeof(double) * (n_steps + 1), st));
-    int pred = 64;
-    int64_t inner_total = 0;
-    const int inner_max = 1000;
-    View hv = whole_view(h);
-    launch_panel_init(h->ds, p, st);
-    if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
-    launch_lz_start(p, p.Rp, cs.row, U, nd, st);
-    for (int n = 0; n < n_steps; ++n) {
-        launch_lz_spmv(h->ds, h->ds.H, U, p.W, st);                  // H u^n
-        launch_lz_dot(p, U, p.W, ad + n, 0, st);                     // a_n = u^T H u
-        TB_CK(cudaMemcpyAsync(p.Rin, p.W, sizeof(double2) * npad, cudaMemcpyDeviceToDevice, st));
-        if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;   // S^-1 H u^n
-        launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, st);  // w = S^-1 H u - a u - b u_prev
-        launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, st);                 // S w
-        launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, st);                // b_{n+1} = ||w||_S
-        launch_lz_scale(p, Wv, U, Uprev, bd + n + 1, st);
-        TB_CK(cudaGetLastError());
-    }
-    if (h->flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
-    const bool ad_dev = is_device_ptr(a), bd_dev = is_device_ptr(b), nd_dev = is_device_ptr(norm);
-    TB_CK(cudaMemcpyAsync(a, ad, sizeof(double) * n_steps, ad_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    TB_CK(cudaMemcpyAsync(b, bd, sizeof(double) * (n_steps + 1), bd_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    TB_CK(cudaMemcpyAsync(norm, nd, sizeof(double), nd_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    TB_CK(cudaStreamSynchronize(st));
-    return TB_OK;
+    if (!h || j < 0 || j >= h->n_orb) return TB_ERR_INVALID_ARG;
+    tb_solve_opts o;
+    tb_default_opts(&o);
+    o.inner_tol = inner_tol > 0.0 ? inner_tol : 1e-13;
+    const int32_t col = j;
+    return tb_generalized_lanczos_batch(h, 1, &col, n_steps, &o, a, b, norm, stream);
 }
 
 }  // extern "C"
@@ -1786,16 +1828,16 @@ tb_status tb_generalized_lanczos_noalloc(tb_handle* h, int32_t j, int32_t n_step
     View hv = whole_view(h);
     launch_panel_init(h->ds, p, st);
     if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
-    launch_lz_start(p, p.Rp, cs.row, U, nd, st);
+    launch_lz_start(p, p.Rp, U, nd, st);
     for (int n = 0; n < n_steps; ++n) {
-        launch_lz_spmv(h->ds, h->ds.H, U, p.W, st);
-        launch_lz_dot(p, U, p.W, ad + n, 0, st);
+        launch_lz_spmv(h->ds, h->ds.H, U, p.W, 1, st);
+        launch_lz_dot(p, U, p.W, ad + n, 1, 0, st);
         TB_CK(cudaMemcpyAsync(p.Rin, p.W, sizeof(double2) * npad, cudaMemcpyDeviceToDevice, st));
         if ((s = inner_cg(hv, p, inner_max, pred, inner_total, st)) != TB_OK) return s;
-        launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, st);
-        launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, st);
-        launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, st);
-        launch_lz_scale(p, Wv, U, Uprev, bd + n + 1, st);
+        launch_lz_combine(p, p.Rp, U, Uprev, Wv, ad + n, bd + n, 1, 1, st);
+        launch_lz_spmv(h->ds, h->ds.S, Wv, p.W, 1, st);
+        launch_lz_dot(p, Wv, p.W, bd + n + 1, 1, 1, st);
+        launch_lz_scale(p, Wv, U, Uprev, bd + n + 1, 1, st);
         TB_CK(cudaGetLastError());
     }
     if (h->flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;

@@ -190,15 +190,14 @@ void launch_csc_mix(const double* q, const double* q_ref, const double* dq_in, d
 void launch_lanczos_green(const double* a, const double* b, double norm, int n_steps, int K, const double2* z,
                           double2* G, cudaStream_t st);
 
-// generalized Lanczos helpers (single real column carried in a P = 1 panel)
-void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, cudaStream_t st);
-void launch_lz_dot(const PanelDev& p, const double2* x, const double2* y, double* out, int mode,
+// generalized Lanczos on a panel of P independent columns (Section 3.2)
+void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, int P, cudaStream_t st);
+void launch_lz_dot(const PanelDev& p, const double2* x, const double2* y, double* out, int stride, int mode,
                    cudaStream_t st);
 void launch_lz_combine(const PanelDev& p, const double2* y, double2* u, double2* u_prev, double2* w,
-                       const double* a, const double* b, cudaStream_t st);
-void launch_lz_scale(const PanelDev& p, double2* w, double2* u, double2* u_prev, const double* bnext,
+                       const double* a, const double* b, int sa, int sb, cudaStream_t st);
+void launch_lz_scale(const PanelDev& p, double2* w, double2* u, double2* u_prev, const double* bnext, int sb,
                      cudaStream_t st);
-void launch_lz_start(const PanelDev& p, const double2* v, int row, double2* u, double* nrm2,
-                     cudaStream_t st);
+void launch_lz_start(const PanelDev& p, const double2* v, double2* u, double* nrm2, cudaStream_t st);
 
 }  // namespace tb

@@ -1476,51 +1476,84 @@ __global__ void k_mulliken_output(PanelDev p, int ncols, const double2* __restri
 // Generalized Lanczos helpers (Section 3.2), one real vector stored in the
 // real part of a P = 1 panel column.
 // ---------------------------------------------------------------------------
+// Generalized Lanczos on a panel of P columns (Section 3.2), one
+// independent process per column; vectors [npad][P], real parts only.
+// y = M x for M = H or S
 __global__ void k_lz_spmv(DevSystem s, const double* __restrict__ M, const double2* __restrict__ x,
-                          double2* __restrict__ y) {
-    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < s.n_atoms; I += gridDim.x * blockDim.x) {
+                          double2* __restrict__ y, int P) {
+    const long long items = (long long)s.n_atoms * P;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(idx / P), c = (int)(idx % P);
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
             const int J = s.bcol[b];
+            double xv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) xv[e] = x[(size_t)(4 * J + e) * P + c].x;
+#pragma unroll
             for (int a = 0; a < 4; ++a)
-                for (int e = 0; e < 4; ++e) acc[a] += M[16 * (size_t)b + 4 * a + e] * x[4 * J + e].x;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[a] += M[16 * (size_t)b + 4 * a + e] * xv[e];
         }
-        for (int a = 0; a < 4; ++a) y[4 * I + a] = cmk(acc[a], 0.0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) y[(size_t)(4 * I + a) * P + c] = cmk(acc[a], 0.0);
     }
 }
 
+// out[c * stride] = x_c^T y_c (mode 0) or sqrt(x_c^T y_c) (mode 1)
 __global__ void __launch_bounds__(THREADS) k_lz_dot(PanelDev p, const double2* __restrict__ x,
-                                                    const double2* __restrict__ y, double* out, int mode) {
+                                                    const double2* __restrict__ y, double* out, int stride, int mode) {
     __shared__ double smem[THREADS];
+    const int P = p.P;
     double v[1] = {0.0};
-    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS)
+    const long long items = (long long)p.npad * P;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < items; i += (long long)gridDim.x * THREADS)
         v[0] += x[i].x * y[i].x;
-    if (grid_reduce_cols<1>(v, 1, p, smem)) {
-        if (threadIdx.x == 0) *out = (mode == 0) ? smem[0] : sqrt(fmax(smem[0], 0.0));
+    if (grid_reduce_cols<1>(v, P, p, smem)) {
+        if (threadIdx.x < P) {
+            const double t = smem[threadIdx.x];
+            out[(size_t)threadIdx.x * stride] = (mode == 0) ? t : sqrt(fmax(t, 0.0));
+        }
     }
 }
 
-__global__ void k_lz_start(PanelDev p, const double2* __restrict__ v, int row, double2* __restrict__ u,
-                           double* nrm2) {
-    const double n2 = v[row].x;
-    const double inv = 1.0 / sqrt(n2);
-    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS)
-        u[i] = cmk(v[i].x * inv, 0.0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *nrm2 = n2;
+// u_c = v_c / sqrt(n2_c), n2_c = v[row_c][c] = e_j^T S^-1 e_j (inactive columns: u = 0)
+__global__ void k_lz_start(PanelDev p, const double2* __restrict__ v, double2* __restrict__ u, double* nrm2) {
+    const int P = p.P;
+    const long long items = (long long)p.npad * P;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < items; i += (long long)gridDim.x * THREADS) {
+        const int c = (int)(i % P);
+        const ColState& cs = p.col[c];
+        if (!cs.active) {
+            u[i] = cmk(0.0, 0.0);
+            continue;
+        }
+        const double n2 = v[(size_t)cs.row * P + c].x;
+        u[i] = cmk(v[i].x / sqrt(n2), 0.0);
+        if (i / P == 0) nrm2[c] = n2;
+    }
 }
 
+// w = y - a_c u - b_c u_prev
 __global__ void k_lz_combine(PanelDev p, const double2* __restrict__ y, const double2* __restrict__ u,
                              const double2* __restrict__ up, double2* __restrict__ w, const double* a,
-                             const double* b) {
-    const double av = *a, bv = *b;
-    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS)
-        w[i] = cmk(y[i].x - av * u[i].x - bv * up[i].x, 0.0);
+                             const double* b, int sa, int sb) {
+    const int P = p.P;
+    const long long items = (long long)p.npad * P;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < items; i += (long long)gridDim.x * THREADS) {
+        const int c = (int)(i % P);
+        w[i] = cmk(y[i].x - a[(size_t)c * sa] * u[i].x - b[(size_t)c * sb] * up[i].x, 0.0);
+    }
 }
 
+// u_prev = u, u = w / b_c (0 when b_c = 0: invariant subspace found)
 __global__ void k_lz_scale(PanelDev p, const double2* __restrict__ w, double2* __restrict__ u,
-                           double2* __restrict__ up, const double* bnext) {
-    const double bv = *bnext;
-    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < p.npad; i += (long long)gridDim.x * THREADS) {
+                           double2* __restrict__ up, const double* bnext, int sb) {
+    const int P = p.P;
+    const long long items = (long long)p.npad * P;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < items; i += (long long)gridDim.x * THREADS) {
+        const double bv = bnext[(size_t)(i % P) * sb];
         up[i] = u[i];
         u[i] = cmk(bv > 0.0 ? w[i].x / bv : 0.0, 0.0);
     }
@@ -2100,37 +2133,28 @@ void launch_mulliken_output(const PanelDev& p, int ncols, const double2* w, doub
         k_mulliken_output<<<p.P, THREADS, 0, st>>>(p, ncols, w, g_s, out);
     }
 }
-void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, cudaStream_t st) {
-    {
-        LaunchScope ls_(K_OTHER, st);
-        k_lz_spmv<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s, M, x, y);
-    }
+void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, int P, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_lz_spmv<<<grid_for((long long)s.n_atoms * P), THREADS, 0, st>>>(s, M, x, y, P);
 }
-void launch_lz_dot(const PanelDev& p, const double2* x, const double2* y, double* out, int mode, cudaStream_t st) {
-    {
-        LaunchScope ls_(K_OTHER, st);
-        k_lz_dot<<<grid_for(p.npad), THREADS, 0, st>>>(p, x, y, out, mode);
-    }
+void launch_lz_dot(const PanelDev& p, const double2* x, const double2* y, double* out, int stride, int mode,
+                   cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_lz_dot<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, x, y, out, stride, mode);
 }
 void launch_lz_combine(const PanelDev& p, const double2* y, double2* u, double2* u_prev, double2* w,
-                       const double* a, const double* b, cudaStream_t st) {
-    {
-        LaunchScope ls_(K_OTHER, st);
-        k_lz_combine<<<grid_for(p.npad), THREADS, 0, st>>>(p, y, u, u_prev, w, a, b);
-    }
+                       const double* a, const double* b, int sa, int sb, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_lz_combine<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, y, u, u_prev, w, a, b, sa, sb);
 }
-void launch_lz_scale(const PanelDev& p, double2* w, double2* u, double2* u_prev, const double* bnext,
+void launch_lz_scale(const PanelDev& p, double2* w, double2* u, double2* u_prev, const double* bnext, int sb,
                      cudaStream_t st) {
-    {
-        LaunchScope ls_(K_OTHER, st);
-        k_lz_scale<<<grid_for(p.npad), THREADS, 0, st>>>(p, w, u, u_prev, bnext);
-    }
+    LaunchScope ls_(K_OTHER, st);
+    k_lz_scale<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, w, u, u_prev, bnext, sb);
 }
-void launch_lz_start(const PanelDev& p, const double2* v, int row, double2* u, double* nrm2, cudaStream_t st) {
-    {
-        LaunchScope ls_(K_OTHER, st);
-        k_lz_start<<<grid_for(p.npad), THREADS, 0, st>>>(p, v, row, u, nrm2);
-    }
+void launch_lz_start(const PanelDev& p, const double2* v, double2* u, double* nrm2, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_lz_start<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, v, u, nrm2);
 }
 
 

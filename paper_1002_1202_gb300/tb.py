@@ -128,6 +128,8 @@ SIGNATURES = [
                               C.POINTER(SolveOpts), _VP, _VP, C.POINTER(CscStats), _VP]),
     ("tb_generalized_lanczos", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_lanczos_green", C.c_int, [_VP, _VP, C.c_double, C.c_int32, C.c_int32, _DP, _VP, _VP]),
+    ("tb_generalized_lanczos_batch", C.c_int, [_VP, C.c_int32, _I32P, C.c_int32, C.POINTER(SolveOpts), _VP, _VP,
+                                               _VP, _VP]),
     ("tb_generalized_lanczos_noalloc", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
     ("tb_launch_count", C.c_int64, []),
@@ -531,6 +533,22 @@ def tb_lanczos_green(a, b, norm: float, z, out=None, stream=None):
                                         _ptr(zz, C.c_double), _out_ptr(out), _stream(stream))
     _check(s, "tb_lanczos_green", False)
     return out
+
+
+def tb_generalized_lanczos_batch(h: Handle, cols, n_steps: int, opts: SolveOpts | None = None, stream=None):
+    """Lanczos coefficients of R columns: (a [R, n_steps], b [R, n_steps+1],
+    norm [R]) as numpy arrays."""
+    cc = np.ascontiguousarray(cols, dtype=np.int32)
+    R = len(cc)
+    a = np.zeros((R, n_steps))
+    b = np.zeros((R, n_steps + 1))
+    nrm = np.zeros(R)
+    opts = opts or tb_default_opts()
+    s = load_library().tb_generalized_lanczos_batch(h.ptr, R, _ptr(cc, C.c_int32), int(n_steps), C.byref(opts),
+                                                    C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data),
+                                                    C.c_void_p(nrm.ctypes.data), _stream(stream))
+    _check(s, "tb_generalized_lanczos_batch", False)
+    return a, b, nrm
 
 
 def tb_generalized_lanczos_noalloc(h: Handle, j: int, n_steps: int, inner_tol=1e-13, stream=None, out=None):

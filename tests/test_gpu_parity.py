@@ -234,6 +234,28 @@ def test_lanczos(P, c1, h1):
         P.tb_lanczos_green(a, b, float("nan"), zl)
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_lanczos_batch(P, c1, h1, prec):
+    """Lanczos processes of several columns in one panel (two panels with a
+    ragged tail at panel 4) against the oracle's process per column; the
+    single-column call is the batch of one."""
+    s, H, S, z, w, cols = c1
+    js = [9, 0, 255, 100, 31, 64]
+    a, b, nrm = P.tb_generalized_lanczos_batch(h1, js, 60, opts=P.tb_default_opts(precision=prec, panel=4,
+                                                                                   inner_tol=1e-13))
+    for c, j in enumerate(js):
+        ar, br, nr = method.generalized_lanczos(H, S, j, 60)
+        assert abs(nrm[c] - nr) <= 1e-12 * nr
+        assert np.abs(a[c, :20] - ar[:20]).max() <= 1e-8 * np.abs(ar).max()
+        assert np.abs(b[c, :21] - br[:21]).max() <= 1e-8 * np.abs(br).max()
+    if prec == 0:
+        # same process, other panel width (other reduction order): Lanczos
+        # amplifies rounding once orthogonality is lost, so compare early steps
+        a1, b1, n1 = P.tb_generalized_lanczos(h1, js[3], 60)
+        assert np.abs(a1[:20] - a[3, :20]).max() <= 1e-10 * np.abs(a1).max()
+        assert abs(n1 - nrm[3]) <= 1e-13 * n1
+
+
 def test_not_converged_status(P, c1, h1):
     s, H, S, z, w, cols = c1
     opts = P.tb_default_opts(max_iter=5)
