@@ -216,7 +216,7 @@ def lanczos_measure(P, s, prec, panel):
                         "vs one column" % panel,
             "batched_s": t_b, "column_steps_per_s": 1024 * n_steps / t_b,
             "single_column_s": t_1, "single_column_steps_per_s": n_steps / t_1,
-            "speedup_per_column": (n_steps / t_1 and (1024 * n_steps / t_b) / (n_steps / t_1))}
+            "speedup_per_column": (1024 * n_steps / t_b) / (n_steps / t_1)}
 
 
 def rank_columns(n_orb, panel, rank, seed=100):
