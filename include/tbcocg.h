@@ -348,6 +348,14 @@ tb_status tb_generalized_lanczos_batch(tb_handle *h, int32_t R, const int32_t *c
                                        void *stream);
 
 /*
+ * tb_lanczos_green for R processes at once (the outputs of
+ * tb_generalized_lanczos_batch): a [R][n_steps], b [R][n_steps + 1],
+ * norm [R] (host or device), z host complex [K]; G_out complex [R][K].
+ */
+tb_status tb_lanczos_green_batch(int32_t R, const double *a, const double *b, const double *norm, int32_t n_steps,
+                                 int32_t K, const double *z, double *G_out, void *stream);
+
+/*
  * Allocation-free generalized Lanczos.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate GPU memory while they
  * call the library -- for example code that runs with the whole device

@@ -1599,25 +1599,35 @@ tb_status tb_csc_loop(tb_handle* h, int32_t K, const double* z, const double* w,
     return (res <= copts->scf_tol && !cocg_unconverged) ? TB_OK : TB_ERR_NOT_CONVERGED;
 }
 
-tb_status tb_lanczos_green(const double* a, const double* b, double norm, int32_t n_steps, int32_t K,
-                           const double* z, double* G_out, void* stream) {
-    if (!a || !b || !z || !G_out || n_steps < 1 || K < 1 || !std::isfinite(norm)) return TB_ERR_INVALID_ARG;
+tb_status tb_lanczos_green_batch(int32_t R, const double* a, const double* b, const double* norm, int32_t n_steps,
+                                 int32_t K, const double* z, double* G_out, void* stream) {
+    if (R < 1 || !a || !b || !norm || !z || !G_out || n_steps < 1 || K < 1) return TB_ERR_INVALID_ARG;
     for (int k = 0; k < 2 * K; ++k)
         if (!std::isfinite(z[k])) return TB_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Cleanup cl;
     cl.st = st;
     tb_status s;
-    const double *ad = nullptr, *bd = nullptr, *zd = nullptr;
-    if ((s = device_view(cl, a, (size_t)n_steps, &ad, st)) != TB_OK) return s;
-    if ((s = device_view(cl, b, (size_t)n_steps + 1, &bd, st)) != TB_OK) return s;
+    const double *ad = nullptr, *bd = nullptr, *nd = nullptr, *zd = nullptr;
+    if ((s = device_view(cl, a, (size_t)R * n_steps, &ad, st)) != TB_OK) return s;
+    if ((s = device_view(cl, b, (size_t)R * (n_steps + 1), &bd, st)) != TB_OK) return s;
+    if ((s = device_view(cl, norm, (size_t)R, &nd, st)) != TB_OK) return s;
     if ((s = device_view(cl, z, (size_t)2 * K, &zd, st)) != TB_OK) return s;
+    if (!is_device_ptr(norm))
+        for (int r = 0; r < R; ++r)
+            if (!std::isfinite(norm[r])) return TB_ERR_INVALID_ARG;
     OutBuf ob;
-    if ((s = out_prepare(cl, ob, G_out, sizeof(double2) * (size_t)K)) != TB_OK) return s;
-    launch_lanczos_green(ad, bd, norm, n_steps, K, reinterpret_cast<const double2*>(zd),
+    if ((s = out_prepare(cl, ob, G_out, sizeof(double2) * (size_t)R * K)) != TB_OK) return s;
+    launch_lanczos_green(ad, bd, nd, R, n_steps, K, reinterpret_cast<const double2*>(zd),
                          static_cast<double2*>(ob.dev), st);
     TB_CK(cudaGetLastError());
     return out_finish(ob, st);
+}
+
+tb_status tb_lanczos_green(const double* a, const double* b, double norm, int32_t n_steps, int32_t K,
+                           const double* z, double* G_out, void* stream) {
+    if (!std::isfinite(norm)) return TB_ERR_INVALID_ARG;
+    return tb_lanczos_green_batch(1, a, b, &norm, n_steps, K, z, G_out, stream);
 }
 
 tb_status tb_generalized_lanczos_batch(tb_handle* h, int32_t R, const int32_t* cols, int32_t n_steps,

@@ -187,8 +187,8 @@ void launch_atom_sum(const double* q_orb, const int64_t* orb_off, int n_atoms, d
 void launch_csc_mix(const double* q, const double* q_ref, const double* dq_in, double* dq_next, double mix, int n,
                     unsigned long long* res_bits, cudaStream_t st);
 
-void launch_lanczos_green(const double* a, const double* b, double norm, int n_steps, int K, const double2* z,
-                          double2* G, cudaStream_t st);
+void launch_lanczos_green(const double* a, const double* b, const double* norm, int R, int n_steps, int K,
+                          const double2* z, double2* G, cudaStream_t st);
 
 // generalized Lanczos on a panel of P independent columns (Section 3.2)
 void launch_lz_spmv(const DevSystem& s, const double* M, const double2* x, double2* y, int P, cudaStream_t st);

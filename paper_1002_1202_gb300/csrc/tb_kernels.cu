@@ -1644,11 +1644,18 @@ __global__ void k_csc_mix(const double* __restrict__ q, const double* __restrict
 }
 
 
-// G(z_k) = norm / (z_k - a_0 - b_1^2 / (z_k - a_1 - ...)), one thread per
-// point, bottom-up (Section 3.2).
-__global__ void k_lanczos_green(const double* __restrict__ a, const double* __restrict__ b, double norm,
-                                int n_steps, int K, const double2* __restrict__ z, double2* __restrict__ G) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+// G_r(z_k) = norm_r / (z_k - a_r0 - b_r1^2 / (z_k - a_r1 - ...)), one
+// thread per (column r, point k), bottom-up (Section 3.2); a [R][n_steps],
+// b [R][n_steps + 1], norm [R], G [R][K].
+__global__ void k_lanczos_green(const double* __restrict__ a_all, const double* __restrict__ b_all,
+                                const double* __restrict__ norm_all, int R, int n_steps, int K,
+                                const double2* __restrict__ z, double2* __restrict__ G) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)R * K;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / K), k = (int)(i % K);
+        const double* a = a_all + (size_t)r * n_steps;
+        const double* b = b_all + (size_t)r * (n_steps + 1);
+        const double norm = norm_all[r];
         const double2 zk = z[k];
         double2 g = cmk(0.0, 0.0);
         for (int m = n_steps - 1; m >= 0; --m) {
@@ -1656,7 +1663,7 @@ __global__ void k_lanczos_green(const double* __restrict__ a, const double* __re
                                                    : cmk(0.0, 0.0);
             g = cdiv(cmk(1.0, 0.0), csub(cmk(zk.x - a[m], zk.y), tail));
         }
-        G[k] = cmk(norm * g.x, norm * g.y);
+        G[i] = cmk(norm * g.x, norm * g.y);
     }
 }
 
@@ -2180,10 +2187,10 @@ void launch_csc_mix(const double* q, const double* q_ref, const double* dq_in, d
 }
 
 
-void launch_lanczos_green(const double* a, const double* b, double norm, int n_steps, int K, const double2* z,
-                          double2* G, cudaStream_t st) {
+void launch_lanczos_green(const double* a, const double* b, const double* norm, int R, int n_steps, int K,
+                          const double2* z, double2* G, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
-    k_lanczos_green<<<grid_for(K), THREADS, 0, st>>>(a, b, norm, n_steps, K, z, G);
+    k_lanczos_green<<<grid_for((long long)R * K), THREADS, 0, st>>>(a, b, norm, R, n_steps, K, z, G);
 }
 
 

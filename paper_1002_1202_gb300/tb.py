@@ -128,6 +128,7 @@ SIGNATURES = [
                               C.POINTER(SolveOpts), _VP, _VP, C.POINTER(CscStats), _VP]),
     ("tb_generalized_lanczos", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
     ("tb_lanczos_green", C.c_int, [_VP, _VP, C.c_double, C.c_int32, C.c_int32, _DP, _VP, _VP]),
+    ("tb_lanczos_green_batch", C.c_int, [C.c_int32, _VP, _VP, _VP, C.c_int32, C.c_int32, _DP, _VP, _VP]),
     ("tb_generalized_lanczos_batch", C.c_int, [_VP, C.c_int32, _I32P, C.c_int32, C.POINTER(SolveOpts), _VP, _VP,
                                                _VP, _VP]),
     ("tb_generalized_lanczos_noalloc", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
@@ -549,6 +550,23 @@ def tb_generalized_lanczos_batch(h: Handle, cols, n_steps: int, opts: SolveOpts 
                                                     C.c_void_p(nrm.ctypes.data), _stream(stream))
     _check(s, "tb_generalized_lanczos_batch", False)
     return a, b, nrm
+
+
+def tb_lanczos_green_batch(a, b, norm, z, out=None, stream=None):
+    """G_r(z_k) for R Lanczos processes (a [R, n], b [R, n+1], norm [R]);
+    returns complex128 [R, K] (numpy unless ``out`` is given)."""
+    keep = []
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    R, n = a.shape
+    zz = _complex_host(z)
+    K = len(zz) // 2
+    if out is None:
+        out = np.zeros((R, K), dtype=np.complex128)
+    s = load_library().tb_lanczos_green_batch(R, _in_ptr(a, R * n, keep), _in_ptr(b, R * (n + 1), keep),
+                                              _in_ptr(norm, R, keep), n, K, _ptr(zz, C.c_double), _out_ptr(out),
+                                              _stream(stream))
+    _check(s, "tb_lanczos_green_batch", False)
+    return out
 
 
 def tb_generalized_lanczos_noalloc(h: Handle, j: int, n_steps: int, inner_tol=1e-13, stream=None, out=None):

@@ -248,6 +248,12 @@ def test_lanczos_batch(P, c1, h1, prec):
         assert abs(nrm[c] - nr) <= 1e-12 * nr
         assert np.abs(a[c, :20] - ar[:20]).max() <= 1e-8 * np.abs(ar).max()
         assert np.abs(b[c, :21] - br[:21]).max() <= 1e-8 * np.abs(br).max()
+    # continued fractions of all processes at once (local densities of states)
+    zl = np.linspace(-25.0, 10.0, 41) + 2.0j
+    Gb = P.tb_lanczos_green_batch(a, b, nrm, zl)
+    for c in range(len(js)):
+        go = method.lanczos_green(a[c], b[c], nrm[c], zl)
+        assert np.abs(Gb[c] - go).max() <= 1e-12 * np.abs(go).max()
     if prec == 0:
         # same process, other panel width (other reduction order): Lanczos
         # amplifies rounding once orthogonality is lost, so compare early steps
