@@ -302,7 +302,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(config_dict(args, s), panel=1, iterations_per_step=n_iter,
+        "config": dict(config_dict(args, s, precision="fp64"), panel=1, panels_per_step=1, iterations_per_step=n_iter,
+                       precision="FP64 throughout (CPU oracle: numpy + scipy.sparse)", l2="not applicable (CPU)",
                        workload=config_dict(args, s)["workload"] + "; reference arm: CPU oracle, 1 column per step"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"1 column x {n_iter} outer iterations x {K_SHIFTS} shifts per step"},
