@@ -299,3 +299,22 @@ def forces_ased(gH, gS, dS_dd, orb_per_atom, brow_ptr, bcol, eps, K) -> np.ndarr
                         F[j] -= wgt * dS_dd[:, e]
                     e += 1
     return F
+
+
+def mulliken_vjp(H, S, z, w, v, g_s=2.0):
+    """Vector-Jacobian product of the Mulliken populations: for
+    L = sum_a v_a q_a (q_a the gross orbital populations, v_a weights per
+    orbital), with D_v = diag(v) and dG = G (dH - z dS) G,
+      dL/dH_ab = -(g_s/pi) Im sum_k w_k [G S D_v G]_ba,
+      dL/dS_ab = -(g_s/pi) Im sum_k w_k (v_b G_ba - z_k [G S D_v G]_ba),
+    H_ab, S_ab independent entries.  Returns the two (N, N) real matrices."""
+    N = S.shape[0]
+    Dv = np.diag(np.asarray(v, dtype=np.float64))
+    gH = np.zeros((N, N), dtype=np.complex128)
+    gS = np.zeros((N, N), dtype=np.complex128)
+    for zk, wk in zip(z, w):
+        G = green_matrix(H, S, zk)
+        Gam = G @ S @ Dv @ G
+        gH += wk * Gam.T
+        gS += wk * ((Dv @ G).T - zk * Gam.T)
+    return -(g_s / math.pi) * gH.imag, -(g_s / math.pi) * gS.imag

@@ -124,3 +124,33 @@ def test_forces_match_differences_of_energy(small):
                 Es.append(dense.band_energy(dense.ased_hamiltonian(Sd, sd.eps, sd.K, sd.orbital_atom()), Sd, z, w))
             fd = -(Es[0] - Es[1]) / (2 * h)
             assert abs(F[atom, ax] - fd) <= 1e-5 * max(1.0, np.abs(F).max())
+
+
+def test_mulliken_vjp_matches_differences(small):
+    """dL/dH and dL/dS of L = sum_a v_a q_a against central differences of
+    the dense Mulliken populations under symmetric perturbations."""
+    s, H, S = small
+    z, w = linspace_grid(16, -40.0, -8.0, 1.0)
+    rng = np.random.default_rng(8)
+    N = S.shape[0]
+    v = rng.standard_normal(N)
+    gH, gS = dense.mulliken_vjp(H, S, z, w, v)
+    mask = (np.abs(S) > 0).astype(float)
+
+    def L(Hm, Sm):
+        return float(v @ dense.mulliken_orbital(Hm, Sm, z, w))
+
+    for grad, which in ((gH, "H"), (gS, "S")):
+        A = rng.standard_normal((N, N)) * mask
+        D = 0.5 * (A + A.T)
+        h = 1e-6
+        if which == "H":
+            fd = (L(H + h * D, S) - L(H - h * D, S)) / (2 * h)
+        else:
+            fd = (L(H, S + h * D) - L(H, S - h * D)) / (2 * h)
+        assert abs(fd - float(np.sum(grad * D))) <= 1e-6 * max(1.0, abs(fd)), which
+    # v = 1 on every orbital: L is the electron count, whose H-gradient is
+    # -(g_s/pi) Im sum_k w_k [G S G]^T = dE/dH of the energy with weights w_k / z_k
+    gH1, _ = dense.mulliken_vjp(H, S, z, w, np.ones(N))
+    gE, _ = dense.band_energy_gradients(H, S, z, w / z)
+    assert np.abs(gH1 - gE).max() <= 1e-10 * np.abs(gE).max()
