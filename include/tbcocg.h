@@ -228,6 +228,24 @@ tb_status tb_forces(tb_handle *h, const double *dE_dH, const double *dE_dS, cons
                     const double *dH_dd, double *F_out, void *stream);
 
 /*
+ * Vector-Jacobian product of the Mulliken populations (adjoint): for
+ * L = sum_a v_a q_a, q_a the gross population of orbital a (v: double [N]
+ * weights, host or device; per-atom charges take v_a = the atom's weight on
+ * each of its orbitals),
+ *     dL/dH_ab = -(g_s/pi) Im sum_k w_k [G S D_v G]_ba,
+ *     dL/dS_ab = -(g_s/pi) Im sum_k w_k (v_b G_ba - z_k [G S D_v G]_ba),
+ * D_v = diag(v), at every stored entry (the caller's block layout).  It needs
+ * full-vector shifted solves with right-hand sides e_c and s_c (column c of
+ * S) for every orbital c, contracted on the pattern:
+ * [G S D_v G]_ba = sum_c v_c (G s_c)_b (G e_c)_a -- O(N K nnz) work, meant
+ * for systems up to a few thousand orbitals.  Solves use opts; status as
+ * tb_shifted_cocg; a batch handle of more than one system is
+ * TB_ERR_INVALID_ARG.  dL_dH, dL_dS: double [n_values], host or device.
+ */
+tb_status tb_mulliken_vjp(tb_handle *h, int32_t K, const double *z, const double *w, double g_s, const double *v,
+                          const tb_solve_opts *opts, double *dL_dH, double *dL_dS, tb_stats *stats, void *stream);
+
+/*
  * Gross Mulliken populations of selected orbitals (Section 2.2, the
  * Mulliken partition of the charge density), from the energy integral of
  * the Green's function with the quadrature (z_k, w_k) (host, complex):

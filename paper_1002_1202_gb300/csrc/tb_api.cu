@@ -125,6 +125,8 @@ struct Solve {
     double2* x_out = nullptr;           // full
     double2* g_out = nullptr;           // rows
     double2* dg_out = nullptr;          // rows: d/dz of the elements (optional)
+    const double* rhs = nullptr;        // device [R][N] real right-hand sides (caller order) instead
+                                        // of e_j; whole-system views only
     double* q_out = nullptr;            // srow, per column
 };
 
@@ -455,7 +457,7 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
             cs.sc_prev = make_double2(1.0, 0.0);
             cs.seed = o->seed;
             cs.active = c < ncols ? 1 : 0;
-            cs.row = c < ncols ? v.o2p_h[q.cols[c0 + c]] : -1;
+            cs.row = c < ncols && !q.rhs ? v.o2p_h[q.cols[c0 + c]] : -1;
             cs.nfun = q.proj == PROJ_ROWS && c < ncols ? (int)(q.row_ptr[c0 + c + 1] - q.row_ptr[c0 + c])
                                                        : (q.proj == PROJ_SROW ? 1 : 0);
             colh[c] = cs;
@@ -479,6 +481,7 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
 
         // r_0 = e_j, r'_0 = S^-1 r_0, rho_0, pi = 1, x^k = 0, p^k = r'_0
         launch_panel_init(v.ds, p, st);
+        if (q.rhs) launch_panel_rhs(p, q.rhs + (size_t)c0 * v.n_orb, v.o2p_d, (int)v.n_orb, ncols, st);
         if ((s = inner_solve(v, p, p.Rcur, o->inner_max_iter, ic, st)) != TB_OK) return s;
         if (v.flags_host[0] & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
         launch_finish(v.ds, p, st);
@@ -1369,6 +1372,118 @@ tb_status tb_forces(tb_handle* h, const double* dE_dH, const double* dE_dS, cons
     launch_force_atoms(n, h->ds.brow, h->ds.bcol, btr, vblk, static_cast<double*>(ob.dev), st);
     TB_CK(cudaGetLastError());
     return out_finish(ob, st);
+}
+
+tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double* w, double g_s, const double* v,
+                          const tb_solve_opts* opts, double* dL_dH, double* dL_dS, tb_stats* stats, void* stream) {
+    if (!h || !w || !v || !dL_dH || !dL_dS || !std::isfinite(g_s)) return TB_ERR_INVALID_ARG;
+    if (h->sys_atom_off.size() > 2) return TB_ERR_INVALID_ARG;   // one system per handle
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(w[k])) return TB_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int n = h->n_atoms;
+    const int64_t N = h->n_orb;
+    const int64_t nvals = h->boff_h.back();
+    std::vector<int64_t> ooff(n + 1, 0);
+    for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + h->orb_per_atom[i];
+    // every stored entry (a, b) in the caller's block layout
+    std::vector<int32_t> ea(nvals), eb(nvals);
+    for (int I = 0; I < n; ++I)
+        for (int64_t blk = h->brow_h[I]; blk < h->brow_h[I + 1]; ++blk) {
+            const int J = h->bcol_h[blk];
+            const int ni = h->orb_per_atom[I], nj = h->orb_per_atom[J];
+            for (int ai = 0; ai < ni; ++ai)
+                for (int bj = 0; bj < nj; ++bj) {
+                    const int64_t e = h->boff_h[blk] + (int64_t)ai * nj + bj;
+                    ea[e] = (int32_t)(ooff[I] + ai);
+                    eb[e] = (int32_t)(ooff[J] + bj);
+                }
+        }
+    // columns per chunk: the two full-solution panels X, Y ([K][Rc][N]) within ~2 GiB
+    const int64_t per_col = 2 * (int64_t)K * N * (int64_t)sizeof(double2);
+    const int Rc = (int)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)2 * 1024 * 1024 * 1024 / per_col));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cleanup cl;
+    cl.st = st;
+    int32_t *ead, *ebd;
+    double *gH, *gS, *Sc;
+    double2 *X, *Y, *zd, *wd;
+    const double* vd = nullptr;
+    if ((s = dalloc(cl, &ead, (size_t)nvals)) != TB_OK) return s;
+    if ((s = dalloc(cl, &ebd, (size_t)nvals)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gH, (size_t)nvals)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gS, (size_t)nvals)) != TB_OK) return s;
+    if ((s = dalloc(cl, &Sc, (size_t)Rc * N)) != TB_OK) return s;
+    if ((s = dalloc(cl, &X, (size_t)K * Rc * N)) != TB_OK) return s;
+    if ((s = dalloc(cl, &Y, (size_t)K * Rc * N)) != TB_OK) return s;
+    if ((s = dalloc(cl, &zd, (size_t)K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &wd, (size_t)K)) != TB_OK) return s;
+    if ((s = device_view(cl, v, (size_t)N, &vd, st)) != TB_OK) return s;
+    TB_CK(cudaMemcpyAsync(ead, ea.data(), sizeof(int32_t) * nvals, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(ebd, eb.data(), sizeof(int32_t) * nvals, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(zd, z, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(wd, w, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemsetAsync(gH, 0, sizeof(double) * nvals, st));
+    TB_CK(cudaMemsetAsync(gS, 0, sizeof(double) * nvals, st));
+    View vw = whole_view(h);
+    tb_stats agg{};
+    bool unconverged = false;
+    std::vector<double> Sh((size_t)Rc * N);
+    std::vector<int32_t> cols(Rc);
+    for (int64_t c0 = 0; c0 < N; c0 += Rc) {
+        const int rc = (int)std::min<int64_t>(Rc, N - c0);
+        // columns s_c of S (= rows, S symmetric) in caller order
+        std::fill(Sh.begin(), Sh.end(), 0.0);
+        for (int c = 0; c < rc; ++c) {
+            const int64_t o = c0 + c;
+            cols[c] = (int32_t)o;
+            const int J = (int)(std::upper_bound(ooff.begin(), ooff.end(), o) - ooff.begin()) - 1;
+            const int bj = (int)(o - ooff[J]);
+            for (int64_t blk = h->brow_h[J]; blk < h->brow_h[J + 1]; ++blk) {
+                const int I = h->bcol_h[blk];
+                const int ni = h->orb_per_atom[I];
+                for (int ai = 0; ai < ni; ++ai)
+                    Sh[(size_t)c * N + ooff[I] + ai] = h->S_h[h->boff_h[blk] + (int64_t)bj * ni + ai];
+            }
+        }
+        TB_CK(cudaMemcpyAsync(Sc, Sh.data(), sizeof(double) * (size_t)rc * N, cudaMemcpyHostToDevice, st));
+        for (int pass = 0; pass < 2; ++pass) {
+            Solve q;
+            q.K = K; q.z = z; q.R = rc; q.cols = cols.data(); q.proj = PROJ_NONE;
+            q.x_out = pass == 0 ? X : Y;
+            if (pass == 1) q.rhs = Sc;
+            tb_stats ts{};
+            const tb_status run = run_view(vw, q, opts, &ts, st);
+            if (run == TB_ERR_NOT_CONVERGED) unconverged = true;
+            else if (run != TB_OK) return run;
+            agg.outer_iterations += ts.outer_iterations;
+            agg.inner_iterations += ts.inner_iterations;
+            agg.max_column_iterations = std::max(agg.max_column_iterations, ts.max_column_iterations);
+            agg.switches += ts.switches;
+            agg.unconverged += ts.unconverged;
+            agg.inner_redos += ts.inner_redos;
+        }
+        launch_vjp_accumulate(X, Y, K, rc, N, (int)c0, ead, ebd, nvals, vd, zd, wd, g_s, gH, gS, st);
+        TB_CK(cudaGetLastError());
+    }
+    OutBuf oH, oS;
+    if ((s = out_prepare(cl, oH, dL_dH, sizeof(double) * nvals)) != TB_OK) return s;
+    if ((s = out_prepare(cl, oS, dL_dS, sizeof(double) * nvals)) != TB_OK) return s;
+    TB_CK(cudaMemcpyAsync(oH.dev, gH, sizeof(double) * nvals, cudaMemcpyDeviceToDevice, st));
+    TB_CK(cudaMemcpyAsync(oS.dev, gS, sizeof(double) * nvals, cudaMemcpyDeviceToDevice, st));
+    tb_status fin = out_finish(oH, st);
+    if (fin == TB_OK) fin = out_finish(oS, st);
+    if (stats) {
+        int32_t* ci = stats->conv_iter;
+        *stats = agg;
+        stats->conv_iter = ci;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (fin != TB_OK) return fin;
+    return unconverged ? TB_ERR_NOT_CONVERGED : TB_OK;
 }
 
 tb_status tb_band_energy(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,

@@ -1776,6 +1776,54 @@ __global__ void k_force_atoms(int n_atoms, const int* __restrict__ brow, const i
     }
 }
 
+
+// r_0 = b for real right-hand sides b [ncols][n_orb] in caller orbital order
+// (instead of e_j): written into Rcur and Rin at the padded slots
+__global__ void k_panel_rhs(PanelDev p, const double* __restrict__ rhs, const int32_t* __restrict__ orb2pad,
+                            int n_orb, int ncols) {
+    const long long items = (long long)ncols * n_orb;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < items; i += (long long)gridDim.x * THREADS) {
+        const int c = (int)(i / n_orb), o = (int)(i % n_orb);
+        const size_t e = (size_t)orb2pad[o] * p.P + c;
+        const double2 v = cmk(rhs[i], 0.0);
+        p.Rcur[e] = v;
+        p.Rin[e] = v;
+    }
+}
+
+// Mulliken vector-Jacobian product, one chunk of columns c0 .. c0+Rc-1 at a
+// time: X[k][c][.] = G(z_k) e_c, Y[k][c][.] = G(z_k) s_c (caller order).
+// For every stored entry (a, b):
+//   Gamma_ba(z) = sum_c v_c Y[c]_b X[c]_a     ([G S D_v G]_ba, this chunk's share)
+//   gH += -(g_s/pi) Im sum_k w_k Gamma_ba
+//   gS += -(g_s/pi) Im sum_k w_k (v_b G_ba - z_k Gamma_ba), G_ba = X[a]_b when a is in the chunk
+__global__ void k_vjp_accumulate(const double2* __restrict__ X, const double2* __restrict__ Y, int K, int Rc,
+                                 int64_t N, int c0, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
+                                 int64_t ne, const double* __restrict__ v, const double2* __restrict__ z,
+                                 const double2* __restrict__ w, double g_s, double* __restrict__ gH,
+                                 double* __restrict__ gS) {
+    const double f = -g_s / 3.14159265358979323846;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+        const int a = ea[e], b = eb[e];
+        double ah = 0.0, as = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double2 gam = cmk(0.0, 0.0);
+            for (int c = 0; c < Rc; ++c) {
+                const size_t base = ((size_t)k * Rc + c) * N;
+                gam = cadd(gam, cmul(cmk(v[c0 + c], 0.0), cmul(Y[base + b], X[base + a])));
+            }
+            ah += cmul(w[k], gam).y;
+            as -= cmul(cmul(w[k], z[k]), gam).y;
+            if (a >= c0 && a < c0 + Rc) {
+                const double2 gba = X[((size_t)k * Rc + (a - c0)) * N + b];
+                as += v[b] * cmul(w[k], gba).y;
+            }
+        }
+        gH[e] += f * ah;
+        gS[e] += f * as;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -2228,6 +2276,20 @@ void launch_force_atoms(int n_atoms, const int* brow, const int* bcol, const int
                         double* F, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
     k_force_atoms<<<grid_for(n_atoms), THREADS, 0, st>>>(n_atoms, brow, bcol, btrans, vblk, F);
+}
+
+
+void launch_panel_rhs(const PanelDev& p, const double* rhs, const int32_t* orb2pad, int n_orb, int ncols,
+                      cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_panel_rhs<<<grid_for((long long)ncols * n_orb), THREADS, 0, st>>>(p, rhs, orb2pad, n_orb, ncols);
+}
+
+void launch_vjp_accumulate(const double2* X, const double2* Y, int K, int Rc, int64_t N, int c0,
+                           const int32_t* ea, const int32_t* eb, int64_t ne, const double* v, const double2* z,
+                           const double2* w, double g_s, double* gH, double* gS, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_vjp_accumulate<<<grid_for(ne), THREADS, 0, st>>>(X, Y, K, Rc, N, c0, ea, eb, ne, v, z, w, g_s, gH, gS);
 }
 
 }  // namespace tb

@@ -118,6 +118,8 @@ SIGNATURES = [
     ("tb_band_energy", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP, _VP, _VP,
                                  C.POINTER(Stats), _VP]),
     ("tb_forces", C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("tb_mulliken_vjp", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, C.POINTER(SolveOpts), _VP, _VP,
+                                  C.POINTER(Stats), _VP]),
     ("tb_mulliken_orbital", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.c_int32, _I32P,
                                       C.POINTER(SolveOpts), _VP, C.POINTER(Stats), _VP]),
     ("tb_mulliken_charges", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP,
@@ -393,6 +395,25 @@ def tb_band_energy(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None, n_va
                                       _stream(stream))
     _check(s, "tb_band_energy", allow_unconverged)
     return float(E[0]), gH, gS, _stats_dict(st, None, h.n_orb, K, s)
+
+
+def tb_mulliken_vjp(h: Handle, z, w, v, n_values: int, g_s=2.0, opts: SolveOpts | None = None, stream=None,
+                    allow_unconverged=False):
+    """dL/dH, dL/dS (caller block layout, length n_values) of
+    L = sum_a v_a q_a; returns (dL_dH, dL_dS, stats) as numpy."""
+    keep = []
+    zz = _complex_host(z)
+    ww = _complex_host(w)
+    K = len(zz) // 2
+    gH = np.zeros(int(n_values))
+    gS = np.zeros(int(n_values))
+    opts = opts or tb_default_opts()
+    st, _ = _stats(h.n_orb, K, False)
+    s = load_library().tb_mulliken_vjp(h.ptr, K, _ptr(zz, C.c_double), _ptr(ww, C.c_double), float(g_s),
+                                       _in_ptr(v, h.n_orb, keep), C.byref(opts), _out_ptr(gH), _out_ptr(gS),
+                                       C.byref(st), _stream(stream))
+    _check(s, "tb_mulliken_vjp", allow_unconverged)
+    return gH, gS, _stats_dict(st, None, h.n_orb, K, s)
 
 
 def tb_forces(h: Handle, dE_dH, dE_dS, dS_dd, dH_dd=None, stream=None):

@@ -162,3 +162,13 @@ def test_batch_validation(lib, si):
     assert _status(lambda: tb.tb_create_batch([], stream=0)) == 1
     if not torch.cuda.is_available():
         assert _status(lambda: tb.tb_create_batch([si, si], stream=0)) == 9
+
+
+def test_mulliken_vjp_null_arguments(lib):
+    import ctypes as C
+    from paper_1002_1202_gb300 import tb
+    so = tb.SolveOpts()
+    lib.tb_default_opts(C.byref(so))
+    z = np.array([0.0, 1.0])
+    zp = z.ctypes.data_as(C.POINTER(C.c_double))
+    assert lib.tb_mulliken_vjp(None, 1, zp, zp, 2.0, None, C.byref(so), None, None, None, None) == 1

@@ -202,3 +202,36 @@ def test_autograd_band_energy(P):
     Ep = band_energy(structure, torch.tensor(s.S_vals + step * D), Ht.detach(), z, w).item()
     Em = band_energy(structure, torch.tensor(s.S_vals - step * D), Ht.detach(), z, w).item()
     assert abs((Ep - Em) / (2 * step) - float(np.dot(gS, D))) <= 1e-5 * max(1.0, abs(float(np.dot(gS, D))))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_mulliken_vjp(P, prec):
+    """dL/dH, dL/dS of L = sum_a v_a q_a from the device against the
+    oracle's dense G S D_v G contraction, on every stored entry."""
+    s = water_system(8, seed=4, cutoff=3.0, excess_proton=False)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(16, -40.0, -8.0, 1.0)
+    v = np.random.default_rng(8).standard_normal(s.n_orb)
+    h = P.tb_create_system(s)
+    gH, gS, st = P.tb_mulliken_vjp(h, z, w, v, len(s.S_vals), opts=P.tb_default_opts(precision=prec))
+    assert st["status"] == "TB_OK"
+    gHd, gSd = dense.mulliken_vjp(H, S, z, w, v)
+    mask = _dense_blocks(s, np.ones(len(s.S_vals))) > 0
+    assert np.abs(_dense_blocks(s, gH)[mask] - gHd[mask]).max() <= 1e-7 * np.abs(gHd).max()
+    assert np.abs(_dense_blocks(s, gS)[mask] - gSd[mask]).max() <= 1e-7 * np.abs(gSd).max()
+
+
+def test_mulliken_vjp_chunks_and_device_weights(P, si):
+    """A silicon cell (256 orbitals, so 4x4 blocks and many columns) with the
+    weights v already on the device: the same contraction."""
+    import torch
+    s, H, S = si
+    z, w = linspace_grid(8, -20.0, 5.0, 1.0)
+    v = np.random.default_rng(3).standard_normal(s.n_orb)
+    h = P.tb_create_system(s)
+    gH, gS, _ = P.tb_mulliken_vjp(h, z, w, torch.tensor(v, device="cuda"), len(s.S_vals))
+    gHd, gSd = dense.mulliken_vjp(H, S, z, w, v)
+    mask = _dense_blocks(s, np.ones(len(s.S_vals))) > 0
+    assert np.abs(_dense_blocks(s, gH)[mask] - gHd[mask]).max() <= 1e-7 * np.abs(gHd).max()
+    assert np.abs(_dense_blocks(s, gS)[mask] - gSd[mask]).max() <= 1e-7 * np.abs(gSd).max()
