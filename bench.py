@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
-                    help="mixed: FP32 inner CG inside FP64 refinement (FP64-accurate); fp64: every product in FP64")
+                    help="mixed: FP32 Chebyshev corrections inside FP64 refinement (FP64-accurate); fp64: every product in FP64")
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the other precision, reported beside the headline (0: skip)")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
@@ -247,7 +247,7 @@ def config_dict(args, s, precision=None):
         "n_atoms": s.n_atoms, "N": s.n_orb, "blocks": int(s.nb), "shifts": K_SHIFTS, "panel": args.panel,
         "panels_per_step": args.panels_per_step,
         "iterations_per_step": args.iters, "tol": args.tol, "inner_tol": args.inner_tol,
-        "precision": ("FP32 inner CG (to 1e-6 per round) inside FP64 iterative refinement; FP64 outer SpMM, "
+        "precision": ("FP32 Chebyshev corrections (to 1e-6 per round) inside FP64 iterative refinement; FP64 outer SpMM, "
                       "vectors, recurrences, switching and charges" if precision == "mixed" else "FP64 throughout"),
         "l2": "flushed (256 MiB write) before every timed step", "seed": SEED,
     }
@@ -403,6 +403,7 @@ KERNEL_INFO = {
     "outer_spmm": ("k_outer_spmm", 8, 16, True),
     "refine_residual": ("k_refine_residual", 8, 16, True),
     "inner32_spmv": ("k_inner32_spmv", 4, 8, False),
+    "inner32_cheb": ("k_inner32_cheb", 4, 8, False),
 }
 
 
@@ -425,7 +426,11 @@ def roofline_for(kname, ms, launches, s, panel, peaks, mixed=False, busy_ms=None
     nnz = 16 * s.nb
     mats = 2 if kname == "outer_spmm" else 1
     flops = 2.0 * nnz * 2 * panel * mats
-    vec_io = {"inner_spmv": 2, "inner32_spmv": 2, "refine_residual": 3, "outer_spmm": 5}[kname]
+    if kname == "inner32_cheb":
+        flops += 5.0 * s.n_orb * 2 * panel      # d_{k+1} = d_{k-1} + omega (gamma (f - S d_k) + d_k - d_{k-1})
+    # panel vectors moved once: the SpMVs read x and write y; the Chebyshev
+    # step reads d_k, f and d_{k-1} and writes d_{k+1}
+    vec_io = {"inner_spmv": 2, "inner32_spmv": 2, "inner32_cheb": 4, "refine_residual": 3, "outer_spmm": 5}[kname]
     nbytes = mats * nnz * mb + 4 * s.nb + 4 * (s.n_atoms + 1) + vec_io * s.n_orb * panel * vb
     mean_s = ms / max(launches, 1) / 1e3
     avg_s = busy_ms / max(launches, 1) / 1e3 if busy_ms else mean_s
@@ -586,16 +591,17 @@ def run_ours(args):
     share = {k: round(v[1], 3) for k, v in kernel_ms.items() if v[0] > 0}
     # second part of the metric: SpMM algorithmic HBM GB/s against the measured copy peak
     spmm_hbm = {}
-    for k in ("inner32_spmv", "outer_spmm", "inner_spmv"):
+    for k in ("inner32_cheb", "inner32_spmv", "outer_spmm", "inner_spmv"):
         rec = roofline if roofline and roofline.get("kernel") == KERNEL_INFO[k][0] else others.get(k)
         if not rec:
             continue
         gbs = rec["algorithmic_bytes_per_launch"] / (rec["avg_launch_us"] * 1e-6) / 1e9
         spmm_hbm[k] = {"kernel": rec["kernel"], "algorithmic_GBps": gbs, "peak_GBps": peaks["hbm_gbs"],
                        "frac": gbs / peaks["hbm_gbs"],
-                       "note": "algorithmic bytes (matrix once, panel read once and written once) per busy "
-                               "time per launch; at 256 columns per panel the SpMM does ~16 flop per such byte, "
-                               "so it is limited by the gathers and the ALUs, not by HBM"}
+                       "note": "algorithmic bytes (matrix once, every panel vector the kernel touches read or "
+                               "written once) per busy time per launch; at 128-256 columns per panel the SpMM "
+                               "does 8-16 flop per such byte, so it is limited by the gathers and the ALUs, not "
+                               "by HBM"}
 
     # the other precision on the same panel, for comparison
     compare = None

@@ -112,6 +112,15 @@ tb_status tb_create_batch(tb_handle **out, const tb_system_desc *descs, int32_t 
 int32_t tb_num_systems(const tb_handle *h);
 tb_status tb_batch_offsets(const tb_handle *h, int64_t *atom_off, int64_t *orb_off);
 
+/*
+ * Bounds [lo, hi] of the spectrum of S used by the Chebyshev corrections of
+ * TB_MIXED: extreme Ritz values of an 80-step Lanczos run on S (host, FP64,
+ * computed once per handle), widened by their residual norms and by 3 % /
+ * 1 %.  lo <= 0 means no usable lower bound (the FP32 CG corrections are
+ * used).  TB_ERR_S_NOT_SPD if a Ritz value of S is <= 0.
+ */
+tb_status tb_overlap_bounds(tb_handle *h, double *lo, double *hi);
+
 /* Release all device memory of the handle (NULL is allowed). */
 tb_status tb_destroy(tb_handle *h);
 
@@ -138,9 +147,21 @@ typedef struct {
                                  ||r - S r'|| <= inner_tol ||r||; all other steps FP64 */
     double inner_lo_tol;      /* TB_MIXED: relative tolerance of each FP32 CG round;
                                  default 1e-6                                            */
+    int32_t inner_method;     /* TB_MIXED: how the FP32 corrections of a round are made.
+                                 TB_INNER_CHEBYSHEV (default): a fixed number of
+                                 Chebyshev steps for the spectrum of S (bounds from a
+                                 Lanczos run on S on the host, once per handle), enough
+                                 to reduce the error by inner_lo_tol, each step one
+                                 kernel with no inner products; from the fourth round on
+                                 (and for an S whose bounds are unusable) FP32 CG.
+                                 TB_INNER_CG: FP32 CG in every round.  Either way the
+                                 FP64 residual of each round decides convergence, so both
+                                 reach the same inner_tol.  Ignored for TB_FP64 (CG).   */
 } tb_solve_opts;
 
 /* Fill *opts with the defaults listed above. */
+enum { TB_INNER_CHEBYSHEV = 0, TB_INNER_CG = 1 };
+
 void tb_default_opts(tb_solve_opts *opts);
 
 /* Optional statistics; every pointer member may be NULL. */
@@ -426,12 +447,15 @@ enum {
     TB_K_FULL_UPDATE = 6,  /* full-mode x^k, p^k updates                   */
     TB_K_OTHER = 7,        /* set-up, outputs, Lanczos helpers             */
     TB_K_INNER32_SPMV = 8, /* TB_MIXED: FP32 w = S r and dot products      */
-    TB_K_INNER32_UPDATE = 9, /* TB_MIXED: FP32 CG vector updates           */
+    TB_K_INNER32_UPDATE = 9, /* TB_MIXED: FP32 CG vector updates (and the
+                              first Chebyshev step)                           */
     TB_K_REFINE_RESIDUAL = 10, /* TB_MIXED: FP64 residual r - S r'         */
     TB_K_REFINE_AUX = 11,  /* TB_MIXED: refinement start and correction add */
     TB_K_CSC = 12,         /* charge self-consistency: potential, Hamiltonian
                               update, atom sums, mixing                        */
-    TB_K_COUNT = 13
+    TB_K_INNER32_CHEB = 13, /* TB_MIXED: one Chebyshev correction step (FP32
+                              S d and the update of d in one kernel)          */
+    TB_K_COUNT = 14
 };
 int64_t tb_launch_count(void);
 void tb_profile_enable(int32_t enable);

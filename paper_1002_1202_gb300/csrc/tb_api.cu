@@ -58,6 +58,11 @@ struct tb_handle {
     int32_t* orb2pad_local = nullptr;      // device copy
     int32_t* bcol_local = nullptr;         // device [nb]: block column local to its system
     int* flags_pool = nullptr;             // pinned [NPOOL][NFLAGS]: status words of the worker threads
+    // spectrum of S (Chebyshev corrections of TB_MIXED): bounds [s_lo, s_hi]
+    // from a Lanczos run on the host, computed once on first use
+    std::once_flag s_once;
+    double s_lo = 0.0, s_hi = 0.0;
+    tb_status s_status = TB_OK;
 };
 
 namespace {
@@ -140,6 +145,7 @@ struct View {
     const int32_t* o2p_d = nullptr;   // device [n_orb]
     int64_t n_orb = 0;
     int* flags_host = nullptr;        // pinned [NFLAGS]
+    tb_handle* owner = nullptr;       // the handle the view belongs to
 };
 
 tb_status check_opts(const tb_solve_opts* o) {
@@ -149,7 +155,178 @@ tb_status check_opts(const tb_solve_opts* o) {
     if (o->seed < 0 || o->force_switch_every < 0) return TB_ERR_INVALID_ARG;
     if (o->precision != TB_FP64 && o->precision != TB_MIXED) return TB_ERR_INVALID_ARG;
     if (o->precision == TB_MIXED && !(o->inner_lo_tol > 0.0 && o->inner_lo_tol < 1.0)) return TB_ERR_INVALID_ARG;
+    if (o->inner_method != TB_INNER_CHEBYSHEV && o->inner_method != TB_INNER_CG) return TB_ERR_INVALID_ARG;
     return TB_OK;
+}
+
+// ---- spectrum of S for the Chebyshev corrections ---------------------------
+// m Lanczos steps on S (FP64, the caller's blocks, no reorthogonalisation:
+// the extreme Ritz values are what is wanted, and lost orthogonality only
+// repeats converged ones), then the extreme eigenvalues theta of the
+// tridiagonal T by Sturm-count bisection and their residual norms
+// beta_m |y_m| (y the unit eigenvector of T, by inverse iteration).  Every
+// eigenvalue of S lies at or above lambda_min <= theta_min, and some
+// eigenvalue lies within the residual of each theta; the bounds widen both
+// by their residuals and by a relative margin.  A wrong bound costs
+// refinement rounds, never accuracy: the FP64 residual of every round
+// decides convergence.
+static uint64_t splitmix64(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int sturm_below(const std::vector<double>& a, const std::vector<double>& b, double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// k-th smallest eigenvalue (0-based) of the symmetric tridiagonal (a, b)
+static double tri_eig(const std::vector<double>& a, const std::vector<double>& b, int k) {
+    const size_t m = a.size();
+    double lo = a[0], hi = a[0];
+    for (size_t i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(lo) + std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_below(a, b, mid) > k) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// |last component| of the unit eigenvector of (a, b) for eigenvalue theta
+static double tri_last_component(const std::vector<double>& a, const std::vector<double>& b, double theta) {
+    const size_t m = a.size();
+    const double shift = theta + 1e-10 * (std::fabs(theta) + 1.0);
+    std::vector<double> y(m, 1.0), c(m), d(m);
+    for (int pass = 0; pass < 3; ++pass) {
+        // (T - shift) y_new = y by elimination without pivoting (tiny pivots
+        // replaced: only the direction of the result matters)
+        for (size_t i = 0; i < m; ++i) {
+            double piv = a[i] - shift - (i > 0 ? b[i - 1] * c[i - 1] : 0.0);
+            if (std::fabs(piv) < 1e-300) piv = 1e-300;
+            c[i] = i + 1 < m ? b[i] / piv : 0.0;
+            d[i] = (y[i] - (i > 0 ? b[i - 1] * d[i - 1] : 0.0)) / piv;
+        }
+        for (size_t i = m; i-- > 0;) y[i] = d[i] - (i + 1 < m ? c[i] * y[i + 1] : 0.0);
+        double nrm = 0.0;
+        for (double v : y) nrm += v * v;
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) return 1.0;
+        for (double& v : y) v /= nrm;
+    }
+    return std::fabs(y[m - 1]);
+}
+
+static void compute_s_bounds(tb_handle* h) {
+    const int n = h->n_atoms;
+    const int64_t N = h->n_orb;
+    std::vector<int64_t> ooff(n + 1, 0);
+    for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + h->orb_per_atom[i];
+    auto smul = [&](const std::vector<double>& x, std::vector<double>& y) {
+        for (int I = 0; I < n; ++I) {
+            const int ni = h->orb_per_atom[I];
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int64_t blk = h->brow_h[I]; blk < h->brow_h[I + 1]; ++blk) {
+                const int J = h->bcol_h[blk];
+                const int nj = h->orb_per_atom[J];
+                const double* sb = h->S_h.data() + h->boff_h[blk];
+                for (int a = 0; a < ni; ++a)
+                    for (int bj = 0; bj < nj; ++bj) acc[a] += sb[a * nj + bj] * x[ooff[J] + bj];
+            }
+            for (int a = 0; a < ni; ++a) y[ooff[I] + a] = acc[a];
+        }
+    };
+    const int m_max = (int)std::min<int64_t>(N, 80);
+    std::vector<double> q(N), qp(N, 0.0), w(N), al, be;
+    uint64_t seed = 0x5EED5EEDull;
+    double nrm = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        q[i] = (double)(splitmix64(seed) >> 11) * 0x1.0p-53 - 0.5;
+        nrm += q[i] * q[i];
+    }
+    nrm = std::sqrt(nrm);
+    for (double& v : q) v /= nrm;
+    double beta = 0.0, amax = 0.0;
+    for (int j = 0; j < m_max; ++j) {
+        smul(q, w);
+        double a = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            w[i] -= beta * qp[i];
+            a += q[i] * w[i];
+        }
+        double b2 = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            w[i] -= a * q[i];
+            b2 += w[i] * w[i];
+        }
+        beta = std::sqrt(b2);
+        al.push_back(a);
+        be.push_back(beta);
+        amax = std::max(amax, std::fabs(a));
+        if (!std::isfinite(beta) || beta <= 1e-12 * amax) break;   // invariant subspace
+        for (int64_t i = 0; i < N; ++i) {
+            qp[i] = q[i];
+            q[i] = w[i] / beta;
+        }
+    }
+    const int m = (int)al.size();
+    std::vector<double> boff(be.begin(), be.end() - 1);
+    const double tmin = tri_eig(al, boff, 0), tmax = tri_eig(al, boff, m - 1);
+    const double bm = be.back();
+    const double rmin = bm * tri_last_component(al, boff, tmin);
+    const double rmax = bm * tri_last_component(al, boff, tmax);
+    if (!(tmin > 0.0) || !std::isfinite(tmax)) {
+        h->s_status = std::isfinite(tmin) ? TB_ERR_S_NOT_SPD : TB_ERR_INVALID_ARG;
+        return;
+    }
+    h->s_lo = 0.97 * (tmin - rmin);     // <= 0: no usable lower bound, the FP32 CG is used
+    h->s_hi = 1.01 * (tmax + rmax);
+}
+
+tb_status s_bounds(tb_handle* h, double& lo, double& hi) {
+    std::call_once(h->s_once, compute_s_bounds, h);
+    lo = h->s_lo;
+    hi = h->s_hi;
+    return h->s_status;
+}
+
+// Coefficients of the Chebyshev corrections: n steps (odd, so that d_n ends
+// in x32) reduce the error by at least 1 / T_n(1 / sigma) <= tol.
+struct ChebPlan {
+    int n = 0;                 // 0: FP32 CG corrections
+    float gamma = 0.f;
+    std::vector<float> omega;  // omega[k] multiplies step k (1 <= k < n)
+};
+
+ChebPlan cheb_plan(double lo, double hi, double tol, int cap) {
+    ChebPlan cp;
+    if (!(lo > 0.0) || !(hi > lo)) return cp;
+    const double sigma = (hi - lo) / (hi + lo);
+    int n = (int)std::ceil(std::acosh(1.0 / tol) / std::acosh(1.0 / sigma));
+    n = std::max(n, 1);
+    if ((n & 1) == 0) ++n;
+    if (n > cap) return cp;
+    cp.n = n;
+    cp.gamma = (float)(2.0 / (lo + hi));
+    cp.omega.assign(n, 0.f);
+    double om = 1.0;
+    for (int k = 1; k < n; ++k) {
+        om = (k == 1) ? 1.0 / (1.0 - 0.5 * sigma * sigma) : 1.0 / (1.0 - 0.25 * om * sigma * sigma);
+        cp.omega[k] = (float)om;
+    }
+    return cp;
 }
 
 // Inner CG for S r' = r on the current panel; one host synchronisation in the
@@ -232,10 +409,23 @@ void debug_inner32(View& v, const PanelDev& p, int round, cudaStream_t st) {
 static const bool g_trace = std::getenv("TB_TRACE") != nullptr;
 
 tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_max, int& pred32,
-                      int& rounds_pred, int64_t& inner_total, cudaStream_t st) {
+                      int& rounds_pred, int64_t& inner_total, const ChebPlan& cp, cudaStream_t st) {
+    // Chebyshev corrections for the first rounds (no host round trip); a
+    // solve that needs more rounds than that finishes with FP32 CG
+    auto cheb_round = [&](int round) { return cp.n > 0 && round < 3; };
     launch_refine_start(v.ds, p, b, st);
-    launch_refine_scale(v.ds, p, b, st);
+    launch_refine_scale(v.ds, p, b, cheb_round(0) ? cp.gamma : 0.f, st);   // f and d_1
     for (int round = 0;; ++round) {
+        if (cheb_round(round)) {
+            for (int k = 1; k < cp.n; ++k) {
+                const float2* cur = (k & 1) ? p.x32 : p.p32;
+                float2* io = (k & 1) ? p.p32 : p.x32;
+                const int mode = k == cp.n - 1 ? 2 : (k == 1 ? 1 : 0);   // 2: adds d_n to the FP64 solution
+                launch_inner32_cheb(v.ds, p, cur, io, cp.omega[k], cp.gamma, mode, st);
+            }
+            if (cp.n == 1) launch_refine_add(v.ds, p, st);
+            inner_total += cp.n;
+        } else {
         tb_status s = inner_cg32(v, p, inner_max, pred32, inner_total, st);
         if (s != TB_OK) return s;
         if (g_trace && p.hist) {
@@ -272,8 +462,9 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
             return TB_OK;
         }
         launch_refine_add(v.ds, p, st);
+        }
         launch_refine_residual(v.ds, p, b, st);
-        launch_refine_scale(v.ds, p, p.Rin, st);
+        launch_refine_scale(v.ds, p, p.Rin, cheb_round(round + 1) ? cp.gamma : 0.f, st);
         if (g_trace) {
             cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st);
             cudaStreamSynchronize(st);
@@ -292,6 +483,7 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
             TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
             TB_CK(cudaStreamSynchronize(st));
             prof_harvest();
+            if (v.flags_host[0] & ERR_BREAKDOWN) return TB_ERR_BREAKDOWN;
             if (v.flags_host[4] == 0) {
                 rounds_pred = round + 1;
                 return TB_OK;
@@ -305,13 +497,26 @@ struct InnerCtx {
     int pred = 64, pred32 = 32, rounds = 2;
     int64_t total = 0;
     int redo = 0;
+    ChebPlan cheb;
 };
+
+// The Chebyshev plan of a solve's inner corrections (TB_MIXED with
+// TB_INNER_CHEBYSHEV and a usable spectrum of S).
+tb_status inner_ctx_init(const View& v, const tb_solve_opts* o, InnerCtx& ic) {
+    if (o->precision != TB_MIXED || o->inner_method != TB_INNER_CHEBYSHEV || !v.owner) return TB_OK;
+    double lo = 0.0, hi = 0.0;
+    const tb_status s = s_bounds(v.owner, lo, hi);
+    if (s != TB_OK) return s;
+    ic.cheb = cheb_plan(lo, hi, o->inner_lo_tol, o->inner_max_iter);
+    return TB_OK;
+}
 
 tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic,
                       cudaStream_t st) {
     if (!p.mixed) return inner_cg(v, p, inner_max, ic.pred, ic.total, st);
-    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, st);
+    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, st);
     if (s != TB_ERR_BREAKDOWN && s != TB_ERR_NOT_CONVERGED) return s;
+    ic.cheb.n = 0;   // the rest of this solve uses the FP32 CG corrections
     // The FP32 corrections failed to converge (or produced a non-finite
     // residual): redo this inner solve with the FP64 CG, on the device.
     // flags[0] keeps no trace of the failed attempt.
@@ -443,6 +648,7 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
     int64_t outer_total = 0, max_col_iters = 0;
     int switches = 0, unconverged = 0, errbits = 0;
     InnerCtx ic;
+    if ((s = inner_ctx_init(v, o, ic)) != TB_OK) return s;
     tb_status final_status = TB_OK;
 
     for (int c0 = 0; c0 < R; c0 += P) {
@@ -553,6 +759,7 @@ View whole_view(tb_handle* h) {
     v.o2p_d = h->orb2pad;
     v.n_orb = h->n_orb;
     v.flags_host = h->flags_host;
+    v.owner = h;
     return v;
 }
 
@@ -951,6 +1158,7 @@ void tb_default_opts(tb_solve_opts* o) {
     o->force_switch_every = 0;
     o->precision = TB_FP64;
     o->inner_lo_tol = 1e-6;
+    o->inner_method = TB_INNER_CHEBYSHEV;
 }
 
 int64_t tb_launch_count(void) { return launch_count(); }
@@ -1276,6 +1484,11 @@ tb_status tb_create_batch(tb_handle** out, const tb_system_desc* descs, int32_t 
         h->sys_ds.push_back(v);
     }
     return TB_OK;
+}
+
+tb_status tb_overlap_bounds(tb_handle* h, double* lo, double* hi) {
+    if (!h || !lo || !hi) return TB_ERR_INVALID_ARG;
+    return s_bounds(h, *lo, *hi);
 }
 
 int32_t tb_num_systems(const tb_handle* h) { return h ? (int32_t)h->sys_atom_off.size() - 1 : 0; }
@@ -1806,6 +2019,7 @@ tb_status tb_generalized_lanczos_batch(tb_handle* h, int32_t R, const int32_t* c
         TB_CK(cudaMemsetAsync(ap, 0, sizeof(double) * P * n_steps, st));
         TB_CK(cudaMemsetAsync(bp, 0, sizeof(double) * P * (n_steps + 1), st));
         InnerCtx ic;
+        if ((s = inner_ctx_init(v, opts, ic)) != TB_OK) return s;
         // u^0 = S^-1 e_j / sqrt(e_j^T S^-1 e_j); inner solves take the right-hand
         // side in Rcur (refinement) and Rin (FP64 CG), the solution in Rp
         launch_panel_init(h->ds, p, st);

@@ -129,7 +129,8 @@ struct PanelDev {
 // kernel classes for launch accounting (same order as the TB_K_* constants
 // of the public header)
 enum { K_INNER_SPMV = 0, K_INNER_UPDATE, K_OUTER_SPMM, K_OUTER_UPDATE, K_FINISH, K_SHIFT_STEP,
-       K_FULL_UPDATE, K_OTHER, K_INNER32_SPMV, K_INNER32_UPDATE, K_REFINE_RESIDUAL, K_REFINE_AUX, K_CSC, K_COUNT };
+       K_FULL_UPDATE, K_OTHER, K_INNER32_SPMV, K_INNER32_UPDATE, K_REFINE_RESIDUAL, K_REFINE_AUX, K_CSC, K_INNER32_CHEB,
+       K_COUNT };
 void profile_enable(bool on);
 void prof_harvest();
 void profile_read(int id, int64_t* launches, double* ms);
@@ -153,9 +154,11 @@ void launch_finish(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_refine_start(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st);
 void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st);
 void launch_refine_add(const DevSystem& s, const PanelDev& p, cudaStream_t st);
-void launch_refine_scale(const DevSystem& s, const PanelDev& p, const double2* src, cudaStream_t st);
+void launch_refine_scale(const DevSystem& s, const PanelDev& p, const double2* src, float cheb_gamma, cudaStream_t st);
 void launch_split_panel(const PanelDev& p, cudaStream_t st);
 void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
+void launch_inner32_cheb(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
+                         float gamma, int mode, cudaStream_t st);
 void launch_inner32_update(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st);

@@ -599,8 +599,11 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
     }
 }
 
-// FP32 right-hand side of the round: src * scale (0 for skipped columns)
-__global__ void k_refine_scale(PanelDev p, const double2* __restrict__ src) {
+// FP32 right-hand side of the round: src * scale (0 for a skipped real
+// column; columns with both parts skipped are left alone, no kernel of the
+// round reads them).  cheb_gamma > 0: also the first Chebyshev iterate
+// d_1 = gamma f into x32 (the next round makes Chebyshev corrections).
+__global__ void k_refine_scale(PanelDev p, const double2* __restrict__ src, float cheb_gamma) {
     const int P = p.P;
     const int c = threadIdx.x % P;
     if (blockIdx.x == 0) {
@@ -608,12 +611,16 @@ __global__ void k_refine_scale(PanelDev p, const double2* __restrict__ src) {
         if (threadIdx.x == 0) p.flags[7] = -1;                                  // no CG scalars yet
     }
     if (!p.col[c].active) return;
-    const double s0 = p.inner32[2 * c].scale, s1 = p.inner32[2 * c + 1].scale;
+    const InnerState i0 = p.inner32[2 * c], i1 = p.inner32[2 * c + 1];
+    if (i0.skip && i1.skip) return;
+    const double s0 = i0.scale, s1 = i1.scale;
     const long long items = (long long)p.npad * P;
     for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
          idx += (long long)gridDim.x * THREADS) {
         const double2 v = src[idx];
-        p.r32[idx] = make_float2((float)(v.x * s0), (float)(v.y * s1));
+        const float2 f = make_float2((float)(v.x * s0), (float)(v.y * s1));
+        p.r32[idx] = f;
+        if (cheb_gamma > 0.f) p.x32[idx] = make_float2(cheb_gamma * f.x, cheb_gamma * f.y);
     }
 }
 
@@ -1090,6 +1097,125 @@ __global__ void k_inner32_update(PanelDev p, int it) {
         s32[idx] = sv;
         x32[idx] = xv;
         r32[idx] = rn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 corrections of a refinement round by Chebyshev iteration (the default
+// of TB_MIXED).  With the spectrum of S inside [a, b] (bounds from a Lanczos
+// run on S, with margins), gamma = 2 / (a + b) and sigma = (b - a) / (b + a),
+// the semi-iterative recurrence
+//     d_0 = 0,  d_1 = gamma f,
+//     d_{k+1} = d_{k-1} + omega_{k+1} (gamma (f - S d_k) + d_k - d_{k-1}),
+//     omega_2 = 1 / (1 - sigma^2 / 2),  omega_{k+1} = 1 / (1 - omega_k sigma^2 / 4),
+// reduces the error of S d = f by 1 / T_k(1 / sigma) after k steps (T_k the
+// Chebyshev polynomial).  Its coefficients are fixed in advance, so a step
+// needs no inner product: the product S d_k and the update of the own rows
+// are one kernel, and the FP64 residual of the refinement decides what is
+// left.  d_k and d_{k-1} alternate between x32 and p32; d_{k+1} overwrites
+// d_{k-1} in place (each element is read and written by one thread only,
+// and the gather reads d_k alone).  f is the round's right-hand side r32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool cheb_live(const PanelDev& p, int c) {
+    return p.col[c].active && !(p.inner32[2 * c].skip && p.inner32[2 * c + 1].skip);
+}
+
+// One Chebyshev step: io <- io + omega (gamma (f - S cur) + cur - io) on the
+// own rows, with S cur gathered as in k_inner32_spmv (CPT complex columns
+// per thread, P / CPT threads per block row, PW the panel width when it is
+// a compile-time constant).  mode 1: the first step (d_0 = 0, io is not
+// read).  mode 2: the last step, which adds its result to the FP64 solution
+// of the refinement instead of storing it (x += d_n / scale and the
+// double-float split, as k_refine_add; a non-finite value is dropped).
+template <int CPT, int PW = 0>
+__global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelDev p, const float2* __restrict__ cur,
+                                                            float2* io, float omega, float gamma, int mode) {
+    if (*(volatile int*)&p.flags[4] == 0) return;
+    const int P = PW > 0 ? PW : p.P;
+    const int TPR = P / CPT;
+    const int t0 = threadIdx.x % TPR;
+    const int c0 = t0 * CPT;
+    bool live = false;
+    double fin[2 * CPT];   // mode 2: 1 / scale of every real column, 0 for a skipped one
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+        live |= cheb_live(p, c0 + j);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const InnerState is = p.inner32[2 * (c0 + j) + part];
+            fin[2 * j + part] = (p.col[c0 + j].active && !is.skip) ? 1.0 / is.scale : 0.0;
+        }
+    }
+    if (!live) return;
+    const long long items = (long long)s.n_atoms * TPR;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const int I = (int)(idx / TPR);
+        float acc[4][2 * CPT];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 2 * CPT; ++q) acc[a][q] = 0.f;
+        const int b0 = s.brow[I], b1 = s.brow[I + 1];
+        int Jn = __ldg(s.bcol + b0);
+        for (int bb = b0; bb < b1; ++bb) {
+            const int J = Jn;
+            if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
+            float xv[4][2 * CPT];
+            const float2* xb = cur + (size_t)(4 * J) * P + c0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2* xr = xb + e * P;
+                if (CPT == 2) {
+                    const float4 q4 = *reinterpret_cast<const float4*>(xr);
+                    xv[e][0] = q4.x; xv[e][1] = q4.y; xv[e][2] = q4.z; xv[e][3] = q4.w;
+                } else {
+                    const float2 q2 = *xr;
+                    xv[e][0] = q2.x; xv[e][1] = q2.y;
+                }
+            }
+            const float4* Sb = reinterpret_cast<const float4*>(s.S32 + 16 * (size_t)bb);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float4 sr = __ldg(Sb + a);
+#pragma unroll
+                for (int q = 0; q < 2 * CPT; ++q)
+                    acc[a][q] += sr.x * xv[0][q] + sr.y * xv[1][q] + sr.z * xv[2][q] + sr.w * xv[3][q];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const size_t e = (size_t)(4 * I + a) * P + c0;
+            float f[2 * CPT], dc[2 * CPT], dp[2 * CPT];
+            if (CPT == 2) {
+                const float4 f4 = *reinterpret_cast<const float4*>(p.r32 + e);
+                const float4 c4 = *reinterpret_cast<const float4*>(cur + e);
+                const float4 p4 = mode == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(io + e);
+                f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
+                dc[0] = c4.x; dc[1] = c4.y; dc[2] = c4.z; dc[3] = c4.w;
+                dp[0] = p4.x; dp[1] = p4.y; dp[2] = p4.z; dp[3] = p4.w;
+            } else {
+                const float2 f2 = p.r32[e], c2 = cur[e], p2 = mode == 1 ? make_float2(0.f, 0.f) : io[e];
+                f[0] = f2.x; f[1] = f2.y; dc[0] = c2.x; dc[1] = c2.y; dp[0] = p2.x; dp[1] = p2.y;
+            }
+            float dn[2 * CPT];
+#pragma unroll
+            for (int q = 0; q < 2 * CPT; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - acc[a][q]) + dc[q] - dp[q]);
+            if (mode == 2) {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    double2 x = p.Rp[e + j];
+                    if (fin[2 * j] != 0.0 && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] * fin[2 * j];
+                    if (fin[2 * j + 1] != 0.0 && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] * fin[2 * j + 1];
+                    p.Rp[e + j] = x;
+                    p.RpS[e + j] = df_split(x);
+                }
+            } else if (CPT == 2) {
+                *reinterpret_cast<float4*>(io + e) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+            } else {
+                io[e] = make_float2(dn[0], dn[1]);
+            }
+        }
     }
 }
 
@@ -2064,9 +2190,9 @@ void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2
     LaunchScope ls_(K_REFINE_RESIDUAL, st);
     k_refine_residual<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
 }
-void launch_refine_scale(const DevSystem&, const PanelDev& p, const double2* src, cudaStream_t st) {
+void launch_refine_scale(const DevSystem&, const PanelDev& p, const double2* src, float cheb_gamma, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_AUX, st);
-    k_refine_scale<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, src);
+    k_refine_scale<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, src, cheb_gamma);
 }
 void launch_split_panel(const PanelDev& p, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_AUX, st);
@@ -2115,6 +2241,25 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
     }
     else
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
+}
+void launch_inner32_cheb(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
+                         float gamma, int mode, cudaStream_t st) {
+    LaunchScope ls_(K_INNER32_CHEB, st);
+    if (p.P >= 2) {
+        const int g = grid_for((long long)s.n_atoms * (p.P / 2));
+        switch (p.P) {
+            case 256: k_inner32_cheb<2, 256><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 128: k_inner32_cheb<2, 128><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 64: k_inner32_cheb<2, 64><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 32: k_inner32_cheb<2, 32><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 16: k_inner32_cheb<2, 16><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 8: k_inner32_cheb<2, 8><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 4: k_inner32_cheb<2, 4><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            default: k_inner32_cheb<2><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+        }
+    } else {
+        k_inner32_cheb<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode);
+    }
 }
 void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
     LaunchScope ls_(K_INNER32_UPDATE, st);

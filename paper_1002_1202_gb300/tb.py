@@ -48,6 +48,10 @@ class SystemDesc(C.Structure):
     ]
 
 
+TB_INNER_CHEBYSHEV = 0
+TB_INNER_CG = 1
+
+
 class SolveOpts(C.Structure):
     _fields_ = [
         ("tol", C.c_double),
@@ -60,6 +64,7 @@ class SolveOpts(C.Structure):
         ("force_switch_every", C.c_int32),
         ("precision", C.c_int32),
         ("inner_lo_tol", C.c_double),
+        ("inner_method", C.c_int32),
     ]
 
 
@@ -118,6 +123,7 @@ SIGNATURES = [
     ("tb_band_energy", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), _VP, _VP, _VP,
                                  C.POINTER(Stats), _VP]),
     ("tb_forces", C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("tb_overlap_bounds", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("tb_mulliken_vjp", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, C.POINTER(SolveOpts), _VP, _VP,
                                   C.POINTER(Stats), _VP]),
     ("tb_mulliken_orbital", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.c_int32, _I32P,
@@ -143,7 +149,7 @@ SIGNATURES = [
 
 KERNELS = {"inner_spmv": 0, "inner_update": 1, "outer_spmm": 2, "outer_update": 3, "finish": 4,
            "shift_step": 5, "full_update": 6, "other": 7, "inner32_spmv": 8, "inner32_update": 9,
-           "refine_residual": 10, "refine_aux": 11, "csc": 12}
+           "refine_residual": 10, "refine_aux": 11, "csc": 12, "inner32_cheb": 13}
 
 _lib = None
 
@@ -395,6 +401,14 @@ def tb_band_energy(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None, n_va
                                       _stream(stream))
     _check(s, "tb_band_energy", allow_unconverged)
     return float(E[0]), gH, gS, _stats_dict(st, None, h.n_orb, K, s)
+
+
+def tb_overlap_bounds(h: Handle):
+    """(lo, hi): the bounds of the spectrum of S used by the Chebyshev
+    corrections of the mixed-precision inner solve."""
+    lo, hi = C.c_double(), C.c_double()
+    _check(load_library().tb_overlap_bounds(h.ptr, C.byref(lo), C.byref(hi)), "tb_overlap_bounds", False)
+    return lo.value, hi.value
 
 
 def tb_mulliken_vjp(h: Handle, z, w, v, n_values: int, g_s=2.0, opts: SolveOpts | None = None, stream=None,

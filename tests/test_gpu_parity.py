@@ -49,11 +49,17 @@ def h1(P, c1):
     return P.tb_create_system(c1[0])
 
 
-@pytest.fixture(params=[0, 1], ids=["fp64", "mixed"])
+@pytest.fixture(params=[0, 1, 2], ids=["fp64", "mixed", "mixed-cg"])
 def prec(request):
-    """TB_FP64, or TB_MIXED (FP32 inner CG inside FP64 refinement): both must
-    meet the same parity bars."""
+    """TB_FP64; TB_MIXED with its default Chebyshev corrections inside FP64
+    refinement; TB_MIXED with FP32 CG corrections (2 here): all must meet
+    the same parity bars."""
     return request.param
+
+
+def _pm(prec):
+    """Options of a `prec` case."""
+    return dict(precision=min(prec, 1), inner_method=1 if prec == 2 else 0)
 
 
 def _true_rel_res(H, S, z, X, cols):
@@ -69,7 +75,7 @@ def _true_rel_res(H, S, z, X, cols):
 
 def test_full_mode_c1(P, c1, c1_ref, h1, prec):
     s, H, S, z, w, cols = c1
-    x, st = P.tb_shifted_cocg(h1, z, cols, opts=P.tb_default_opts(precision=prec))
+    x, st = P.tb_shifted_cocg(h1, z, cols, opts=P.tb_default_opts(**_pm(prec)))
     X = x.cpu().numpy()
     assert st["status"] == "TB_OK" and st["unconverged"] == 0
     assert np.all(st["conv_iter"] > 0) and st["switches"] >= 1
@@ -94,7 +100,7 @@ def test_complex_symmetry(P, c1, h1):
 def test_fixed_iterations_match_method_oracle(P, c1, h1, force, prec):
     s, H, S, z, w, cols = c1
     n = 30
-    opts = P.tb_default_opts(max_iter=n, force_switch_every=force, precision=prec)
+    opts = P.tb_default_opts(max_iter=n, force_switch_every=force, **_pm(prec))
     x, st = P.tb_shifted_cocg(h1, z, cols[:3], opts=opts, allow_unconverged=True)
     X = x.cpu().numpy()
     for c, j in enumerate(cols[:3]):
@@ -135,14 +141,14 @@ def c1_mulliken(c1):
 
 def test_mulliken_orbital(P, c1, c1_mulliken, h1, prec):
     s, H, S, z, w, cols = c1
-    q, st = P.tb_mulliken_orbital(h1, z, w, cols, 2.0, opts=P.tb_default_opts(precision=prec))
+    q, st = P.tb_mulliken_orbital(h1, z, w, cols, 2.0, opts=P.tb_default_opts(**_pm(prec)))
     q = q.cpu().numpy()
     assert np.abs(q - c1_mulliken[cols]).max() <= 1e-6
 
 
 def test_mulliken_charges_and_sum_rule(P, c1, c1_mulliken, h1, prec):
     s, H, S, z, w, cols = c1
-    q, st = P.tb_mulliken_charges(h1, z, w, 2.0, opts=P.tb_default_opts(precision=prec))
+    q, st = P.tb_mulliken_charges(h1, z, w, 2.0, opts=P.tb_default_opts(**_pm(prec)))
     q = q.cpu().numpy()
     ref = dense.mulliken_atom(c1_mulliken, s.orbital_atom(), s.n_atoms)
     assert np.abs(q - ref).max() <= 1e-6
@@ -179,7 +185,7 @@ def test_panel_split_with_ragged_tail(P, c1, c1_ref, h1, prec):
     s, H, S, z, w, cols = c1
     cols13 = choose_columns(256, 13, seed=7)
     zz = z[::6]
-    opts = P.tb_default_opts(panel=8, precision=prec)
+    opts = P.tb_default_opts(panel=8, **_pm(prec))
     x, st = P.tb_shifted_cocg(h1, zz, cols13, opts=opts)
     X = x.cpu().numpy()
     res = _true_rel_res(H, S, zz, X, cols13)
@@ -201,7 +207,7 @@ def test_water_ragged_blocks(P, prec):
     z, w = linspace_grid(8, -35.0, 5.0, 0.05)
     cols = [0, 1, 4, s.n_orb - 1]
     h = P.tb_create_system(s)
-    opts = P.tb_default_opts(precision=prec)
+    opts = P.tb_default_opts(**_pm(prec))
     x, st = P.tb_shifted_cocg(h, z, cols, opts=opts)
     X = x.cpu().numpy()
     assert _true_rel_res(H, S, z, X, cols).max() <= 1e-8
@@ -294,7 +300,7 @@ def test_overlap_not_positive_definite(P, c1, prec):
                 sv[bo[b]:bo[b + 1]] *= 3.0       # eigenvalues 1 + 3(l - 1) < 0
     h = P.tb_create(s.orb_per_atom, s.brow_ptr, s.bcol, sv, None, s.eps, s.K)
     with pytest.raises(P.TBError) as e:
-        P.tb_shifted_cocg(h, linspace_grid(4)[0], [0], opts=P.tb_default_opts(precision=prec))
+        P.tb_shifted_cocg(h, linspace_grid(4)[0], [0], opts=P.tb_default_opts(**_pm(prec)))
     assert e.value.status == 3
 
 
@@ -323,10 +329,11 @@ def test_full_size_sampled_columns(P, precision, ncols, panel, sample, rtol):
     inner 1e-12).  Sampled columns, from every panel, after 12 outer steps,
     against the oracle's method on the same column.  Both sides solve
     S r' = r only to inner_tol = 1e-12, by different solvers (FP64 CG against
-    FP32 CG inside FP64 refinement); to first order the populations then
+    FP32 corrections inside FP64 refinement); to first order the populations then
     differ by up to n cond(A) inner_tol ~ 12 x (40 eV / 0.01 eV) x 1e-12
     ~ 5e-8, hence 1e-7 for the mixed case (the FP64 case runs the oracle's
-    own CG steps and agrees to 1e-9)."""
+    own CG steps and agrees to 1e-9).  The mixed case runs the default
+    Chebyshev corrections inside FP64 refinement."""
     s = si_system((8, 8, 8), sigma=0.05, seed=3, cutoff=4.0)
     z, w = gauss_legendre_grid(256, -20.0, 5.0, 0.01)
     cols = choose_columns(s.n_orb, ncols, seed=5)
@@ -362,7 +369,7 @@ def test_mixed_inner_tolerances(P, c1, h1):
 
 @pytest.mark.parametrize("group", ["0", "2", "16"], ids=["gather", "group2", "group16"])
 def test_mixed_spmv_forms(P, c1, monkeypatch, group):
-    """The FP32 inner SpMV of TB_MIXED in its register-gather form (no atom
+    """The FP32 CG SpMV of TB_MIXED in its register-gather form (no atom
     groups) and its grouped shared-memory form (groups of 2 and 16 atoms,
     40 columns: a 64-column panel, two 32-column slices, ragged tail) give
     the oracle's fixed-iteration iterates and fully converged solutions."""
@@ -372,19 +379,19 @@ def test_mixed_spmv_forms(P, c1, monkeypatch, group):
     monkeypatch.delenv("TB_SPMV_GROUP")
     many = choose_columns(256, 40, seed=5)
     n = 25
-    opts = P.tb_default_opts(max_iter=n, precision=1)
+    opts = P.tb_default_opts(max_iter=n, precision=1, inner_method=1)
     x, st = P.tb_shifted_cocg(h, z[::4], many, opts=opts, allow_unconverged=True)
     X = x.cpu().numpy()
     for c in (0, 17, 39):
         ref = method.generalized_shifted_cocg(H, S, z[::4], int(many[c]), max_iter=n)["x"]
         assert np.abs(X[:, c] - ref).max() <= 1e-9 * np.abs(ref).max()
-    x, st = P.tb_shifted_cocg(h, z[::4], many, opts=P.tb_default_opts(precision=1))
+    x, st = P.tb_shifted_cocg(h, z[::4], many, opts=P.tb_default_opts(precision=1, inner_method=1))
     assert st["status"] == "TB_OK"
     assert _true_rel_res(H, S, z[::4], x.cpu().numpy(), many).max() <= 1e-8
 
 
 def test_mixed_spmv_grouped_water(P, monkeypatch):
-    """Grouped FP32 SpMV on ragged blocks (O: 4 orbitals, H: 1) with a
+    """Grouped FP32 CG SpMV on ragged blocks (O: 4 orbitals, H: 1) with a
     partial last group: converged Mulliken populations of 36 columns."""
     s = water_system(32, seed=4)
     S = s.dense_S()
@@ -394,6 +401,36 @@ def test_mixed_spmv_grouped_water(P, monkeypatch):
     monkeypatch.setenv("TB_SPMV_GROUP", "16")
     h = P.tb_create_system(s)
     monkeypatch.delenv("TB_SPMV_GROUP")
-    q, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1))
+    q, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1, inner_method=1))
     ref = dense.mulliken_orbital(H, S, z, w, 2.0)[cols]
     assert np.abs(q.cpu().numpy() - ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("which", ["si64", "water8"])
+def test_overlap_bounds(P, c1, which):
+    """The Chebyshev bounds enclose the spectrum of S (dense eigenvalues)
+    and are tight to within their margins."""
+    if which == "si64":
+        s = c1[0]
+    else:
+        s = water_system(8, seed=4, cutoff=3.0, excess_proton=False)
+    ev = np.linalg.eigvalsh(s.dense_S())
+    lo, hi = P.tb_overlap_bounds(P.tb_create_system(s))
+    assert 0.0 < lo <= ev[0] and hi >= ev[-1]
+    assert lo >= 0.9 * ev[0] and hi <= 1.05 * ev[-1]
+
+
+def test_chebyshev_and_cg_corrections_agree(P, c1, h1):
+    """Mixed precision with Chebyshev and with CG corrections: converged
+    Mulliken populations of the same columns agree with each other and the
+    oracle to 1e-7 e; the Chebyshev solve launches fewer inner steps per
+    refinement round than CG needs iterations plus its scalar tails."""
+    s, H, S, z, w, cols = c1
+    ref = dense.mulliken_orbital(H, S, z, w, 2.0)[cols]
+    qs = []
+    for m in (0, 1):
+        q, st = P.tb_mulliken_orbital(h1, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1, inner_method=m))
+        assert st["status"] == "TB_OK"
+        qs.append(q.cpu().numpy())
+        assert np.abs(qs[-1] - ref).max() <= 1e-7
+    assert np.abs(qs[0] - qs[1]).max() <= 1e-7
