@@ -1124,10 +1124,11 @@ __device__ __forceinline__ bool cheb_live(const PanelDev& p, int c) {
 // own rows, with S cur gathered as in k_inner32_spmv (CPT complex columns
 // per thread, P / CPT threads per block row, PW the panel width when it is
 // a compile-time constant).  mode 1: the first step (d_0 = 0, io is not
-// read).  mode 2: the last step, which adds its result to the FP64 solution
-// of the refinement instead of storing it (x += d_n / scale and the
-// double-float split, as k_refine_add; a non-finite value is dropped).
-template <int CPT, int PW = 0>
+// read).  mode 2 (the LAST instance): the last step, which adds its result
+// to the FP64 solution of the refinement instead of storing it
+// (x += d_n / scale and the double-float split, as k_refine_add; a
+// non-finite value is dropped).
+template <int CPT, int PW = 0, bool LAST = false>
 __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelDev p, const float2* __restrict__ cur,
                                                             float2* io, float omega, float gamma, int mode) {
     if (*(volatile int*)&p.flags[4] == 0) return;
@@ -1136,16 +1137,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelD
     const int t0 = threadIdx.x % TPR;
     const int c0 = t0 * CPT;
     bool live = false;
-    double fin[2 * CPT];   // mode 2: 1 / scale of every real column, 0 for a skipped one
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-        live |= cheb_live(p, c0 + j);
-#pragma unroll
-        for (int part = 0; part < 2; ++part) {
-            const InnerState is = p.inner32[2 * (c0 + j) + part];
-            fin[2 * j + part] = (p.col[c0 + j].active && !is.skip) ? 1.0 / is.scale : 0.0;
-        }
-    }
+    for (int j = 0; j < CPT; ++j) live |= cheb_live(p, c0 + j);
     if (!live) return;
     const long long items = (long long)s.n_atoms * TPR;
     for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
@@ -1201,12 +1194,15 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelD
             float dn[2 * CPT];
 #pragma unroll
             for (int q = 0; q < 2 * CPT; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - acc[a][q]) + dc[q] - dp[q]);
-            if (mode == 2) {
+            if (LAST) {
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) {
+                    // 1 / scale of the real columns that took the round (0: skipped)
+                    const InnerState i0 = p.inner32[2 * (c0 + j)], i1 = p.inner32[2 * (c0 + j) + 1];
+                    const bool ca = p.col[c0 + j].active != 0;
                     double2 x = p.Rp[e + j];
-                    if (fin[2 * j] != 0.0 && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] * fin[2 * j];
-                    if (fin[2 * j + 1] != 0.0 && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] * fin[2 * j + 1];
+                    if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] / i0.scale;
+                    if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] / i1.scale;
                     p.Rp[e + j] = x;
                     p.RpS[e + j] = df_split(x);
                 }
@@ -2242,24 +2238,31 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
     else
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
 }
-void launch_inner32_cheb(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
-                         float gamma, int mode, cudaStream_t st) {
-    LaunchScope ls_(K_INNER32_CHEB, st);
+template <bool LAST>
+static void cheb_launch(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
+                        float gamma, int mode, cudaStream_t st) {
     if (p.P >= 2) {
         const int g = grid_for((long long)s.n_atoms * (p.P / 2));
         switch (p.P) {
-            case 256: k_inner32_cheb<2, 256><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
-            case 128: k_inner32_cheb<2, 128><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
-            case 64: k_inner32_cheb<2, 64><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
-            case 32: k_inner32_cheb<2, 32><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
-            case 16: k_inner32_cheb<2, 16><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
-            case 8: k_inner32_cheb<2, 8><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
-            case 4: k_inner32_cheb<2, 4><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
-            default: k_inner32_cheb<2><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 256: k_inner32_cheb<2, 256, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 128: k_inner32_cheb<2, 128, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 64: k_inner32_cheb<2, 64, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 32: k_inner32_cheb<2, 32, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 16: k_inner32_cheb<2, 16, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 8: k_inner32_cheb<2, 8, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 4: k_inner32_cheb<2, 4, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            default: k_inner32_cheb<2, 0, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
         }
     } else {
-        k_inner32_cheb<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode);
+        k_inner32_cheb<1, 0, LAST><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, cur, io, omega,
+                                                                                          gamma, mode);
     }
+}
+void launch_inner32_cheb(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
+                         float gamma, int mode, cudaStream_t st) {
+    LaunchScope ls_(K_INNER32_CHEB, st);
+    if (mode == 2) cheb_launch<true>(s, p, cur, io, omega, gamma, mode, st);
+    else cheb_launch<false>(s, p, cur, io, omega, gamma, mode, st);
 }
 void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
     LaunchScope ls_(K_INNER32_UPDATE, st);
