@@ -498,6 +498,7 @@ struct InnerCtx {
     int64_t total = 0;
     int redo = 0;
     ChebPlan cheb;
+    bool res_exact = false;   // Rin holds b - S r' of the last solve (double-float refinement residual)
 };
 
 // The Chebyshev plan of a solve's inner corrections (TB_MIXED with
@@ -513,8 +514,10 @@ tb_status inner_ctx_init(const View& v, const tb_solve_opts* o, InnerCtx& ic) {
 
 tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic,
                       cudaStream_t st) {
+    ic.res_exact = false;
     if (!p.mixed) return inner_cg(v, p, inner_max, ic.pred, ic.total, st);
     tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, st);
+    if (s == TB_OK) ic.res_exact = b == p.Rcur;
     if (s != TB_ERR_BREAKDOWN && s != TB_ERR_NOT_CONVERGED) return s;
     ic.cheb.n = 0;   // the rest of this solve uses the FP32 CG corrections
     // The FP32 corrections failed to converge (or produced a non-finite
@@ -696,7 +699,7 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
 
         int active = ncols;
         for (int n = 0; n < o->max_iter && active > 0; ++n) {
-            launch_outer_spmm(v.ds, p, st);
+            launch_outer_spmm(v.ds, p, ic.res_exact, st);
             launch_outer_update(v.ds, p, st);
             s = inner_solve(v, p, p.Rcur, o->inner_max_iter, ic, st);
             if (s != TB_OK) return s;

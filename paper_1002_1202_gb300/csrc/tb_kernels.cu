@@ -196,8 +196,11 @@ __global__ void k_panel_init(PanelDev p) {
 // A p_n = q + (beta_{n-1}/alpha_{n-1}) (r_{n-1} - r_n), mu = r'_n^T A p_n,
 // alpha_n = rho_n / mu (Eqs. CGp:p, CGp:r and the alpha_n of Section 3.3).
 // Pending seed-switch scales of r_n, r'_n, r_{n-1} are applied on the fly.
+// SX (mixed path): S r'_n is taken as r_n - res, res = r_n - S r'_n being
+// the refinement's last double-float residual (in Rin), so only H r'_n is
+// formed here -- half the double-float products.
 // ---------------------------------------------------------------------------
-template <bool DF>
+template <bool DF, bool SX = false>
 __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p) {
     __shared__ double smem[2 * THREADS];
     const int P = p.P;
@@ -230,14 +233,19 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
                     const float4* Hl = reinterpret_cast<const float4*>(s.H32lo + 16 * (size_t)b);
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
-                        const float4 s4h = __ldg(Sh + a), s4l = __ldg(Sl + a);
                         const float4 h4h = __ldg(Hh + a), h4l = __ldg(Hl + a);
-                        const float svh[4] = {s4h.x, s4h.y, s4h.z, s4h.w}, svl[4] = {s4l.x, s4l.y, s4l.z, s4l.w};
                         const float hvh[4] = {h4h.x, h4h.y, h4h.z, h4h.w}, hvl[4] = {h4l.x, h4l.y, h4l.z, h4l.w};
+                        if (!SX) {
+                            const float4 s4h = __ldg(Sh + a), s4l = __ldg(Sl + a);
+                            const float svh[4] = {s4h.x, s4h.y, s4h.z, s4h.w}, svl[4] = {s4l.x, s4l.y, s4l.z, s4l.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                df_mac(sh[a][0], sl[a][0], svh[e], svl[e], x[e].x, x[e].y);
+                                df_mac(sh[a][1], sl[a][1], svh[e], svl[e], x[e].z, x[e].w);
+                            }
+                        }
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            df_mac(sh[a][0], sl[a][0], svh[e], svl[e], x[e].x, x[e].y);
-                            df_mac(sh[a][1], sl[a][1], svh[e], svl[e], x[e].z, x[e].w);
                             df_mac(hh[a][0], hl[a][0], hvh[e], hvl[e], x[e].x, x[e].y);
                             df_mac(hh[a][1], hl[a][1], hvh[e], hvl[e], x[e].z, x[e].w);
                         }
@@ -245,7 +253,12 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    aS[a] = cmk((double)sh[a][0] + (double)sl[a][0], (double)sh[a][1] + (double)sl[a][1]);
+                    if (SX) {
+                        const size_t e = (size_t)(4 * I + a) * P + c;
+                        aS[a] = csub(p.Rcur[e], p.Rin[e]);
+                    } else {
+                        aS[a] = cmk((double)sh[a][0] + (double)sl[a][0], (double)sh[a][1] + (double)sl[a][1]);
+                    }
                     aH[a] = cmk((double)hh[a][0] + (double)hl[a][0], (double)hh[a][1] + (double)hl[a][1]);
                 }
             } else {
@@ -2145,10 +2158,12 @@ void launch_panel_init(const DevSystem&, const PanelDev& p, cudaStream_t st) {
         k_panel_init<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p);
     }
 }
-void launch_outer_spmm(const DevSystem& s, const PanelDev& p, cudaStream_t st) {
+void launch_outer_spmm(const DevSystem& s, const PanelDev& p, bool sx_from_residual, cudaStream_t st) {
     {
         LaunchScope ls_(K_OUTER_SPMM, st);
-        if (p.mixed)
+        if (p.mixed && sx_from_residual)
+            k_outer_spmm<true, true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+        else if (p.mixed)
             k_outer_spmm<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
         else
             k_outer_spmm<false><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
