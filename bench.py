@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
                     help="mixed: FP32 Chebyshev corrections inside FP64 refinement (FP64-accurate); fp64: every product in FP64")
+    ap.add_argument("--inner-method", choices=["chebyshev", "cg"], default="chebyshev",
+                    help="mixed: FP32 corrections by Chebyshev steps (default) or by FP32 CG")
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the other precision, reported beside the headline (0: skip)")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
@@ -247,7 +249,8 @@ def config_dict(args, s, precision=None):
         "n_atoms": s.n_atoms, "N": s.n_orb, "blocks": int(s.nb), "shifts": K_SHIFTS, "panel": args.panel,
         "panels_per_step": args.panels_per_step,
         "iterations_per_step": args.iters, "tol": args.tol, "inner_tol": args.inner_tol,
-        "precision": ("FP32 Chebyshev corrections (to 1e-6 per round) inside FP64 iterative refinement; FP64 outer SpMM, "
+        "precision": (("FP32 CG" if getattr(args, "inner_method", "chebyshev") == "cg" else "FP32 Chebyshev")
+                      + " corrections (to 1e-6 per round) inside FP64 iterative refinement; FP64 outer SpMM, "
                       "vectors, recurrences, switching and charges" if precision == "mixed" else "FP64 throughout"),
         "l2": "flushed (256 MiB write) before every timed step", "seed": SEED,
     }
@@ -380,9 +383,10 @@ def kernel_source_sha256(kernel_file, kernel_name):
     return None
 
 
-def stored_traffic(kernel_file, kernel_name):
+def stored_traffic(kernel_file, kernel_name, panel=None):
     """DRAM bytes per launch from a committed ncu summary, valid only while
-    the text of the kernel it was taken from is unchanged."""
+    the text of the kernel it was taken from is unchanged and (for entries
+    captured per panel width) for the panel width it was taken at."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -393,6 +397,10 @@ def stored_traffic(kernel_file, kernel_name):
     if not rec:
         return None
     if kernel_source_sha256(kernel_file, kernel_name) != rec.get("kernel_sha256"):
+        return None
+    if "by_panel" in rec:
+        return rec["by_panel"].get(str(panel))
+    if "panel" in rec and panel is not None and rec["panel"] != panel:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -461,7 +469,7 @@ def roofline_for(kname, ms, launches, s, panel, peaks, mixed=False, busy_ms=None
                 "avg_launch_us_basis": "busy time (union of launch intervals on all streams) / launches",
                 "mean_launch_duration_us": mean_s * 1e6,
                 "flops_per_launch": flops, "algorithmic_bytes_per_launch": int(nbytes),
-                "traffic": stored_traffic("tb_kernels.cu", kern)})
+                "traffic": stored_traffic("tb_kernels.cu", kern, panel)})
     return rec
 
 
@@ -492,12 +500,14 @@ def run_ours(args):
     s, z, w = workload()
     h = P.tb_create_system(s)
     prec = 1 if args.precision == "mixed" else 0
+    inner_method = P.tb.TB_INNER_CG if args.inner_method == "cg" else P.tb.TB_INNER_CHEBYSHEV
     tune = None
     if args.panel == 0:
         # panel-width autotune: 3 outer iterations per candidate, best rate wins
         tune = {}
         for cand in (64, 128, 256):
-            o_t = P.tb_default_opts(max_iter=3, panel=cand, tol=args.tol, precision=prec, inner_tol=args.inner_tol)
+            o_t = P.tb_default_opts(max_iter=3, panel=cand, tol=args.tol, precision=prec, inner_tol=args.inner_tol,
+                                    inner_method=inner_method)
             c_t = rank_columns(s.n_orb, cand * args.panels_per_step, rank)
             P.tb_mulliken_orbital(h, z, w, c_t, 2.0, opts=o_t, allow_unconverged=True)
             torch.cuda.synchronize()
@@ -514,7 +524,7 @@ def run_ours(args):
     cols = rank_columns(s.n_orb, args.panel * args.panels_per_step, rank)
     ncols = len(cols)
     opts = P.tb_default_opts(max_iter=args.iters, panel=args.panel, tol=args.tol, precision=prec,
-                             inner_tol=args.inner_tol)
+                             inner_tol=args.inner_tol, inner_method=inner_method)
     q_dev = torch.empty(ncols, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
