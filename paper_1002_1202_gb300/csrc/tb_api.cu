@@ -408,8 +408,15 @@ void debug_inner32(View& v, const PanelDev& p, int round, cudaStream_t st) {
 // TB_TRACE=1 in the environment prints the progress of every refinement round
 static const bool g_trace = std::getenv("TB_TRACE") != nullptr;
 
+// TB_GRAPHS=0 in the environment launches the Chebyshev steps one by one
+static const bool g_graphs = [] {
+    const char* e = std::getenv("TB_GRAPHS");
+    return !(e && std::atoi(e) == 0);
+}();
+
 tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_max, int& pred32,
-                      int& rounds_pred, int64_t& inner_total, const ChebPlan& cp, cudaStream_t st) {
+                      int& rounds_pred, int64_t& inner_total, const ChebPlan& cp, cudaGraphExec_t* graph,
+                      cudaStream_t st) {
     // Chebyshev corrections for the first rounds (no host round trip); a
     // solve that needs more rounds than that finishes with FP32 CG
     auto cheb_round = [&](int round) { return cp.n > 0 && round < 3; };
@@ -417,11 +424,17 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
     launch_refine_scale(v.ds, p, b, cheb_round(0) ? cp.gamma : 0.f, st);   // f and d_1
     for (int round = 0;; ++round) {
         if (cheb_round(round)) {
-            for (int k = 1; k < cp.n; ++k) {
-                const float2* cur = (k & 1) ? p.x32 : p.p32;
-                float2* io = (k & 1) ? p.p32 : p.x32;
-                const int mode = k == cp.n - 1 ? 2 : (k == 1 ? 1 : 0);   // 2: adds d_n to the FP64 solution
-                launch_inner32_cheb(v.ds, p, cur, io, cp.omega[k], cp.gamma, mode, st);
+            if (g_graphs && graph && !*graph && cp.n > 2)
+                cheb_graph_build(v.ds, p, cp.omega.data(), cp.n, cp.gamma, graph);
+            if (graph && *graph) {
+                cheb_graph_launch(*graph, cp.n - 1, st);
+            } else {
+                for (int k = 1; k < cp.n; ++k) {
+                    const float2* cur = (k & 1) ? p.x32 : p.p32;
+                    float2* io = (k & 1) ? p.p32 : p.x32;
+                    const int mode = k == cp.n - 1 ? 2 : (k == 1 ? 1 : 0);   // 2: adds d_n to the FP64 solution
+                    launch_inner32_cheb(v.ds, p, cur, io, cp.omega[k], cp.gamma, mode, st);
+                }
             }
             if (cp.n == 1) launch_refine_add(v.ds, p, st);
             inner_total += cp.n;
@@ -499,6 +512,13 @@ struct InnerCtx {
     int redo = 0;
     ChebPlan cheb;
     bool res_exact = false;   // Rin holds b - S r' of the last solve (double-float refinement residual)
+    // the Chebyshev steps of a round as a graph, captured on first use for
+    // the PanelDev of this context (its buffers stay fixed)
+    cudaGraphExec_t cheb_graph = nullptr;
+    InnerCtx() = default;
+    InnerCtx(const InnerCtx&) = delete;
+    InnerCtx& operator=(const InnerCtx&) = delete;
+    ~InnerCtx() { cheb_graph_destroy(cheb_graph); }
 };
 
 // The Chebyshev plan of a solve's inner corrections (TB_MIXED with
@@ -516,7 +536,7 @@ tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_ma
                       cudaStream_t st) {
     ic.res_exact = false;
     if (!p.mixed) return inner_cg(v, p, inner_max, ic.pred, ic.total, st);
-    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, st);
+    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, &ic.cheb_graph, st);
     if (s == TB_OK) ic.res_exact = b == p.Rcur;
     if (s != TB_ERR_BREAKDOWN && s != TB_ERR_NOT_CONVERGED) return s;
     ic.cheb.n = 0;   // the rest of this solve uses the FP32 CG corrections

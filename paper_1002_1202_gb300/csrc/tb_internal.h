@@ -160,6 +160,11 @@ void launch_split_panel(const PanelDev& p, cudaStream_t st);
 void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_inner32_cheb(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
                          float gamma, int mode, cudaStream_t st);
+// steps 1 .. n-1 of a Chebyshev round captured as a graph (false: not built)
+bool cheb_graph_build(const DevSystem& s, const PanelDev& p, const float* omega, int n, float gamma,
+                      cudaGraphExec_t* out);
+void cheb_graph_launch(cudaGraphExec_t g, int steps, cudaStream_t st);
+void cheb_graph_destroy(cudaGraphExec_t g);
 void launch_inner32_update(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_shift_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_shift_step(const DevSystem& s, const PanelDev& p, cudaStream_t st);

@@ -1991,12 +1991,18 @@ struct Profiler {
 };
 Profiler g_prof;
 
+// set while this thread captures launches into a CUDA graph: they run (and
+// are counted and timed) when the graph is launched
+thread_local bool g_capturing = false;
+
 struct LaunchScope {
     cudaStream_t st;
     size_t pair = (size_t)-1;
-    LaunchScope(int id, cudaStream_t s) : st(s) {
-        g_prof.total.fetch_add(1, std::memory_order_relaxed);
-        g_prof.launches[id].fetch_add(1, std::memory_order_relaxed);
+    // count: kernels this launch runs (a graph launch runs several)
+    LaunchScope(int id, cudaStream_t s, int count = 1) : st(s) {
+        if (g_capturing) return;
+        g_prof.total.fetch_add(count, std::memory_order_relaxed);
+        g_prof.launches[id].fetch_add(count, std::memory_order_relaxed);
         if (!g_prof.on) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
         if (g_prof.free_pairs.empty()) {
@@ -2278,6 +2284,49 @@ void launch_inner32_cheb(const DevSystem& s, const PanelDev& p, const float2* cu
     LaunchScope ls_(K_INNER32_CHEB, st);
     if (mode == 2) cheb_launch<true>(s, p, cur, io, omega, gamma, mode, st);
     else cheb_launch<false>(s, p, cur, io, omega, gamma, mode, st);
+}
+
+// Steps 1 .. n-1 of a Chebyshev round as one CUDA graph: the launches of a
+// round have the same arguments in every round of a panel (the kernels read
+// the round's state from device memory), so they are captured once, on a
+// private stream (the caller's may be the legacy default stream, which
+// cannot be captured), and replayed with one launch per round.
+bool cheb_graph_build(const DevSystem& s, const PanelDev& p, const float* omega, int n, float gamma,
+                      cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        g_capturing = true;
+        for (int k = 1; k < n; ++k) {
+            const float2* cur = (k & 1) ? p.x32 : p.p32;
+            float2* io = (k & 1) ? p.p32 : p.x32;
+            const int mode = k == n - 1 ? 2 : (k == 1 ? 1 : 0);
+            launch_inner32_cheb(s, p, cur, io, omega[k], gamma, mode, cs);
+        }
+        g_capturing = false;
+        ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+        cudaGetLastError();
+        *out = nullptr;
+    }
+    return ok;
+}
+void cheb_graph_launch(cudaGraphExec_t g, int steps, cudaStream_t st) {
+    LaunchScope ls_(K_INNER32_CHEB, st, steps);
+    cudaGraphLaunch(g, st);
+}
+void cheb_graph_destroy(cudaGraphExec_t g) {
+    if (g) cudaGraphExecDestroy(g);
 }
 void launch_inner32_update(const DevSystem&, const PanelDev& p, int it, cudaStream_t st) {
     LaunchScope ls_(K_INNER32_UPDATE, st);

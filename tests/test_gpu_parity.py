@@ -27,14 +27,19 @@ def P():
     return pkg
 
 
-@pytest.fixture(scope="module")
-def c1():
+def _c1_case():
     """Si 64 atoms, sp3 (N = 256), 32 shifts on [-20, 5] eV + 0.01i, 8 columns."""
     s = si_system((2, 2, 2), sigma=0.05, seed=1, cutoff=4.0)
-    S = s.dense_S()
-    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
     z, w = linspace_grid(32)
     cols = choose_columns(256, 8, seed=2)
+    return s, z, w, cols
+
+
+@pytest.fixture(scope="module")
+def c1():
+    s, z, w, cols = _c1_case()
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
     return s, H, S, z, w, cols
 
 
@@ -434,3 +439,29 @@ def test_chebyshev_and_cg_corrections_agree(P, c1, h1):
         qs.append(q.cpu().numpy())
         assert np.abs(qs[-1] - ref).max() <= 1e-7
     assert np.abs(qs[0] - qs[1]).max() <= 1e-7
+
+
+def test_graph_and_direct_launches_agree(P, c1, h1, tmp_path):
+    """The Chebyshev steps of a round replayed as a CUDA graph (default) and
+    launched one by one (TB_GRAPHS=0, in a child process) give bit-identical
+    populations: the same kernels with the same arguments in the same
+    order."""
+    import os
+    import subprocess
+    import sys
+    s, H, S, z, w, cols = c1
+    q, st = P.tb_mulliken_orbital(h1, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1, max_iter=30),
+                                  allow_unconverged=True)
+    out = tmp_path / "q.npy"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = (
+        "import numpy as np, paper_1002_1202_gb300 as P\n"
+        "from tests.test_gpu_parity import _c1_case\n"
+        "s, z, w, cols = _c1_case()\n"
+        "h = P.tb_create_system(s)\n"
+        "q, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1, max_iter=30),"
+        " allow_unconverged=True)\n"
+        f"np.save({str(out)!r}, q.cpu().numpy())\n")
+    env = dict(os.environ, TB_GRAPHS="0", PYTHONPATH=root)
+    subprocess.run([sys.executable, "-c", child], env=env, cwd=root, check=True, timeout=600)
+    assert np.array_equal(np.load(out), q.cpu().numpy())
