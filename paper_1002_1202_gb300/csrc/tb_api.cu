@@ -303,22 +303,36 @@ tb_status s_bounds(tb_handle* h, double& lo, double& hi) {
 }
 
 // Coefficients of the Chebyshev corrections: n steps (odd, so that d_n ends
-// in x32) reduce the error by at least 1 / T_n(1 / sigma) <= tol.
+// in x32) reduce the error by at least 1 / T_n(1 / sigma) <= lo_tol per
+// round.  R rounds are planned so that lo_tol^(R-1) times the last round's
+// reduction reaches inner_tol; the last one needs only that remainder
+// (with a factor 2 to spare) and takes n_last <= n steps.  The recurrence
+// coefficients do not depend on where it stops, so both share omega.
 struct ChebPlan {
     int n = 0;                 // 0: FP32 CG corrections
+    int n_last = 0;            // steps of round R - 1
+    int R = 1;                 // rounds planned
     float gamma = 0.f;
     std::vector<float> omega;  // omega[k] multiplies step k (1 <= k < n)
+    int steps(int round) const { return round == R - 1 ? n_last : n; }
 };
 
-ChebPlan cheb_plan(double lo, double hi, double tol, int cap) {
+static int cheb_steps(double sigma, double tol) {
+    int n = (int)std::ceil(std::acosh(1.0 / std::min(tol, 0.5)) / std::acosh(1.0 / sigma));
+    n = std::max(n, 1);
+    return (n & 1) ? n : n + 1;
+}
+
+ChebPlan cheb_plan(double lo, double hi, double lo_tol, double inner_tol, int cap) {
     ChebPlan cp;
     if (!(lo > 0.0) || !(hi > lo)) return cp;
     const double sigma = (hi - lo) / (hi + lo);
-    int n = (int)std::ceil(std::acosh(1.0 / tol) / std::acosh(1.0 / sigma));
-    n = std::max(n, 1);
-    if ((n & 1) == 0) ++n;
+    const int n = cheb_steps(sigma, lo_tol);
     if (n > cap) return cp;
     cp.n = n;
+    cp.R = std::max(1, (int)std::ceil(std::log(inner_tol) / std::log(lo_tol) - 1e-9));
+    const double rest = 0.5 * inner_tol / std::pow(lo_tol, cp.R - 1);
+    cp.n_last = std::min(n, cheb_steps(sigma, rest));
     cp.gamma = (float)(2.0 / (lo + hi));
     cp.omega.assign(n, 0.f);
     double om = 1.0;
@@ -424,20 +438,21 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
     launch_refine_scale(v.ds, p, b, cheb_round(0) ? cp.gamma : 0.f, st);   // f and d_1
     for (int round = 0;; ++round) {
         if (cheb_round(round)) {
-            if (g_graphs && graph && !*graph && cp.n > 2)
-                cheb_graph_build(v.ds, p, cp.omega.data(), cp.n, cp.gamma, graph);
-            if (graph && *graph) {
-                cheb_graph_launch(*graph, cp.n - 1, st);
+            const int n = cp.steps(round);
+            cudaGraphExec_t* gr = graph ? &graph[n == cp.n ? 0 : 1] : nullptr;
+            if (g_graphs && gr && !*gr && n > 2) cheb_graph_build(v.ds, p, cp.omega.data(), n, cp.gamma, gr);
+            if (gr && *gr) {
+                cheb_graph_launch(*gr, n - 1, st);
             } else {
-                for (int k = 1; k < cp.n; ++k) {
+                for (int k = 1; k < n; ++k) {
                     const float2* cur = (k & 1) ? p.x32 : p.p32;
                     float2* io = (k & 1) ? p.p32 : p.x32;
-                    const int mode = k == cp.n - 1 ? 2 : (k == 1 ? 1 : 0);   // 2: adds d_n to the FP64 solution
+                    const int mode = k == n - 1 ? 2 : (k == 1 ? 1 : 0);   // 2: adds d_n to the FP64 solution
                     launch_inner32_cheb(v.ds, p, cur, io, cp.omega[k], cp.gamma, mode, st);
                 }
             }
-            if (cp.n == 1) launch_refine_add(v.ds, p, st);
-            inner_total += cp.n;
+            if (n == 1) launch_refine_add(v.ds, p, st);
+            inner_total += n;
         } else {
         tb_status s = inner_cg32(v, p, inner_max, pred32, inner_total, st);
         if (s != TB_OK) return s;
@@ -512,13 +527,16 @@ struct InnerCtx {
     int redo = 0;
     ChebPlan cheb;
     bool res_exact = false;   // Rin holds b - S r' of the last solve (double-float refinement residual)
-    // the Chebyshev steps of a round as a graph, captured on first use for
-    // the PanelDev of this context (its buffers stay fixed)
-    cudaGraphExec_t cheb_graph = nullptr;
+    // the Chebyshev steps of a full and of a last round as graphs, captured
+    // on first use for the PanelDev of this context (its buffers stay fixed)
+    cudaGraphExec_t cheb_graph[2] = {nullptr, nullptr};
     InnerCtx() = default;
     InnerCtx(const InnerCtx&) = delete;
     InnerCtx& operator=(const InnerCtx&) = delete;
-    ~InnerCtx() { cheb_graph_destroy(cheb_graph); }
+    ~InnerCtx() {
+        cheb_graph_destroy(cheb_graph[0]);
+        cheb_graph_destroy(cheb_graph[1]);
+    }
 };
 
 // The Chebyshev plan of a solve's inner corrections (TB_MIXED with
@@ -528,7 +546,8 @@ tb_status inner_ctx_init(const View& v, const tb_solve_opts* o, InnerCtx& ic) {
     double lo = 0.0, hi = 0.0;
     const tb_status s = s_bounds(v.owner, lo, hi);
     if (s != TB_OK) return s;
-    ic.cheb = cheb_plan(lo, hi, o->inner_lo_tol, o->inner_max_iter);
+    ic.cheb = cheb_plan(lo, hi, o->inner_lo_tol, o->inner_tol, o->inner_max_iter);
+    if (ic.cheb.n > 0) ic.rounds = std::max(ic.cheb.R, 1);   // no host check before the planned last round
     return TB_OK;
 }
 
@@ -536,7 +555,7 @@ tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_ma
                       cudaStream_t st) {
     ic.res_exact = false;
     if (!p.mixed) return inner_cg(v, p, inner_max, ic.pred, ic.total, st);
-    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, &ic.cheb_graph, st);
+    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, ic.cheb_graph, st);
     if (s == TB_OK) ic.res_exact = b == p.Rcur;
     if (s != TB_ERR_BREAKDOWN && s != TB_ERR_NOT_CONVERGED) return s;
     ic.cheb.n = 0;   // the rest of this solve uses the FP32 CG corrections
