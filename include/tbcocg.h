@@ -257,9 +257,11 @@ tb_status tb_forces(tb_handle *h, const double *dE_dH, const double *dE_dS, cons
  *     dL/dS_ab = -(g_s/pi) Im sum_k w_k (v_b G_ba - z_k [G S D_v G]_ba),
  * D_v = diag(v), at every stored entry (the caller's block layout).  It needs
  * full-vector shifted solves with right-hand sides e_c and s_c (column c of
- * S) for every orbital c, contracted on the pattern:
- * [G S D_v G]_ba = sum_c v_c (G s_c)_b (G e_c)_a -- O(N K nnz) work, meant
- * for systems up to a few thousand orbitals.  Solves use opts; status as
+ * S) for every orbital c with v_c != 0, contracted on the pattern:
+ * [G S D_v G]_ba = sum_c v_c (G s_c)_b (G e_c)_a -- 2 m full-vector solves
+ * and O(m K nnz) work for m nonzero weights: cheap for a local L (a few
+ * atoms' charges) on any system size, O(N K nnz) for weights on every
+ * orbital.  Solves use opts; status as
  * tb_shifted_cocg; a batch handle of more than one system is
  * TB_ERR_INVALID_ARG.  dL_dH, dL_dS: double [n_values], host or device.
  */

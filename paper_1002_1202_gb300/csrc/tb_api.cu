@@ -1657,16 +1657,33 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
                     eb[e] = (int32_t)(ooff[J] + bj);
                 }
         }
+    // the columns c with v_c != 0: only they enter G S D_v G and v_b G_ba
+    std::vector<double> vh((size_t)N);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (is_device_ptr(v)) {
+        TB_CK(cudaMemcpyAsync(vh.data(), v, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        TB_CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(vh.data(), v, sizeof(double) * N);
+    }
+    std::vector<int32_t> supp;
+    for (int64_t o = 0; o < N; ++o) {
+        if (!std::isfinite(vh[o])) return TB_ERR_INVALID_ARG;
+        if (vh[o] != 0.0) supp.push_back((int32_t)o);
+    }
+    const int64_t ns = (int64_t)supp.size();
     // columns per chunk: the two full-solution panels X, Y ([K][Rc][N]) within ~2 GiB
     const int64_t per_col = 2 * (int64_t)K * N * (int64_t)sizeof(double2);
-    const int Rc = (int)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)2 * 1024 * 1024 * 1024 / per_col));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int Rc = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ns, 1),
+                                                                (int64_t)2 * 1024 * 1024 * 1024 / per_col));
     Cleanup cl;
     cl.st = st;
-    int32_t *ead, *ebd;
-    double *gH, *gS, *Sc;
+    int32_t *ead, *ebd, *cpos;
+    double *gH, *gS, *Sc, *vc;
     double2 *X, *Y, *zd, *wd;
     const double* vd = nullptr;
+    if ((s = dalloc(cl, &cpos, (size_t)N)) != TB_OK) return s;
+    if ((s = dalloc(cl, &vc, (size_t)Rc)) != TB_OK) return s;
     if ((s = dalloc(cl, &ead, (size_t)nvals)) != TB_OK) return s;
     if ((s = dalloc(cl, &ebd, (size_t)nvals)) != TB_OK) return s;
     if ((s = dalloc(cl, &gH, (size_t)nvals)) != TB_OK) return s;
@@ -1687,14 +1704,20 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
     tb_stats agg{};
     bool unconverged = false;
     std::vector<double> Sh((size_t)Rc * N);
-    std::vector<int32_t> cols(Rc);
-    for (int64_t c0 = 0; c0 < N; c0 += Rc) {
-        const int rc = (int)std::min<int64_t>(Rc, N - c0);
-        // columns s_c of S (= rows, S symmetric) in caller order
+    std::vector<int32_t> cols(Rc), cposh((size_t)N, -1);
+    std::vector<double> vch(Rc);
+    for (int64_t c0 = 0; c0 < ns; c0 += Rc) {
+        const int rc = (int)std::min<int64_t>(Rc, ns - c0);
+        // columns s_c of S (= rows, S symmetric) in caller order; the
+        // chunk position of every orbital that is one of its columns
         std::fill(Sh.begin(), Sh.end(), 0.0);
+        if (c0 > 0)
+            for (int64_t q = c0 - Rc; q < c0; ++q) cposh[supp[q]] = -1;
         for (int c = 0; c < rc; ++c) {
-            const int64_t o = c0 + c;
+            const int64_t o = supp[c0 + c];
             cols[c] = (int32_t)o;
+            cposh[o] = c;
+            vch[c] = vh[o];
             const int J = (int)(std::upper_bound(ooff.begin(), ooff.end(), o) - ooff.begin()) - 1;
             const int bj = (int)(o - ooff[J]);
             for (int64_t blk = h->brow_h[J]; blk < h->brow_h[J + 1]; ++blk) {
@@ -1705,6 +1728,8 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
             }
         }
         TB_CK(cudaMemcpyAsync(Sc, Sh.data(), sizeof(double) * (size_t)rc * N, cudaMemcpyHostToDevice, st));
+        TB_CK(cudaMemcpyAsync(cpos, cposh.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+        TB_CK(cudaMemcpyAsync(vc, vch.data(), sizeof(double) * rc, cudaMemcpyHostToDevice, st));
         for (int pass = 0; pass < 2; ++pass) {
             Solve q;
             q.K = K; q.z = z; q.R = rc; q.cols = cols.data(); q.proj = PROJ_NONE;
@@ -1721,8 +1746,9 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
             agg.unconverged += ts.unconverged;
             agg.inner_redos += ts.inner_redos;
         }
-        launch_vjp_accumulate(X, Y, K, rc, N, (int)c0, ead, ebd, nvals, vd, zd, wd, g_s, gH, gS, st);
+        launch_vjp_accumulate(X, Y, K, rc, N, cpos, vc, ead, ebd, nvals, vd, zd, wd, g_s, gH, gS, st);
         TB_CK(cudaGetLastError());
+        TB_CK(cudaStreamSynchronize(st));   // the host staging arrays are refilled for the next chunk
     }
     OutBuf oH, oS;
     if ((s = out_prepare(cl, oH, dL_dH, sizeof(double) * nvals)) != TB_OK) return s;

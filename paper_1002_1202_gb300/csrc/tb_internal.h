@@ -143,9 +143,9 @@ void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaSt
 void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_panel_rhs(const PanelDev& p, const double* rhs, const int32_t* orb2pad, int n_orb, int ncols,
                       cudaStream_t st);
-void launch_vjp_accumulate(const double2* X, const double2* Y, int K, int Rc, int64_t N, int c0,
-                           const int32_t* ea, const int32_t* eb, int64_t ne, const double* v, const double2* z,
-                           const double2* w, double g_s, double* gH, double* gS, cudaStream_t st);
+void launch_vjp_accumulate(const double2* X, const double2* Y, int K, int Rc, int64_t N, const int32_t* cpos,
+                           const double* vc, const int32_t* ea, const int32_t* eb, int64_t ne, const double* v,
+                           const double2* z, const double2* w, double g_s, double* gH, double* gS, cudaStream_t st);
 // sx_from_residual (mixed path): Rin holds r_n - S r'_n from the refinement
 void launch_outer_spmm(const DevSystem& s, const PanelDev& p, bool sx_from_residual, cudaStream_t st);
 void launch_outer_update(const DevSystem& s, const PanelDev& p, cudaStream_t st);

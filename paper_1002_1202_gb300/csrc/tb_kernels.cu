@@ -1933,25 +1933,29 @@ __global__ void k_panel_rhs(PanelDev p, const double* __restrict__ rhs, const in
 //   gH += -(g_s/pi) Im sum_k w_k Gamma_ba
 //   gS += -(g_s/pi) Im sum_k w_k (v_b G_ba - z_k Gamma_ba), G_ba = X[a]_b when a is in the chunk
 __global__ void k_vjp_accumulate(const double2* __restrict__ X, const double2* __restrict__ Y, int K, int Rc,
-                                 int64_t N, int c0, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
-                                 int64_t ne, const double* __restrict__ v, const double2* __restrict__ z,
+                                 int64_t N, const int32_t* __restrict__ cpos, const double* __restrict__ vc,
+                                 const int32_t* __restrict__ ea, const int32_t* __restrict__ eb, int64_t ne,
+                                 const double* __restrict__ v, const double2* __restrict__ z,
                                  const double2* __restrict__ w, double g_s, double* __restrict__ gH,
                                  double* __restrict__ gS) {
     const double f = -g_s / 3.14159265358979323846;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
         const int a = ea[e], b = eb[e];
+        // position of column b in this chunk (-1: not one of its columns);
+        // v_b G_ba = v_b (G e_b)_a, G being complex symmetric
+        const int pb = cpos[b];
         double ah = 0.0, as = 0.0;
         for (int k = 0; k < K; ++k) {
             double2 gam = cmk(0.0, 0.0);
             for (int c = 0; c < Rc; ++c) {
                 const size_t base = ((size_t)k * Rc + c) * N;
-                gam = cadd(gam, cmul(cmk(v[c0 + c], 0.0), cmul(Y[base + b], X[base + a])));
+                gam = cadd(gam, cmul(cmk(vc[c], 0.0), cmul(Y[base + b], X[base + a])));
             }
             ah += cmul(w[k], gam).y;
             as -= cmul(cmul(w[k], z[k]), gam).y;
-            if (a >= c0 && a < c0 + Rc) {
-                const double2 gba = X[((size_t)k * Rc + (a - c0)) * N + b];
-                as += v[b] * cmul(w[k], gba).y;
+            if (pb >= 0) {
+                const double2 gba = X[((size_t)k * Rc + pb) * N + a];
+                as += vc[pb] * cmul(w[k], gba).y;
             }
         }
         gH[e] += f * ah;
@@ -2497,11 +2501,11 @@ void launch_panel_rhs(const PanelDev& p, const double* rhs, const int32_t* orb2p
     k_panel_rhs<<<grid_for((long long)ncols * n_orb), THREADS, 0, st>>>(p, rhs, orb2pad, n_orb, ncols);
 }
 
-void launch_vjp_accumulate(const double2* X, const double2* Y, int K, int Rc, int64_t N, int c0,
-                           const int32_t* ea, const int32_t* eb, int64_t ne, const double* v, const double2* z,
-                           const double2* w, double g_s, double* gH, double* gS, cudaStream_t st) {
+void launch_vjp_accumulate(const double2* X, const double2* Y, int K, int Rc, int64_t N, const int32_t* cpos,
+                           const double* vc, const int32_t* ea, const int32_t* eb, int64_t ne, const double* v,
+                           const double2* z, const double2* w, double g_s, double* gH, double* gS, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
-    k_vjp_accumulate<<<grid_for(ne), THREADS, 0, st>>>(X, Y, K, Rc, N, c0, ea, eb, ne, v, z, w, g_s, gH, gS);
+    k_vjp_accumulate<<<grid_for(ne), THREADS, 0, st>>>(X, Y, K, Rc, N, cpos, vc, ea, eb, ne, v, z, w, g_s, gH, gS);
 }
 
 }  // namespace tb

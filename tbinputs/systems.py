@@ -200,6 +200,52 @@ def water_box(n_mol: int, density=1.0, seed=4, excess_proton=True,
     return species, pos, np.array([L, L, L]), (True, True, True)
 
 
+def si_cracked_slab(cells=(10, 10, 10), a=5.431, tip_frac=0.5, tip_width=2.0, opening_deg=10.0, sigma=0.1,
+                    seed=7) -> tuple:
+    """Si slab with a wedge-shaped crack (a stand-in for the paper's Si
+    fracture workload): the diamond lattice of ``cells`` cubic cells, periodic
+    only along y (the crack front), open along x and z.  The crack enters
+    from the x = 0 face at mid-height z_c and runs to the tip at
+    x_tip = tip_frac * L_x; an atom is removed when x < x_tip and
+    |z - z_c| < tip_width / 2 + (x_tip - x) tan(opening / 2), so the gap is
+    ``tip_width`` wide at the tip and opens by ``opening_deg`` towards the
+    mouth.  Then Gaussian displacements of ``sigma`` (Angstrom) per
+    coordinate.  Returns (species, positions, box, pbc, tip) with tip the
+    crack-tip point."""
+    base = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    frac = np.concatenate([base, base + 0.25])
+    nx, ny, nz = cells
+    grid = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"), -1).reshape(-1, 3)
+    pos = (grid[:, None, :] + frac[None, :, :]).reshape(-1, 3) * a
+    box = np.array([nx, ny, nz], dtype=np.float64) * a
+    x_tip = tip_frac * box[0]
+    z_c = 0.5 * box[2] - 0.125 * a          # between two atomic planes
+    half = 0.5 * tip_width + (x_tip - pos[:, 0]) * math.tan(math.radians(0.5 * opening_deg))
+    keep = ~((pos[:, 0] < x_tip) & (np.abs(pos[:, 2] - z_c) < half))
+    pos = pos[keep]
+    rng = np.random.default_rng(seed)
+    pos = pos + rng.normal(0.0, sigma, size=pos.shape)
+    tip = np.array([x_tip, 0.5 * box[1], z_c])
+    return [SI] * len(pos), pos, box, (False, True, False), tip
+
+
+def cut_out(system, center, n_atoms=64, cutoff=None) -> "TBSystem":
+    """The ``n_atoms`` atoms of ``system`` nearest to ``center`` (minimum
+    image along periodic axes) as an isolated cluster (no periodic axis),
+    rebuilt with the same species, cutoff and K."""
+    d = system.positions - np.asarray(center, dtype=np.float64)
+    for ax in range(3):
+        if system.pbc[ax]:
+            d[:, ax] -= system.box[ax] * np.round(d[:, ax] / system.box[ax])
+    idx = np.sort(np.argsort(np.einsum("ij,ij->i", d, d), kind="stable")[:n_atoms])
+    pos = np.asarray(center, dtype=np.float64) + d[idx]
+    sp = [system.species[i] for i in idx]
+    cut = cutoff if cutoff is not None else system.meta.get("cutoff", 4.0)
+    span = pos.max(0) - pos.min(0) + 2.0 * cut
+    return build_system(sp, pos, span, (False, False, False), cut, system.K,
+                        meta={"kind": "cut_out", "of": system.meta.get("kind"), "n_atoms": n_atoms, "cutoff": cut})
+
+
 def _pairs(pos, box, pbc, cutoff):
     big = np.where(pbc, box, (pos.max(0) - pos.min(0)) + 4.0 * cutoff + 1.0)
     shifted = pos - np.where(pbc, 0.0, pos.min(0) - 2.0 * cutoff)
@@ -331,6 +377,15 @@ def si_system(cells=(2, 2, 2), sigma=0.05, seed=1, cutoff=4.0, K=1.75) -> TBSyst
     return build_system(sp, pos, box, pbc, cutoff, K,
                         meta={"kind": "si_diamond", "cells": list(cells), "sigma": sigma, "seed": seed,
                               "cutoff": cutoff})
+
+
+def si_slab_system(cells=(10, 10, 10), sigma=0.1, seed=7, cutoff=4.0, K=1.75, **crack) -> TBSystem:
+    """The cracked Si slab of ``si_cracked_slab`` as a system; the crack tip
+    is in ``meta["tip"]``."""
+    sp, pos, box, pbc, tip = si_cracked_slab(cells, sigma=sigma, seed=seed, **crack)
+    return build_system(sp, pos, box, pbc, cutoff, K,
+                        meta={"kind": "si_cracked_slab", "cells": list(cells), "sigma": sigma, "seed": seed,
+                              "cutoff": cutoff, "tip": tip.tolist()})
 
 
 def water_system(n_mol=64, seed=4, cutoff=4.5, K=1.75, excess_proton=True) -> TBSystem:

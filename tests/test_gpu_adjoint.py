@@ -235,3 +235,119 @@ def test_mulliken_vjp_chunks_and_device_weights(P, si):
     mask = _dense_blocks(s, np.ones(len(s.S_vals))) > 0
     assert np.abs(_dense_blocks(s, gH)[mask] - gHd[mask]).max() <= 1e-7 * np.abs(gHd).max()
     assert np.abs(_dense_blocks(s, gS)[mask] - gSd[mask]).max() <= 1e-7 * np.abs(gSd).max()
+
+
+# ---------------------------------------------------------------------------
+# Si slab with a wedge crack (7680 atoms, N = 30720): the adjoint on a 64-atom
+# cut-out around the crack tip against the dense oracle, and the Mulliken VJP
+# of the full slab against central finite differences at 64 stored entries.
+# Broadening 1 eV (the workload gives the shift count, 128, not eta).
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def slab():
+    from tbinputs import si_slab_system
+    return si_slab_system()
+
+
+def _ased_block_values(s):
+    """H of Eq. Hap-1 in the block layout of S_vals (4x4 blocks only)."""
+    n, nb = s.n_atoms, s.nb
+    assert np.all(s.orb_per_atom == 4)
+    rows = np.repeat(np.arange(n), np.diff(s.brow_ptr))
+    Sb = s.S_vals.reshape(nb, 4, 4)
+    e = s.eps.reshape(n, 4)
+    Hb = 0.5 * s.K * (e[rows][:, :, None] + e[s.bcol][:, None, :]) * Sb
+    diag = rows == s.bcol
+    Hb[diag] = np.einsum("bi,ij->bij", e[rows[diag]], np.eye(4))
+    return Hb.reshape(-1)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_slab_cutout_adjoint_vs_dense(P, slab, prec):
+    from tbinputs import cut_out, gauss_legendre_grid
+    c = cut_out(slab, slab.meta["tip"], 64)
+    S = c.dense_S()
+    H = dense.ased_hamiltonian(S, c.eps, c.K, c.orbital_atom())
+    z, w = gauss_legendre_grid(128, -20.0, 5.0, 1.0)
+    h = P.tb_create_system(c)
+    opts = P.tb_default_opts(precision=prec)
+    E, gH, gS, st = P.tb_band_energy(h, z, w, opts=opts, n_values=len(c.S_vals))
+    assert abs(E - dense.band_energy(H, S, z, w)) <= 1e-8 * abs(E)
+    gHd, gSd = dense.band_energy_gradients(H, S, z, w)
+    mask = _dense_blocks(c, np.ones(len(c.S_vals))) > 0
+    assert np.abs(_dense_blocks(c, gH)[mask] - gHd[mask]).max() <= 1e-7 * np.abs(gHd).max()
+    assert np.abs(_dense_blocks(c, gS)[mask] - gSd[mask]).max() <= 1e-7 * np.abs(gSd).max()
+    # Mulliken VJP with weights on 8 orbitals (only their columns are solved)
+    rng = np.random.default_rng(11)
+    v = np.zeros(c.n_orb)
+    v[rng.choice(c.n_orb, 8, replace=False)] = rng.standard_normal(8)
+    vH, vS, _ = P.tb_mulliken_vjp(h, z, w, v, len(c.S_vals), opts=opts)
+    rH, rS = dense.mulliken_vjp(H, S, z, w, v)
+    assert np.abs(_dense_blocks(c, vH)[mask] - rH[mask]).max() <= 1e-7 * np.abs(rH).max()
+    assert np.abs(_dense_blocks(c, vS)[mask] - rS[mask]).max() <= 1e-7 * np.abs(rS).max()
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not __import__("os").environ.get("TB_SLAB_FD"),
+                    reason="128 full-slab solves; run with TB_SLAB_FD=1")
+def test_slab_mulliken_vjp_finite_differences(P, slab):
+    """L = sum_a v_a q_a with weights on 16 orbitals of the atoms nearest the
+    crack tip; dL/dH and dL/dS from the device VJP (mixed precision) at 32
+    stored H entries and 32 stored S entries of blocks within 6 A of the
+    tip, each against a central difference (h = 1e-5) of L recomputed on the
+    whole slab (FP64, outer tol 1e-12) with the entry and its transpose
+    perturbed together.  Error bound: the central difference's truncation
+    (O(h^2)) plus 2 eps / (2 h) for populations accurate to
+    eps = 1e-12 sum |v|; the test asserts 1e-5 of the largest gradient
+    plus that rounding term.  Every solve is capped at 5000 outer
+    iterations."""
+    from tbinputs import gauss_legendre_grid
+    s = slab
+    z, w = gauss_legendre_grid(128, -20.0, 5.0, 1.0)
+    tip = np.asarray(s.meta["tip"])
+    d = s.positions - tip
+    d[:, 1] -= s.box[1] * np.round(d[:, 1] / s.box[1])
+    near = np.argsort(np.einsum("ij,ij->i", d, d))
+    sup_atoms = near[:4]
+    sup = np.concatenate([4 * a + np.arange(4) for a in sup_atoms]).astype(np.int32)
+    rng = np.random.default_rng(5)
+    v = np.zeros(s.n_orb)
+    v[sup] = rng.standard_normal(len(sup))
+    Hv = _ased_block_values(s)
+    h0 = P.tb_create(s.orb_per_atom, s.brow_ptr, s.bcol, s.S_vals, Hv)
+    gH, gS, st = P.tb_mulliken_vjp(h0, z, w, v, len(s.S_vals), opts=P.tb_default_opts(precision=1, max_iter=5000))
+    assert st["status"] == "TB_OK"
+    cols = np.sort(sup)
+    fd_opts = P.tb_default_opts(precision=0, tol=1e-12, inner_tol=1e-13, max_iter=5000)
+
+    def L(Svals, Hvals):
+        hh = P.tb_create(s.orb_per_atom, s.brow_ptr, s.bcol, Svals, Hvals)
+        q, _ = P.tb_mulliken_orbital(hh, z, w, cols, 2.0, opts=fd_opts)
+        hh.close()
+        return float(np.dot(v[cols], q.cpu().numpy()))
+
+    # stored entries of blocks (I, J), I != J, with both atoms within 6 A of the tip
+    rows = np.repeat(np.arange(s.n_atoms), np.diff(s.brow_ptr))
+    r2 = np.einsum("ij,ij->i", d, d)
+    cand = np.nonzero((rows != s.bcol) & (r2[rows] < 36.0) & (r2[s.bcol] < 36.0))[0]
+    blocks = rng.choice(cand, 64, replace=False)
+    step = 1e-5
+    errs, scale = [], max(np.abs(gH).max(), np.abs(gS).max())
+    for k, b in enumerate(blocks):
+        i, j = rows[b], s.bcol[b]
+        t = int(np.nonzero((rows == j) & (s.bcol == i))[0][0])
+        ai, bj = rng.integers(0, 4, size=2)
+        e, et = 16 * b + 4 * ai + bj, 16 * t + 4 * bj + ai
+        which = "H" if k < 32 else "S"
+        D = np.zeros(len(s.S_vals))
+        D[e] += 1.0
+        D[et] += 1.0
+        if which == "H":
+            fd = (L(s.S_vals, Hv + step * D) - L(s.S_vals, Hv - step * D)) / (2 * step)
+            an = gH[e] + gH[et]
+        else:
+            fd = (L(s.S_vals + step * D, Hv) - L(s.S_vals - step * D, Hv)) / (2 * step)
+            an = gS[e] + gS[et]
+        errs.append((abs(fd - an), abs(an), which, fd, an))
+    worst = max(errs)
+    assert worst[0] <= 1e-5 * scale + 2e-12 * np.abs(v).sum() / (2 * step), worst

@@ -90,3 +90,26 @@ def test_si_counts():
 def test_water_counts():
     sy = water_system(64, seed=4, excess_proton=True)
     assert sy.n_atoms == 3 * 64 + 1 and sy.n_orb == 6 * 64 + 1
+
+
+def test_cracked_slab_geometry():
+    """The wedge-cracked Si slab: no atom centre (before displacement) inside
+    the wedge, the gap 2 A wide at the tip and opening by 10 degrees, open
+    along x and z, periodic along y; S symmetric and positive definite on a
+    64-atom cut-out around the tip."""
+    from tbinputs import si_cracked_slab, si_slab_system, cut_out
+    sp, pos, box, pbc, tip = si_cracked_slab((6, 4, 6), sigma=0.0, seed=1)
+    assert pbc == (False, True, False)
+    assert len(pos) < 8 * 6 * 4 * 6
+    x_tip, z_c = tip[0], tip[2]
+    half = 1.0 + (x_tip - pos[:, 0]) * math.tan(math.radians(5.0))
+    assert not np.any((pos[:, 0] < x_tip) & (np.abs(pos[:, 2] - z_c) < half))
+    # atoms do remain just beyond the tip and beside the gap
+    assert np.any((pos[:, 0] > x_tip) & (np.abs(pos[:, 2] - z_c) < 1.0))
+    s = si_slab_system((6, 4, 6), seed=1)
+    assert s.n_orb == 4 * s.n_atoms
+    c = cut_out(s, s.meta["tip"], 64)
+    assert c.n_atoms == 64 and c.pbc == (False, False, False)
+    S = c.dense_S()
+    assert np.allclose(S, S.T, atol=1e-14)
+    assert np.linalg.eigvalsh(S)[0] > 0.0
