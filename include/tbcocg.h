@@ -121,6 +121,27 @@ tb_status tb_batch_offsets(const tb_handle *h, int64_t *atom_off, int64_t *orb_o
  */
 tb_status tb_overlap_bounds(tb_handle *h, double *lo, double *hi);
 
+/*
+ * The same bounds for a system description, on the host only (no device,
+ * no handle): d as for tb_create (S_vals used, assumed symmetric; H_vals,
+ * eps and K ignored).  TB_ERR_INVALID_ARG for a malformed pattern.
+ */
+tb_status tb_overlap_bounds_desc(const tb_system_desc *d, double *lo, double *hi);
+
+/*
+ * Chebyshev plan of the TB_MIXED corrections for spectrum bounds [lo, hi]
+ * (host only): n (odd) steps per round reduce the error by at least
+ * 1 / T_n(1 / sigma) <= lo_tol, sigma = (hi - lo) / (hi + lo); rounds =
+ * ceil(log inner_tol / log lo_tol) rounds are planned, the last of n_last
+ * <= n steps (enough for half the remaining reduction); gamma = 2 / (lo + hi);
+ * omega[k] (1 <= k < n; omega[0] = 0) the step coefficients of the
+ * recurrence d_{k+1} = d_{k-1} + omega[k] (gamma (f - S d_k) + d_k - d_{k-1}),
+ * d_0 = 0, d_1 = gamma f.  omega: float [omega_len] or NULL.  *n = 0 when
+ * lo <= 0, hi <= lo or n > cap (the FP32 CG corrections are used then).
+ */
+tb_status tb_chebyshev_plan(double lo, double hi, double lo_tol, double inner_tol, int32_t cap, int32_t *n,
+                            int32_t *n_last, int32_t *rounds, double *gamma, float *omega, int32_t omega_len);
+
 /* Release all device memory of the handle (NULL is allowed). */
 tb_status tb_destroy(tb_handle *h);
 

@@ -8,7 +8,8 @@ functions carry the names of the C entry points.
 from .tb import (  # noqa: F401
     Handle, TBError, SolveOpts, load_library, library_path,
     tb_create, tb_create_system, tb_create_batch, tb_default_opts, tb_shifted_cocg, tb_green_elements,
-    tb_green_elements_dz, tb_band_energy, tb_forces, tb_mulliken_vjp, tb_overlap_bounds,
+    tb_green_elements_dz, tb_band_energy, tb_forces, tb_mulliken_vjp, tb_overlap_bounds, tb_overlap_bounds_desc,
+    tb_chebyshev_plan,
     tb_mulliken_orbital, tb_mulliken_charges, tb_generalized_lanczos, tb_generalized_lanczos_noalloc,
     tb_generalized_lanczos_batch, tb_lanczos_green_batch,
     tb_default_csc_opts, tb_csc_hamiltonian, tb_csc_loop, CscOpts, tb_lanczos_green,

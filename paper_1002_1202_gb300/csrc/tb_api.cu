@@ -229,19 +229,22 @@ static double tri_last_component(const std::vector<double>& a, const std::vector
     return std::fabs(y[m - 1]);
 }
 
-static void compute_s_bounds(tb_handle* h) {
-    const int n = h->n_atoms;
-    const int64_t N = h->n_orb;
+// Bounds of the spectrum of a block-sparse symmetric S (caller layout:
+// atom block rows brow, block columns bcol, block value offsets boff,
+// row-major blocks) by the Lanczos run above.
+static tb_status lanczos_bounds(int n, const int32_t* opa, const int64_t* brow, const int32_t* bcol,
+                                const int64_t* boff, const double* S, double& lo_out, double& hi_out) {
     std::vector<int64_t> ooff(n + 1, 0);
-    for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + h->orb_per_atom[i];
+    for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + opa[i];
+    const int64_t N = ooff[n];
     auto smul = [&](const std::vector<double>& x, std::vector<double>& y) {
         for (int I = 0; I < n; ++I) {
-            const int ni = h->orb_per_atom[I];
+            const int ni = opa[I];
             double acc[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int64_t blk = h->brow_h[I]; blk < h->brow_h[I + 1]; ++blk) {
-                const int J = h->bcol_h[blk];
-                const int nj = h->orb_per_atom[J];
-                const double* sb = h->S_h.data() + h->boff_h[blk];
+            for (int64_t blk = brow[I]; blk < brow[I + 1]; ++blk) {
+                const int J = bcol[blk];
+                const int nj = opa[J];
+                const double* sb = S + boff[blk];
                 for (int a = 0; a < ni; ++a)
                     for (int bj = 0; bj < nj; ++bj) acc[a] += sb[a * nj + bj] * x[ooff[J] + bj];
             }
@@ -282,17 +285,21 @@ static void compute_s_bounds(tb_handle* h) {
         }
     }
     const int m = (int)al.size();
-    std::vector<double> boff(be.begin(), be.end() - 1);
-    const double tmin = tri_eig(al, boff, 0), tmax = tri_eig(al, boff, m - 1);
+    std::vector<double> boffd(be.begin(), be.end() - 1);
+    const double tmin = tri_eig(al, boffd, 0), tmax = tri_eig(al, boffd, m - 1);
     const double bm = be.back();
-    const double rmin = bm * tri_last_component(al, boff, tmin);
-    const double rmax = bm * tri_last_component(al, boff, tmax);
-    if (!(tmin > 0.0) || !std::isfinite(tmax)) {
-        h->s_status = std::isfinite(tmin) ? TB_ERR_S_NOT_SPD : TB_ERR_INVALID_ARG;
-        return;
-    }
-    h->s_lo = 0.97 * (tmin - rmin);     // <= 0: no usable lower bound, the FP32 CG is used
-    h->s_hi = 1.01 * (tmax + rmax);
+    const double rmin = bm * tri_last_component(al, boffd, tmin);
+    const double rmax = bm * tri_last_component(al, boffd, tmax);
+    if (!std::isfinite(tmin) || !std::isfinite(tmax)) return TB_ERR_INVALID_ARG;
+    if (!(tmin > 0.0)) return TB_ERR_S_NOT_SPD;
+    lo_out = 0.97 * (tmin - rmin);     // <= 0: no usable lower bound, the FP32 CG is used
+    hi_out = 1.01 * (tmax + rmax);
+    return TB_OK;
+}
+
+static void compute_s_bounds(tb_handle* h) {
+    h->s_status = lanczos_bounds(h->n_atoms, h->orb_per_atom.data(), h->brow_h.data(), h->bcol_h.data(),
+                                 h->boff_h.data(), h->S_h.data(), h->s_lo, h->s_hi);
 }
 
 tb_status s_bounds(tb_handle* h, double& lo, double& hi) {
@@ -1525,6 +1532,40 @@ tb_status tb_create_batch(tb_handle** out, const tb_system_desc* descs, int32_t 
         v.grpG = 0;                 // the grouped SpMV's atom groups are built for the whole handle
         h->sys_ds.push_back(v);
     }
+    return TB_OK;
+}
+
+tb_status tb_overlap_bounds_desc(const tb_system_desc* d, double* lo, double* hi) {
+    if (!d || !lo || !hi || d->n_atoms < 1 || !d->orb_per_atom || !d->brow_ptr || !d->bcol || !d->S_vals)
+        return TB_ERR_INVALID_ARG;
+    const int n = d->n_atoms;
+    if (d->brow_ptr[0] != 0) return TB_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (d->orb_per_atom[i] != 1 && d->orb_per_atom[i] != 4) return TB_ERR_INVALID_ARG;
+        if (d->brow_ptr[i + 1] < d->brow_ptr[i]) return TB_ERR_INVALID_ARG;
+    }
+    const int64_t nb = d->brow_ptr[n];
+    std::vector<int64_t> boff(nb + 1, 0);
+    for (int i = 0; i < n; ++i)
+        for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
+            const int j = d->bcol[b];
+            if (j < 0 || j >= n) return TB_ERR_INVALID_ARG;
+            boff[b + 1] = boff[b] + (int64_t)d->orb_per_atom[i] * d->orb_per_atom[j];
+        }
+    return lanczos_bounds(n, d->orb_per_atom, d->brow_ptr, d->bcol, boff.data(), d->S_vals, *lo, *hi);
+}
+
+tb_status tb_chebyshev_plan(double lo, double hi, double lo_tol, double inner_tol, int32_t cap, int32_t* n,
+                            int32_t* n_last, int32_t* rounds, double* gamma, float* omega, int32_t omega_len) {
+    if (!n || !n_last || !rounds || !gamma || !(lo_tol > 0.0 && lo_tol < 1.0) || !(inner_tol > 0.0) || cap < 1)
+        return TB_ERR_INVALID_ARG;
+    const ChebPlan cp = cheb_plan(lo, hi, lo_tol, inner_tol, cap);
+    *n = cp.n;
+    *n_last = cp.n_last;
+    *rounds = cp.R;
+    *gamma = cp.gamma;
+    if (omega)
+        for (int k = 0; k < omega_len; ++k) omega[k] = k < cp.n ? cp.omega[k] : 0.f;
     return TB_OK;
 }
 

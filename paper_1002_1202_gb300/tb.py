@@ -124,6 +124,10 @@ SIGNATURES = [
                                  C.POINTER(Stats), _VP]),
     ("tb_forces", C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("tb_overlap_bounds", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("tb_overlap_bounds_desc", C.c_int, [C.POINTER(SystemDesc), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("tb_chebyshev_plan", C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_float), C.c_int32]),
     ("tb_mulliken_vjp", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, C.POINTER(SolveOpts), _VP, _VP,
                                   C.POINTER(Stats), _VP]),
     ("tb_mulliken_orbital", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.c_int32, _I32P,
@@ -409,6 +413,42 @@ def tb_overlap_bounds(h: Handle):
     lo, hi = C.c_double(), C.c_double()
     _check(load_library().tb_overlap_bounds(h.ptr, C.byref(lo), C.byref(hi)), "tb_overlap_bounds", False)
     return lo.value, hi.value
+
+
+def tb_overlap_bounds_desc(system):
+    """(lo, hi) of ``tb_overlap_bounds`` for a ``tbinputs.TBSystem`` (or any
+    object with orb_per_atom, brow_ptr, bcol, S_vals), on the host only."""
+    arrs = [np.ascontiguousarray(system.orb_per_atom, dtype=np.int32),
+            np.ascontiguousarray(system.brow_ptr, dtype=np.int64),
+            np.ascontiguousarray(system.bcol, dtype=np.int32),
+            np.ascontiguousarray(system.S_vals, dtype=np.float64)]
+    d = SystemDesc()
+    d.n_atoms = len(arrs[0])
+    d.orb_per_atom = _ptr(arrs[0], C.c_int32)
+    d.brow_ptr = _ptr(arrs[1], C.c_int64)
+    d.bcol = _ptr(arrs[2], C.c_int32)
+    d.S_vals = _ptr(arrs[3], C.c_double)
+    d.H_vals = None
+    d.eps = None
+    d.K = 0.0
+    d.precision = TB_FP64
+    lo, hi = C.c_double(), C.c_double()
+    _check(load_library().tb_overlap_bounds_desc(C.byref(d), C.byref(lo), C.byref(hi)), "tb_overlap_bounds_desc",
+           False)
+    return lo.value, hi.value
+
+
+def tb_chebyshev_plan(lo, hi, lo_tol=1e-6, inner_tol=1e-13, cap=1000):
+    """dict(n, n_last, rounds, gamma, omega) of the mixed path's Chebyshev
+    corrections for spectrum bounds [lo, hi] (host only)."""
+    n, nl, r = C.c_int32(), C.c_int32(), C.c_int32()
+    g = C.c_double()
+    om = np.zeros(max(1, int(cap)), dtype=np.float32)
+    _check(load_library().tb_chebyshev_plan(float(lo), float(hi), float(lo_tol), float(inner_tol), int(cap),
+                                            C.byref(n), C.byref(nl), C.byref(r), C.byref(g),
+                                            om.ctypes.data_as(C.POINTER(C.c_float)), len(om)),
+           "tb_chebyshev_plan", False)
+    return {"n": n.value, "n_last": nl.value, "rounds": r.value, "gamma": g.value, "omega": om[:n.value].copy()}
 
 
 def tb_mulliken_vjp(h: Handle, z, w, v, n_values: int, g_s=2.0, opts: SolveOpts | None = None, stream=None,
