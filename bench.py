@@ -4,10 +4,12 @@ Workload: Si diamond supercell of 4096 atoms (8x8x8 conventional cells,
 a = 5.431 A, Gaussian displacements 0.05 A, seed 3), sp3 STO basis
 (N = 16384 orbitals, ~17 4x4 blocks per block row), H by the ASED rule
 (K = 1.75), 256 shifts z_k = E_k + 0.01i eV with E_k the Gauss-Legendre
-nodes on [-20, 5] eV, Mulliken projection (a7).  One step = one panel of
-P right-hand sides e_j run through ``iters`` outer iterations of the whole
-hot path (seed SpMM, inner CG for S^-1, shift updates, seed switching,
-charge accumulation), started from r_0 = e_j.  The full solve of this
+nodes on [-20, 5] eV, Mulliken projection (a7).  One step = four panels
+of P right-hand sides e_j (in flight together) run through ``iters`` outer
+iterations of the whole hot path (seed SpMM, inner solve for S^-1 -- FP32
+Chebyshev corrections inside FP64 refinement on the default mixed path --,
+shift updates, seed switching, charge accumulation), started from
+r_0 = e_j.  The full solve of this
 workload needs ~10^4-10^5 outer iterations per column, so a step is a
 fixed chunk of it; the metric is the rate shift*RHS*iterations/s.
 

@@ -13,7 +13,8 @@
  * matrix of Section 2.2; both are real symmetric, S positive definite.
  * The solver is the generalized shifted COCG method of Section 3.3: one seed
  * system (Eq. shift-E) iterated by Eqs. (CGp:p), (CGp:x), (CGp:r) with
- * r' = S^-1 r from an inner CG, every other shift carried by the scalar
+ * r' = S^-1 r from an inner solve (CG in FP64; with TB_MIXED, FP64
+ * iterative refinement with FP32 corrections), every other shift carried by the scalar
  * recurrence Eq. (shift:pi) through the collinear residuals of
  * Eq. (collinear), and seed switching.  The generalized Lanczos process of
  * Section 3.2 (Eqs. 1.13, 1.18) is exported as well.
@@ -162,11 +163,11 @@ typedef struct {
     int32_t switching;        /* 1 = seed switching (default), 0 = keep the seed       */
     int32_t force_switch_every; /* > 0: also switch every that many steps (testing)    */
     int32_t precision;        /* TB_FP64 (default): every product in FP64;
-                                 TB_MIXED: the inner solve S r' = r runs as FP32 CG
-                                 corrections inside FP64 iterative refinement
+                                 TB_MIXED: the inner solve S r' = r runs as FP32
+                                 corrections (inner_method) inside FP64 iterative refinement
                                  (residual r - S r' in FP64 each round) until
                                  ||r - S r'|| <= inner_tol ||r||; all other steps FP64 */
-    double inner_lo_tol;      /* TB_MIXED: relative tolerance of each FP32 CG round;
+    double inner_lo_tol;      /* TB_MIXED: relative tolerance of each FP32 correction round;
                                  default 1e-6                                            */
     int32_t inner_method;     /* TB_MIXED: how the FP32 corrections of a round are made.
                                  TB_INNER_CHEBYSHEV (default): a fixed number of

@@ -403,9 +403,7 @@ tb_status inner_cg32(View& v, const PanelDev& p, int inner_max, int& pred, int64
     }
 }
 
-// r' = S^-1 b by FP32 CG corrections inside FP64 iterative refinement
-// (TB_MIXED).  The expected number of rounds is carried between calls so
-// that the common case costs one host synchronisation per round.
+// TB_DEBUG=1: the refinement state of the first real columns after a failed round
 void debug_inner32(View& v, const PanelDev& p, int round, cudaStream_t st) {
     if (!std::getenv("TB_DEBUG")) return;
     std::vector<InnerState> is(2 * p.P);
@@ -1722,7 +1720,6 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
     int32_t *ead, *ebd, *cpos;
     double *gH, *gS, *Sc, *vc;
     double2 *X, *Y, *zd, *wd;
-    const double* vd = nullptr;
     if ((s = dalloc(cl, &cpos, (size_t)N)) != TB_OK) return s;
     if ((s = dalloc(cl, &vc, (size_t)Rc)) != TB_OK) return s;
     if ((s = dalloc(cl, &ead, (size_t)nvals)) != TB_OK) return s;
@@ -1734,7 +1731,6 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
     if ((s = dalloc(cl, &Y, (size_t)K * Rc * N)) != TB_OK) return s;
     if ((s = dalloc(cl, &zd, (size_t)K)) != TB_OK) return s;
     if ((s = dalloc(cl, &wd, (size_t)K)) != TB_OK) return s;
-    if ((s = device_view(cl, v, (size_t)N, &vd, st)) != TB_OK) return s;
     TB_CK(cudaMemcpyAsync(ead, ea.data(), sizeof(int32_t) * nvals, cudaMemcpyHostToDevice, st));
     TB_CK(cudaMemcpyAsync(ebd, eb.data(), sizeof(int32_t) * nvals, cudaMemcpyHostToDevice, st));
     TB_CK(cudaMemcpyAsync(zd, z, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
@@ -1787,7 +1783,7 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
             agg.unconverged += ts.unconverged;
             agg.inner_redos += ts.inner_redos;
         }
-        launch_vjp_accumulate(X, Y, K, rc, N, cpos, vc, ead, ebd, nvals, vd, zd, wd, g_s, gH, gS, st);
+        launch_vjp_accumulate(X, Y, K, rc, N, cpos, vc, ead, ebd, nvals, zd, wd, g_s, gH, gS, st);
         TB_CK(cudaGetLastError());
         TB_CK(cudaStreamSynchronize(st));   // the host staging arrays are refilled for the next chunk
     }

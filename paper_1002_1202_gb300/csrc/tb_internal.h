@@ -88,7 +88,7 @@ struct InnerState {
 struct PanelDev {
     int P = 0, K = 0, npad = 0, M = 0, proj = PROJ_NONE;
     int grid = 0;                 // CTAs of the grid-stride kernels
-    int mixed = 0;                // 1: inner S^-1 by FP32 CG inside FP64 refinement
+    int mixed = 0;                // 1: inner S^-1 by FP32 corrections inside FP64 refinement
     double tol = 1e-10, inner_tol = 1e-13, inner_lo_tol = 1e-6;
     int switching = 1, force_switch_every = 0;
     // panel vectors, [npad][P] complex
@@ -144,7 +144,7 @@ void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_panel_rhs(const PanelDev& p, const double* rhs, const int32_t* orb2pad, int n_orb, int ncols,
                       cudaStream_t st);
 void launch_vjp_accumulate(const double2* X, const double2* Y, int K, int Rc, int64_t N, const int32_t* cpos,
-                           const double* vc, const int32_t* ea, const int32_t* eb, int64_t ne, const double* v,
+                           const double* vc, const int32_t* ea, const int32_t* eb, int64_t ne,
                            const double2* z, const double2* w, double g_s, double* gH, double* gS, cudaStream_t st);
 // sx_from_residual (mixed path): Rin holds r_n - S r'_n from the refinement
 void launch_outer_spmm(const DevSystem& s, const PanelDev& p, bool sx_from_residual, cudaStream_t st);

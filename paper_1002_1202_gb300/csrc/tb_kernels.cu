@@ -461,11 +461,12 @@ __global__ void k_inner_update(PanelDev p, int it) {
 // ---------------------------------------------------------------------------
 // Mixed-precision inner solve (TB_MIXED): r' = S^-1 b by iterative
 // refinement.  x_0 = 0; round m computes res_m = b - S x_m in FP64, scales
-// it to unit norm, solves S d = res_m / ||res_m|| by CG in FP32 to relative
-// inner_lo_tol, and sets x_{m+1} = x_m + ||res_m|| d in FP64, until
-// ||res_m|| <= inner_tol ||b|| per real column.  The unit scaling keeps the
-// FP32 values away from underflow however small b or the residual are.
-// The FP32 CG reuses the Chronopoulos-Gear form of the FP64 one.
+// it to unit norm, solves S d = res_m / ||res_m|| in FP32 to relative
+// inner_lo_tol (Chebyshev steps, k_inner32_cheb below, or CG), and sets
+// x_{m+1} = x_m + ||res_m|| d in FP64, until ||res_m|| <= inner_tol ||b||
+// per real column.  The unit scaling keeps the FP32 values away from
+// underflow however small b or the residual are.  The FP32 CG reuses the
+// Chronopoulos-Gear form of the FP64 one.
 // ---------------------------------------------------------------------------
 __device__ void refine_finish_counts(PanelDev& p, int nact) {
     __shared__ int s_cnt;
@@ -1935,7 +1936,7 @@ __global__ void k_panel_rhs(PanelDev p, const double* __restrict__ rhs, const in
 __global__ void k_vjp_accumulate(const double2* __restrict__ X, const double2* __restrict__ Y, int K, int Rc,
                                  int64_t N, const int32_t* __restrict__ cpos, const double* __restrict__ vc,
                                  const int32_t* __restrict__ ea, const int32_t* __restrict__ eb, int64_t ne,
-                                 const double* __restrict__ v, const double2* __restrict__ z,
+                                 const double2* __restrict__ z,
                                  const double2* __restrict__ w, double g_s, double* __restrict__ gH,
                                  double* __restrict__ gS) {
     const double f = -g_s / 3.14159265358979323846;
@@ -2502,10 +2503,10 @@ void launch_panel_rhs(const PanelDev& p, const double* rhs, const int32_t* orb2p
 }
 
 void launch_vjp_accumulate(const double2* X, const double2* Y, int K, int Rc, int64_t N, const int32_t* cpos,
-                           const double* vc, const int32_t* ea, const int32_t* eb, int64_t ne, const double* v,
+                           const double* vc, const int32_t* ea, const int32_t* eb, int64_t ne,
                            const double2* z, const double2* w, double g_s, double* gH, double* gS, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
-    k_vjp_accumulate<<<grid_for(ne), THREADS, 0, st>>>(X, Y, K, Rc, N, cpos, vc, ea, eb, ne, v, z, w, g_s, gH, gS);
+    k_vjp_accumulate<<<grid_for(ne), THREADS, 0, st>>>(X, Y, K, Rc, N, cpos, vc, ea, eb, ne, z, w, g_s, gH, gS);
 }
 
 }  // namespace tb
