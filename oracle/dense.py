@@ -188,7 +188,9 @@ def jacobi_eigvals(A: np.ndarray, tol: float = 1e-14, max_sweeps: int = 60) -> n
     n = A.shape[0]
     scale = np.linalg.norm(A)
     for _ in range(max_sweeps):
-        off = math.sqrt(max(0.0, np.sum(A * A) - np.sum(np.diag(A) ** 2)))
+        # off-diagonal norm summed directly (the difference ||A||^2 - sum diag^2
+        # cancels and cannot fall below ~sqrt(eps) ||A||)
+        off = math.sqrt(float(np.sum(A * A, where=~np.eye(n, dtype=bool))))
         if off <= tol * scale:
             break
         for p in range(n - 1):

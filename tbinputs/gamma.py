@@ -37,3 +37,26 @@ def klopman_ohno_gamma(system, hardness=None) -> np.ndarray:
 def valence_populations(system) -> np.ndarray:
     """Neutral-atom valence electron counts q_ref (Si 4, O 6, H 1)."""
     return np.array([float(sp.z_val) for sp in system.species])
+
+
+def klopman_ohno_gamma_gradient(system, hardness=None) -> np.ndarray:
+    """d gamma_ik / d R_i of ``klopman_ohno_gamma`` as an (n_atoms, n_atoms, 3)
+    array: -e^2 (R_i - R_k) / (R_ik^2 + (e^2 / U_ik)^2)^(3/2), minimum image
+    along periodic axes, zero on the diagonal (gamma_ii = U_i is constant).
+    d gamma_ik / d R_k is its negative."""
+    hard = HARDNESS_EV if hardness is None else hardness
+    U = np.array([hard[sp.name] for sp in system.species])
+    pos = np.asarray(system.positions, dtype=np.float64)
+    d = pos[:, None, :] - pos[None, :, :]
+    box = np.asarray(system.box, dtype=np.float64)
+    pbc = np.asarray(system.pbc, dtype=bool)
+    for ax in range(3):
+        if pbc[ax]:
+            d[..., ax] -= box[ax] * np.round(d[..., ax] / box[ax])
+    r2 = np.sum(d * d, axis=-1)
+    Uik = 0.5 * (U[:, None] + U[None, :])
+    den = (r2 + (COULOMB_EV_ANGSTROM / Uik) ** 2) ** 1.5
+    g = -COULOMB_EV_ANGSTROM * d / den[..., None]
+    idx = np.arange(len(U))
+    g[idx, idx, :] = 0.0
+    return g

@@ -113,3 +113,16 @@ def test_cracked_slab_geometry():
     S = c.dense_S()
     assert np.allclose(S, S.T, atol=1e-14)
     assert np.linalg.eigvalsh(S)[0] > 0.0
+
+
+def test_klopman_ohno_gradient_matches_differences():
+    from tbinputs import klopman_ohno_gamma, klopman_ohno_gamma_gradient, displaced
+    s = water_system(8, seed=4, cutoff=3.0, excess_proton=False)
+    g = klopman_ohno_gamma_gradient(s)
+    h = 1e-5
+    for atom, ax in ((0, 0), (5, 2)):
+        fd = (klopman_ohno_gamma(displaced(s, atom, ax, h)) - klopman_ohno_gamma(displaced(s, atom, ax, -h))) / (2 * h)
+        assert np.abs(fd[atom] - g[atom, :, ax]).max() <= 1e-7 * np.abs(g).max()
+        assert np.abs(fd[:, atom] - g[atom, :, ax]).max() <= 1e-7 * np.abs(g).max()   # symmetric gamma
+        others = np.arange(s.n_atoms) != atom
+        assert np.abs(fd[np.ix_(others, others)]).max() == 0.0

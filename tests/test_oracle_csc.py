@@ -128,3 +128,106 @@ def test_water_loop_reaches_a_fixed_point(water8):
     assert np.abs((q - q_ref) - out["dq"]).max() <= 1e-8
     # self-consistency changed the charges: the first iteration was far from it
     assert out["history"][0] > 1e-2
+
+
+# ---------------------------------------------------------------------------
+# forces of the charge-self-consistent model (contour grand potential Omega,
+# free energy A(dq) = Omega(H0 + H^CSC(dq)) - V^T q_in + 1/2 dq^T gamma dq)
+# ---------------------------------------------------------------------------
+def test_grand_potential_gradients_match_differences(water8):
+    s, S, oa, H0 = water8
+    z, w = gauss_legendre_grid(64, -60.0, -8.0, 2.0)
+    gH, gS = csc.grand_potential_gradients(H0, S, z, w)
+    rng = np.random.default_rng(12)
+    N = S.shape[0]
+    mask = (np.abs(S) > 0).astype(float)
+    for grad, which in ((gH, "H"), (gS, "S")):
+        A = rng.standard_normal((N, N)) * mask
+        D = 0.5 * (A + A.T)
+        h = 1e-6
+        if which == "H":
+            fd = (csc.grand_potential(H0 + h * D, S, z, w) - csc.grand_potential(H0 - h * D, S, z, w)) / (2 * h)
+        else:
+            fd = (csc.grand_potential(H0, S + h * D, z, w) - csc.grand_potential(H0, S - h * D, z, w)) / (2 * h)
+        assert abs(fd - float(np.sum(grad * D))) <= 1e-6 * max(1.0, abs(fd)), which
+    # dOmega/dH is the density matrix itself (not the band-energy gradient)
+    assert np.abs(gH - dense.density_matrix(H0, S, z, w).T).max() <= 1e-12
+
+
+def test_grand_potential_sum_rule(water8):
+    """d/dc Omega(H0 + c S) = Tr(rho S), the electron count, against the
+    eigenvalue closed form of the sum rule."""
+    s, S, oa, H0 = water8
+    z, w = gauss_legendre_grid(64, -60.0, -8.0, 2.0)
+    h = 1e-5
+    fd = (csc.grand_potential(H0 + h * S, S, z, w) - csc.grand_potential(H0 - h * S, S, z, w)) / (2 * h)
+    ne = dense.electron_count_closed_form(dense.generalized_eigvals(H0, S), z, w)
+    assert abs(fd - ne) <= 1e-7 * ne
+
+
+@pytest.fixture(scope="module")
+def scc8(water8):
+    s, S, oa, H0 = water8
+    gamma = 0.25 * klopman_ohno_gamma(s)
+    q_ref = valence_populations(s)
+    z, w = gauss_legendre_grid(64, -60.0, -8.0, 2.0)
+    out = csc.csc_loop(H0, S, oa, s.n_atoms, gamma, q_ref, z, w, mix=0.5, tol=1e-12, max_iter=300)
+    assert out["converged"]
+    return gamma, q_ref, z, w, out["dq"]
+
+
+def test_scc_free_energy_is_stationary_at_self_consistency(water8, scc8):
+    s, S, oa, H0 = water8
+    gamma, q_ref, z, w, dq = scc8
+    rng = np.random.default_rng(3)
+    h = 1e-4
+
+    def A(x):
+        return csc.scc_free_energy(H0, S, oa, gamma, q_ref, x, z, w)
+
+    # away from self-consistency dA/d dq = gamma (q_out - q_in) ...
+    dq0 = np.zeros(s.n_atoms)
+    q_out = dense.mulliken_atom(dense.mulliken_orbital(H0, S, z, w), oa, s.n_atoms)
+    grad0 = gamma @ (q_out - (dq0 + q_ref))
+    for _ in range(2):
+        u = rng.standard_normal(s.n_atoms)
+        fd = (A(dq0 + h * u) - A(dq0 - h * u)) / (2 * h)
+        assert abs(fd - grad0 @ u) <= 1e-6 * max(1.0, abs(grad0 @ u))
+    assert np.abs(grad0).max() > 1e-2
+    # ... and it vanishes at the self-consistent dq
+    for _ in range(2):
+        u = rng.standard_normal(s.n_atoms)
+        fd = (A(dq + h * u) - A(dq - h * u)) / (2 * h)
+        assert abs(fd) <= 1e-7 * np.abs(grad0).max()
+
+
+def test_scc_forces_match_differences(water8, scc8):
+    """F = -dA/dR at self-consistency against central differences of A with
+    the charges made self-consistent again at each displaced geometry (S,
+    Eq. Hap-1 H0 and gamma rebuilt), zero net force, and a force without the
+    Coulomb-gradient term failing."""
+    from tbinputs import overlap_bond_derivatives, displaced, klopman_ohno_gamma_gradient
+    s, S, oa, H0 = water8
+    gamma, q_ref, z, w, dq = scc8
+    dS = overlap_bond_derivatives(s)
+    dg = 0.25 * klopman_ohno_gamma_gradient(s)
+    F = csc.scc_forces(H0, S, oa, gamma, dg, q_ref, dq, z, w, dS, s.orb_per_atom, s.brow_ptr, s.bcol, s.eps, s.K)
+    scale = np.abs(F).max()
+    assert np.abs(F.sum(axis=0)).max() <= 1e-8 * scale
+    h = 1e-4
+    for atom, ax in ((2, 0), (9, 1)):
+        As = []
+        for sgn in (1, -1):
+            sd = displaced(s, atom, ax, sgn * h)
+            Sd = sd.dense_S()
+            H0d = dense.ased_hamiltonian(Sd, sd.eps, sd.K, oa)
+            gd = 0.25 * klopman_ohno_gamma(sd)
+            out = csc.csc_loop(H0d, Sd, oa, s.n_atoms, gd, q_ref, z, w, mix=0.5, tol=1e-12, max_iter=300,
+                               dq_init=dq)
+            assert out["converged"]
+            As.append(csc.scc_free_energy(H0d, Sd, oa, gd, q_ref, out["dq"], z, w))
+        fd = -(As[0] - As[1]) / (2 * h)
+        assert abs(F[atom, ax] - fd) <= 1e-5 * scale, (atom, ax, F[atom, ax], fd)
+        F0 = csc.scc_forces(H0, S, oa, gamma, np.zeros_like(dg), q_ref, dq, z, w, dS, s.orb_per_atom, s.brow_ptr,
+                            s.bcol, s.eps, s.K)
+        assert abs(F0[atom, ax] - fd) > 1e-4 * scale
