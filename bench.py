@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the band-energy gradient measurement")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the batched Lanczos measurement")
+    ap.add_argument("--large", action="store_true",
+                    help="instead of the benchmark step: the 100 000-atom Si system (25x25x20 cells), Chebyshev-step "
+                         "time and HBM fraction per panel width, mixed vs FP64 calls and their populations")
     ap.add_argument("--csc-scf", type=int, default=1,
                     help="timed SCF iterations of the charge-self-consistency measurement (0: skip)")
     return ap.parse_args()
@@ -671,10 +674,71 @@ def run_ours(args):
     return 0
 
 
+def run_large(args):
+    """The 100 000-atom Si system (25x25x20 diamond cells, seed 6, N = 400 000,
+    1.68 M blocks; its FP32 S, 108 MB, exceeds L2): for panels of 4 ... 128
+    columns, one Mulliken call of 3 outer iterations (after a warm-up call)
+    with the library's per-launch CUDA events on, giving the Chebyshev step's
+    busy time per launch and its algorithmic bytes (FP32 S once, index arrays
+    once, four panel passes) against the measured HBM copy rate; at 32 and
+    128 columns the same call in FP64, and the largest difference of the two
+    precisions' populations.  One JSON line."""
+    import torch
+    from tbinputs import si_system, gauss_legendre_grid
+    P = __import__("paper_1002_1202_gb300")
+    P.build()
+    t0 = time.time()
+    s = si_system((25, 25, 20), seed=6)
+    build_s = time.time() - t0
+    z, w = gauss_legendre_grid(128, -20.0, 5.0, 0.01)
+    h = P.tb_create_system(s)
+    peaks = measured_peaks()
+    nnz = 16 * s.nb
+    rows = []
+    for panel in (4, 8, 16, 32, 64, 128):
+        cols = rank_columns(s.n_orb, panel, 0)
+        rec = {"panel": panel}
+        q = {}
+        for prec in ((1, 0) if panel in (32, 128) else (1,)):
+            opts = P.tb_default_opts(max_iter=3, panel=panel, precision=prec, tol=1e-8, inner_tol=1e-12)
+            P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts, allow_unconverged=True)
+            torch.cuda.synchronize()
+            P.tb_profile_enable(True)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            out, _ = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts, allow_unconverged=True)
+            ev1.record()
+            ev1.synchronize()
+            q[prec] = out.cpu().numpy()
+            if prec == 1:
+                n_l, _ms = P.tb_profile_read("inner32_cheb")
+                busy = P.tb_profile_busy("inner32_cheb")
+                us = busy / max(n_l, 1) * 1e3
+                nbytes = nnz * 4 + 4 * s.nb + 4 * (s.n_atoms + 1) + 4 * s.n_orb * panel * 8
+                rec.update({"cheb_launches": n_l, "cheb_us_per_launch": us,
+                            "cheb_algorithmic_GBps": nbytes / us / 1e3,
+                            "cheb_hbm_frac": nbytes / us / 1e3 / peaks["hbm_gbs"]})
+                rec["mixed_call_ms"] = ev0.elapsed_time(ev1)
+            else:
+                rec["fp64_call_ms"] = ev0.elapsed_time(ev1)
+            P.tb_profile_enable(False)
+        if 0 in q:
+            rec["max_population_difference"] = float(np.abs(q[1] - q[0]).max())
+            rec["fp64_over_mixed_time"] = rec["fp64_call_ms"] / rec["mixed_call_ms"]
+        rows.append(rec)
+    print(json.dumps({"metric": "large_system", "workload": "Si diamond 25x25x20 cells, 100000 atoms, N=400000, "
+                      "%d blocks, 128 Gauss-Legendre shifts on [-20,5] eV + 0.01i eV, 3 outer iterations per call, "
+                      "mixed precision (FP32 Chebyshev corrections) and FP64" % s.nb,
+                      "build_s": build_s, "peaks": peaks, "panels": rows}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.large:
+        return run_large(args)
     return run_ours(args)
 
 
