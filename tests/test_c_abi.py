@@ -53,3 +53,31 @@ def test_c_program_runs(exe):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     want = "ok" if torch.cuda.is_available() else "no-device"
     assert r.returncode == 0 and r.stdout.strip() == want, (r.returncode, r.stdout, r.stderr)
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """sizeof and offsetof of every C-ABI struct, printed by a C program
+    compiled against the header, equal those of the ctypes mirrors."""
+    import ctypes
+    from paper_1002_1202_gb300 import tb
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    out = str(tmp_path / "layout")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi", "layout.c"), "-o", out], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lines = subprocess.run([out], capture_output=True, text=True, check=True).stdout.split("\n")
+    mirrors = {"tb_system_desc": tb.SystemDesc, "tb_solve_opts": tb.SolveOpts, "tb_stats": tb.Stats,
+               "tb_csc_opts": tb.CscOpts, "tb_csc_stats": tb.CscStats}
+    seen = set()
+    for ln in filter(None, lines):
+        name, field, value = ln.split()
+        cls = mirrors[name]
+        if field == "sizeof":
+            assert ctypes.sizeof(cls) == int(value), name
+        else:
+            assert getattr(cls, field).offset == int(value), (name, field)
+            seen.add((name, field))
+    for name, cls in mirrors.items():
+        assert {f for f, _ in cls._fields_} == {f for n, f in seen if n == name}, name
+
