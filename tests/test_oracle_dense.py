@@ -86,6 +86,23 @@ def test_jacobi_vs_lapack():
     assert np.abs(dense.jacobi_eigvals(A) - np.linalg.eigvalsh(A)).max() < 1e-11
 
 
+def test_jacobi_stops_on_a_dominant_diagonal():
+    """A matrix whose diagonal dominates its norm: the off-diagonal norm
+    written as ||A||^2 - sum diag^2 cancels to ~sqrt(eps) ||A|| and never
+    meets the tolerance; summed directly it does, and the eigenvalues agree
+    with LAPACK."""
+    rng = np.random.default_rng(0)
+    # advance the generator past two other draws: with the matrix drawn
+    # next, the cancelling form does not stop within 20 sweeps
+    for n, scale in ((40, 1e3), (30, 1.0)):
+        rng.uniform(-scale, scale, n)
+        rng.standard_normal((n, n))
+    A = np.diag(rng.uniform(-40.0, 40.0, 48)) + 0.1 * rng.standard_normal((48, 48))
+    A = 0.5 * (A + A.T)
+    ev = dense.jacobi_eigvals(A, max_sweeps=20)
+    assert np.abs(ev - np.linalg.eigvalsh(A)).max() <= 1e-12 * np.abs(ev).max()
+
+
 @pytest.mark.slow
 def test_mulliken_sum_rule(si64, si64_dense):
     H, S = si64_dense
