@@ -237,8 +237,11 @@ static tb_status lanczos_bounds(int n, const int32_t* opa, const int64_t* brow, 
     std::vector<int64_t> ooff(n + 1, 0);
     for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + opa[i];
     const int64_t N = ooff[n];
-    auto smul = [&](const std::vector<double>& x, std::vector<double>& y) {
-        for (int I = 0; I < n; ++I) {
+    // y = S x, block rows split over host threads for large systems (every
+    // row is computed the same way whatever the split)
+    const int nthreads = n >= 8192 ? (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1;
+    auto smul_rows = [&](const std::vector<double>& x, std::vector<double>& y, int I0, int I1) {
+        for (int I = I0; I < I1; ++I) {
             const int ni = opa[I];
             double acc[4] = {0.0, 0.0, 0.0, 0.0};
             for (int64_t blk = brow[I]; blk < brow[I + 1]; ++blk) {
@@ -250,6 +253,19 @@ static tb_status lanczos_bounds(int n, const int32_t* opa, const int64_t* brow, 
             }
             for (int a = 0; a < ni; ++a) y[ooff[I] + a] = acc[a];
         }
+    };
+    auto smul = [&](const std::vector<double>& x, std::vector<double>& y) {
+        if (nthreads <= 1) {
+            smul_rows(x, y, 0, n);
+            return;
+        }
+        std::vector<std::thread> pool;
+        const int chunk = (n + nthreads - 1) / nthreads;
+        for (int t = 0; t < nthreads; ++t) {
+            const int I0 = t * chunk, I1 = std::min(n, I0 + chunk);
+            if (I0 < I1) pool.emplace_back(smul_rows, std::cref(x), std::ref(y), I0, I1);
+        }
+        for (auto& th : pool) th.join();
     };
     const int m_max = (int)std::min<int64_t>(N, 80);
     std::vector<double> q(N), qp(N, 0.0), w(N), al, be;
