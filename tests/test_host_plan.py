@@ -89,3 +89,27 @@ def test_plan_coefficients_reproduce_chebyshev_polynomials(P):
         ref = np.array([_cheb(k + 1, (hi + lo - 2 * l) / (hi - lo)) for l in lam]) / _cheb(k + 1, mu)
         assert np.abs(err - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max()), k
     assert np.abs((x - d) / x).max() <= 1e-6
+
+
+def test_bounds_and_plan_edge_cases(P):
+    """One s atom (S = [1]) and one sp atom (S = I4, the Lanczos run stops
+    at its first step): the bounds are the margins around 1 and the plan is
+    short; malformed descriptions and tolerances are rejected."""
+    import types
+    one_s = types.SimpleNamespace(orb_per_atom=np.array([1]), brow_ptr=np.array([0, 1]), bcol=np.array([0]),
+                                  S_vals=np.array([1.0]))
+    one_sp = types.SimpleNamespace(orb_per_atom=np.array([4]), brow_ptr=np.array([0, 1]), bcol=np.array([0]),
+                                   S_vals=np.eye(4).ravel())
+    for sysm in (one_s, one_sp):
+        lo, hi = P.tb_overlap_bounds_desc(sysm)
+        assert lo == pytest.approx(0.97) and hi == pytest.approx(1.01)
+        pl = P.tb_chebyshev_plan(lo, hi, 1e-6, 1e-12)
+        assert 1 <= pl["n"] <= 9 and pl["rounds"] == 2
+    bad = types.SimpleNamespace(orb_per_atom=np.array([2]), brow_ptr=np.array([0, 1]), bcol=np.array([0]),
+                                S_vals=np.eye(2).ravel())
+    with pytest.raises(P.TBError) as e:
+        P.tb_overlap_bounds_desc(bad)
+    assert e.value.status == 1
+    for lo_tol, inner_tol in ((1.0, 1e-12), (0.0, 1e-12), (1e-6, 0.0)):
+        with pytest.raises(P.TBError):
+            P.tb_chebyshev_plan(0.2, 2.4, lo_tol, inner_tol)
