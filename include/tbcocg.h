@@ -33,6 +33,14 @@
  *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *    stream.  All device work of a call is enqueued on it.
  *  - Only one call may use a given handle at a time.
+ *  - Shifts: 1 <= K <= 1024 finite complex z_k (and opts->seed < K), else
+ *    TB_ERR_INVALID_ARG.  Im z_k != 0 keeps z_k S - H nonsingular (S is
+ *    positive definite, H real symmetric); a real shift at or near an
+ *    eigenvalue ends in TB_ERR_BREAKDOWN or TB_ERR_NOT_CONVERGED.
+ *  - Columns: 1 <= R, every cols[c] in [0, N) (repeats allowed), else
+ *    TB_ERR_INVALID_ARG; columns are solved in panels of opts->panel
+ *    (a power of two <= 256; 0 picks one), a ragged last panel padded with
+ *    inactive columns.
  */
 #ifndef TBCOCG_H
 #define TBCOCG_H
