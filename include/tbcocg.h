@@ -62,7 +62,10 @@ typedef enum {
     TB_ERR_CUDA = 5,           /* a CUDA runtime call failed              */
     TB_ERR_NOT_CONVERGED = 6,  /* max_iter reached; converged shifts valid*/
     TB_ERR_BREAKDOWN = 7,      /* COCG breakdown (rho or mu == 0)         */
-    TB_ERR_TIMEOUT = 8,        /* a bounded device wait ran out           */
+    TB_ERR_TIMEOUT = 8,        /* reserved: no kernel of this library waits
+                                  on another CTA, flag or stream (grid
+                                  reductions take arrival tickets and never
+                                  spin), so no call returns it              */
     TB_ERR_NO_DEVICE = 9,      /* no usable CUDA device                   */
     TB_ERR_TOO_LARGE = 10      /* request exceeds the fixed scratch of the
                                   allocation-free entry point              */
@@ -436,16 +439,19 @@ tb_status tb_lanczos_green_batch(int32_t R, const double *a, const double *b, co
  * and gives the same results and errors as tb_generalized_lanczos, but it
  * calls no cudaMalloc, cudaFree or other allocating routine: its scratch
  * memory is one fixed device array inside the library,
- * TB_NOALLOC_SCRATCH_BYTES (16 MiB) long, which every GPU that loads the
- * library holds until the process exits.  The handle (made by tb_create,
+ * TB_NOALLOC_SCRATCH_BYTES (16 MiB) long.  The handle (made by tb_create,
  * which does allocate) and the outputs a, b, norm are the caller's.
+ *  - Set-up: tb_create places the array on the handle's device, looks up its
+ *    device address (cudaGetSymbolAddress, with that device current) and
+ *    loads the kernels this call launches (with CUDA's lazy module loading
+ *    both would otherwise happen, and allocate, at the first call).  Every
+ *    GPU on which a handle was created holds the array until the process
+ *    exits.  Call this entry point with the handle's device current
+ *    (otherwise TB_ERR_INVALID_ARG).
  *  - Size limit: the call needs about 160 * 4 * n_atoms + 16 * n_steps bytes
  *    (plus ~50 kB); a request that does not fit returns TB_ERR_TOO_LARGE
  *    before any device work (N up to ~100 000 orbitals with a few hundred
  *    steps).
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current) and caches it; make
- *    that first call before any stream capture on the device.
  *  - All calls share the one array and it keeps the previous call's
  *    contents (each call clears what it needs zeroed).  Calls whose GPU work
  *    overlaps -- on different streams or from different threads, with this

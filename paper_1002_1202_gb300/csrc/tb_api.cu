@@ -17,9 +17,11 @@
 using namespace tb;
 
 // Fixed scratch of tb_generalized_lanczos_noalloc: one file-scope device
-// array, present on every GPU that loads this library until the process
-// exits.  Host code must not use the symbol as an address; it asks the
-// runtime for the array's device address once per device.
+// array.  Host code must not use the symbol as an address; tb_create asks
+// the runtime for the array's device address on the handle's device (which
+// also loads the array there: with lazy module loading a module and its
+// device arrays are placed on a device only when first used) and keeps it
+// in the handle.  From then on the array stays on that GPU until exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TB_NOALLOC_SCRATCH_BYTES];
 
 namespace tb {
@@ -63,7 +65,35 @@ struct tb_handle {
     std::once_flag s_once;
     double s_lo = 0.0, s_hi = 0.0;
     tb_status s_status = TB_OK;
+    // device address of the allocation-free call's fixed scratch on this
+    // handle's device (looked up by tb_create)
+    unsigned char* noalloc_base = nullptr;
 };
+
+// Device address of g_noalloc_scratch on device dev (which must be current),
+// looked up once per device and cached.  The lookup loads the array (and the
+// kernels of the allocation-free path, see preload_noalloc_kernels) onto the
+// device, so it runs inside tb_create, which allocates anyway.
+static tb_status noalloc_scratch(int dev, unsigned char** out) {
+    static std::mutex mu;
+    static void* addr[256] = {nullptr};
+    if (dev < 0 || dev >= 256) return TB_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return TB_ERR_CUDA;
+        }
+        if (!preload_noalloc_kernels()) {
+            cudaGetLastError();
+            return TB_ERR_CUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(addr[dev]);
+    return TB_OK;
+}
 
 namespace {
 
@@ -1449,6 +1479,7 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     launch_split_f64(h->ds.H, h->ds.H32hi, h->ds.H32lo, 16 * (long long)nb, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    if (noalloc_scratch(h->device, &h->noalloc_base) != TB_OK) return fail(cudaErrorUnknown);
     h->sys_atom_off = {0, (int64_t)n};
     h->sys_orb_off = {0, N};
     *out = h;
@@ -2182,29 +2213,6 @@ tb_status tb_generalized_lanczos(tb_handle* h, int32_t j, int32_t n_steps, doubl
 
 }  // extern "C"
 
-// Device address of g_noalloc_scratch for the current device, looked up once
-// per device (with that device current) and cached.
-static tb_status noalloc_scratch(unsigned char** out) {
-    static std::mutex mu;
-    static void* addr[256] = {nullptr};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
-        cudaGetLastError();
-        return TB_ERR_CUDA;
-    }
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return TB_ERR_CUDA;
-        }
-        addr[dev] = p;
-    }
-    *out = static_cast<unsigned char*>(addr[dev]);
-    return TB_OK;
-}
-
 // Carves aligned pieces out of the fixed scratch; fails when it would overrun.
 struct ScratchCarver {
     unsigned char* base;
@@ -2250,10 +2258,16 @@ tb_status tb_generalized_lanczos_noalloc(tb_handle* h, int32_t j, int32_t n_step
     dry.take<double>((size_t)n_steps + 1);
     dry.take<double>(1);
     if (!dry.ok) return TB_ERR_TOO_LARGE;
-    unsigned char* base = nullptr;
-    tb_status s = noalloc_scratch(&base);
-    if (s != TB_OK) return s;
-    ScratchCarver sc(base, TB_NOALLOC_SCRATCH_BYTES);
+    // the handle's device must be current: the scratch address and the
+    // kernels were placed there by tb_create
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TB_ERR_CUDA;
+    }
+    if (dev != h->device || !h->noalloc_base) return TB_ERR_INVALID_ARG;
+    tb_status s = TB_OK;
+    ScratchCarver sc(h->noalloc_base, TB_NOALLOC_SCRATCH_BYTES);
     double2** vecs[] = {&p.Rcur, &p.Rprev, &p.Rp, &p.W, &p.Rin, &p.Pin, &p.Sin};
     for (double2** v : vecs) *v = sc.take<double2>(npad);
     double2* U = sc.take<double2>(npad);

@@ -138,6 +138,7 @@ double profile_busy(int id);
 int64_t launch_count();
 
 // ---- launchers (tb_kernels.cu) -------------------------------------------
+bool preload_noalloc_kernels();   // loads the allocation-free call's kernels onto the current device
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st);
 void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaStream_t st);
 void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);

@@ -2153,6 +2153,20 @@ static int grid_for(long long items) {
     return (int)(g < 1 ? 1 : (g > gm ? gm : g));
 }
 
+// Loads the kernels of the allocation-free Lanczos call onto the current
+// device (cudaFuncGetAttributes loads a kernel that lazy module loading has
+// not placed yet), so that the call's first launches need no device memory.
+bool preload_noalloc_kernels() {
+    const void* ks[] = {(const void*)k_panel_init, (const void*)k_inner_spmv, (const void*)k_inner_update,
+                        (const void*)k_lz_start,   (const void*)k_lz_spmv,    (const void*)k_lz_dot,
+                        (const void*)k_lz_combine, (const void*)k_lz_scale};
+    for (const void* k : ks) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return false;
+    }
+    return true;
+}
+
 void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
     k_split_f64<<<grid_for(n), THREADS, 0, st>>>(v, hi, lo, n);

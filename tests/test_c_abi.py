@@ -81,3 +81,14 @@ def test_struct_layouts_match_the_binding(tmp_path):
     for name, cls in mirrors.items():
         assert {f for f, _ in cls._fields_} == {f for n, f in seen if n == name}, name
 
+
+
+@pytest.mark.gpu
+def test_c_program_solves_dimer_on_gpu(exe):
+    """The same C99 program on a GPU: the two-atom solve through the plain C
+    ABI must print ok (its populations equal their closed form)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)

@@ -128,3 +128,42 @@ def test_mulliken_small_sum_rule_lapack():
     q = dense.mulliken_orbital(H, S, z, w)
     eig = sl.eigh(H, S, eigvals_only=True)
     assert abs(q.sum() - dense.electron_count_closed_form(eig, z, w)) < 1e-9
+
+
+def _sparse_vs_dense(sy):
+    """Eq. Hap-1 on the stored entries of S against the same rule applied
+    to the dense S: the same formula with the same operands, so the two
+    must agree bit for bit (any index slip in the COO walk shows up)."""
+    S = sy.dense_S()
+    oa = sy.orbital_atom()
+    Hd = dense.ased_hamiltonian(S, sy.eps, sy.K, oa)
+    Hs = dense.ased_hamiltonian_sparse(sy.to_csr(), sy.eps, sy.K, oa).toarray()
+    assert Hs.shape == Hd.shape
+    assert np.array_equal(Hs, Hd)
+    return Hd
+
+
+def test_ased_sparse_equals_dense_si64(si64):
+    H = _sparse_vs_dense(si64)
+    # the diagonal carries eps of the orbital itself (s and p levels differ)
+    assert np.array_equal(np.diag(H), si64.eps)
+
+
+def test_ased_sparse_equals_dense_water_ragged():
+    """Water with the excess proton: O sp (4 orbitals) and H s (1 orbital)
+    give 4x4, 4x1, 1x4 and 1x1 blocks and three different on-site levels, so
+    the pairing eps[a] + eps[b] of the rule is checked across block shapes."""
+    from tbinputs import water_box
+    sp, pos, box, _ = water_box(6, seed=11, excess_proton=True)
+    sy = build_system(sp, pos, box + 20.0, (False, False, False), 4.5)
+    shapes = {(int(sy.orb_per_atom[i]), int(sy.orb_per_atom[j]))
+              for i in range(sy.n_atoms) for j in sy.bcol[sy.brow_ptr[i]:sy.brow_ptr[i + 1]]}
+    assert shapes == {(4, 4), (4, 1), (1, 4), (1, 1)}
+    assert sy.n_orb == 6 * 6 + 1
+    H = _sparse_vs_dense(sy)
+    # an O s - H s element follows Eq. Hap-1 with the two different levels
+    oa = sy.orbital_atom()
+    S = sy.dense_S()
+    o_s, h_s = 0, 4          # first O's s orbital, its first H
+    assert oa[o_s] != oa[h_s]
+    assert H[o_s, h_s] == sy.K * 0.5 * (sy.eps[o_s] + sy.eps[h_s]) * S[o_s, h_s] != 0.0

@@ -67,3 +67,40 @@ def test_noalloc_rejects_request_beyond_scratch(P, handle):
     a, b, nrm = P.tb_generalized_lanczos_noalloc(handle, 9, 20)
     a0, b0, n0 = P.tb_generalized_lanczos(handle, 9, 20)
     assert _close(a, a0) and _close(b, b0)
+
+
+_FRESH = r"""
+import sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch
+import paper_1002_1202_gb300 as P
+from tbinputs import si_system
+torch.cuda.init()
+P.load_library()
+h = P.tb_create_system(si_system((2, 2, 2), sigma=0.05, seed=1, cutoff=4.0))
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+out = (np.zeros(30), np.zeros(31), np.zeros(1))
+P.tb_generalized_lanczos_noalloc(h, 9, 30, out=out)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+assert np.all(out[1][1:] > 0) and out[2][0] > 0
+print("FREE", free0, free1)
+"""
+
+
+def test_noalloc_first_call_in_fresh_process_allocates_nothing(P):
+    """In a new process, after tb_create (which allocates), the first call of
+    the allocation-free entry point must leave the device's free memory
+    unchanged: the fixed array and the call's kernels were placed on the
+    device by tb_create, not by this call."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH.format(root=root)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("FREE")][-1].split()
+    assert int(line[1]) == int(line[2]), line
