@@ -391,11 +391,14 @@ def kernel_source_sha256(kernel_file, kernel_name):
     return None
 
 
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+
+
 def stored_traffic(kernel_file, kernel_name, panel=None):
     """DRAM bytes per launch from a committed ncu summary, valid only while
     the text of the kernel it was taken from is unchanged and (for entries
     captured per panel width) for the panel width it was taken at."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = TRAFFIC_PATH
     if not os.path.exists(path):
         return None
     try:

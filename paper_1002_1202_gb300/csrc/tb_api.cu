@@ -532,7 +532,7 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
             }
             cudaMemsetAsync(p.hist, 0, sizeof(double) * nh, st);
         }
-        if (v.flags_host[0] & (ERR_NOT_SPD | ERR_BREAKDOWN)) {
+        if (v.flags_host[0] & (ERR_NOT_SPD | ERR_INNER)) {
             debug_inner32(v, p, round, st);
             return (v.flags_host[0] & ERR_NOT_SPD) ? TB_ERR_S_NOT_SPD : TB_ERR_BREAKDOWN;
         }
@@ -562,7 +562,7 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
             TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
             TB_CK(cudaStreamSynchronize(st));
             prof_harvest();
-            if (v.flags_host[0] & ERR_BREAKDOWN) return TB_ERR_BREAKDOWN;
+            if (v.flags_host[0] & ERR_INNER) return TB_ERR_BREAKDOWN;
             if (v.flags_host[4] == 0) {
                 rounds_pred = round + 1;
                 return TB_OK;
@@ -612,9 +612,13 @@ tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_ma
     ic.cheb.n = 0;   // the rest of this solve uses the FP32 CG corrections
     // The FP32 corrections failed to converge (or produced a non-finite
     // residual): redo this inner solve with the FP64 CG, on the device.
-    // flags[0] keeps no trace of the failed attempt.
-    int zero = 0;
-    TB_CK(cudaMemcpyAsync(p.flags, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    // flags[0] keeps no trace of the failed attempt, but keeps the outer
+    // recurrence's own error bits (a breakdown of a column's COCG is
+    // reported as such, not turned into a redo of the inner solve).
+    TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaStreamSynchronize(st));
+    const int keep = v.flags_host[0] & ~ERR_INNER;
+    TB_CK(cudaMemcpyAsync(p.flags, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
     TB_CK(cudaMemcpyAsync(p.Rin, b, sizeof(double2) * (size_t)p.npad * p.P, cudaMemcpyDeviceToDevice, st));
     s = inner_cg(v, p, inner_max, ic.pred, ic.total, st);
     if (s != TB_OK) return s;

@@ -19,8 +19,9 @@ constexpr int MAX_GROUPS = 64; // upper bound on first-level groups (grids <= 20
 constexpr int HIST_IT = 64;    // FP32 CG iterations kept by the trace history
 
 // error bits in PanelDev::flags[0]
-constexpr int ERR_BREAKDOWN = 1;
+constexpr int ERR_BREAKDOWN = 1;   // COCG breakdown of the outer recurrence (mu or rho zero / non-finite)
 constexpr int ERR_NOT_SPD = 2;
+constexpr int ERR_INNER = 4;       // mixed path: a refinement residual of the inner solve went non-finite
 
 // functional kinds of the projected mode
 constexpr int PROJ_NONE = 0;   // full solutions kept (x^k, p^k are N-vectors)

@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
                     const double r2 = smem[part * THREADS + t];
                     const double b2 = p.inner[2 * t + part].bnorm2;
                     if (!isfinite(r2)) {
-                        atomicOr(&p.flags[0], ERR_BREAKDOWN);
+                        atomicOr(&p.flags[0], ERR_INNER);
                         if (p.dbg) {
                             p.dbg[0] = -1.0; p.dbg[1] = 2 * t + part; p.dbg[2] = r2; p.dbg[3] = st.scale;
                             p.dbg[4] = b2; p.dbg[5] = st.bnorm2; p.dbg[6] = st.gamma_prev; p.dbg[7] = st.alpha;

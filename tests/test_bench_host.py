@@ -20,17 +20,36 @@ def test_kernel_hash_covers_the_kernel_text():
     assert h != bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_spmv")
 
 
-def test_stored_traffic_is_per_panel_and_hash_guarded(monkeypatch):
+def test_stored_traffic_is_per_panel_and_hash_guarded(monkeypatch, tmp_path):
+    import json
+    rec = {"k_inner32_cheb": {"kernel_sha256": bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_cheb"),
+                           "by_panel": {"128": 60e6, "256": 120e6}},
+           "k_inner32_spmv": {"kernel_sha256": bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_spmv"),
+                              "dram_bytes_per_launch": 42e6, "panel": 256}}
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(path))
     t128 = bench.stored_traffic("tb_kernels.cu", "k_inner32_cheb", 128)
     t256 = bench.stored_traffic("tb_kernels.cu", "k_inner32_cheb", 256)
-    assert t128 and t256 and t256 > t128
+    assert t128 == 60e6 and t256 == 120e6
     assert bench.stored_traffic("tb_kernels.cu", "k_inner32_cheb", 64) is None
     # an entry captured at one width is not reported for another
     assert bench.stored_traffic("tb_kernels.cu", "k_inner32_spmv", 128) is None
-    assert bench.stored_traffic("tb_kernels.cu", "k_inner32_spmv", 256)
+    assert bench.stored_traffic("tb_kernels.cu", "k_inner32_spmv", 256) == 42e6
     # once the kernel text changes the stored figure is void
     monkeypatch.setattr(bench, "kernel_source_sha256", lambda f, k: "0" * 64)
     assert bench.stored_traffic("tb_kernels.cu", "k_inner32_cheb", 128) is None
+
+
+def test_committed_traffic_entries_match_their_kernels():
+    """Every entry of the committed traffic record names a kernel that
+    exists; an entry whose kernel text changed is reported as void (None)
+    rather than carried over."""
+    import json
+    import os
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for name in rec:
+        assert bench.kernel_source_sha256("tb_kernels.cu", name) is not None, name
 
 
 @pytest.mark.parametrize("panel", [128, 256])
