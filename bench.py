@@ -422,8 +422,17 @@ KERNEL_INFO = {
     "outer_spmm": ("k_outer_spmm", 8, 16, True),
     "refine_residual": ("k_refine_residual", 8, 16, True),
     "inner32_spmv": ("k_inner32_spmv", 4, 8, False),
-    "inner32_cheb": ("k_inner32_cheb", 4, 8, False),
+    "inner32_cheb": ("k_inner32_cheb4", 4, 8, False),
 }
+
+
+def cheb_kernel_name(panel):
+    """The Chebyshev step's kernel: four columns per thread with packed FMAs
+    for panels of 4 columns or more, else (or with TB_CHEB_CPT=2) the
+    two-columns-per-thread form."""
+    if os.environ.get("TB_CHEB_CPT") == "2" or panel < 4:
+        return "k_inner32_cheb"
+    return "k_inner32_cheb4"
 
 
 DF_INSTR_PER_MAC = 12   # FP32 instructions of one double-float multiply-add (exact product + two-sum)
@@ -441,6 +450,8 @@ def roofline_for(kname, ms, launches, s, panel, peaks, mixed=False, busy_ms=None
     FP64 multiply-add; they are rated against the FP32 issue peak (2 flop per
     FP32 lane-instruction), not against the FP64 units they do not use."""
     kern, mb, vb, fp64 = KERNEL_INFO[kname]
+    if kname == "inner32_cheb":
+        kern = cheb_kernel_name(panel)
     double_float = mixed and kname in ("outer_spmm", "refine_residual")
     nnz = 16 * s.nb
     mats = 2 if kname == "outer_spmm" else 1

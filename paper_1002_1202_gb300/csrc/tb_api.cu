@@ -1286,6 +1286,7 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->ds.H);
     cudaFree(h->ds.S32);
     cudaFree(h->ds.S32lo);
+    cudaFree(h->ds.S32T);
     cudaFree(h->ds.H32hi);
     cudaFree(h->ds.H32lo);
     cudaFree(h->ds.grp_ptr);
@@ -1441,6 +1442,7 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     if ((e = cudaMalloc(&h->ds.H, sizeof(double) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.S32, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.S32lo, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&h->ds.S32T, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.H32hi, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->ds.H32lo, sizeof(float) * 16 * nb)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&h->orb2pad, sizeof(int32_t) * N)) != cudaSuccess) return fail(e);
@@ -1480,6 +1482,7 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     }
     // double-float splits of S and H for the mixed path's FP64-accurate products
     launch_split_f64(h->ds.S, h->ds.S32, h->ds.S32lo, 16 * (long long)nb, st);
+    launch_transpose_blocks(h->ds.S32, h->ds.S32T, nb, st);
     launch_split_f64(h->ds.H, h->ds.H32hi, h->ds.H32lo, 16 * (long long)nb, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);

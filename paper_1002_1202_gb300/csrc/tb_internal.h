@@ -41,6 +41,7 @@ struct DevSystem {
     double* H = nullptr;       // [nb][16]
     float* S32 = nullptr;      // [nb][16] S rounded to FP32 (S_hi of the double-float split)
     float* S32lo = nullptr;    // [nb][16] S - S_hi in FP32
+    float* S32T = nullptr;     // [nb][16] S_hi of every block transposed (column e of the block as row e)
     float* H32hi = nullptr;    // [nb][16] H rounded to FP32
     float* H32lo = nullptr;    // [nb][16] H - H_hi in FP32
     // atom groups of the grouped FP32 SpMV: group g = atoms [g * grpG, (g + 1) * grpG)
@@ -142,6 +143,7 @@ int64_t launch_count();
 bool preload_noalloc_kernels();   // loads the allocation-free call's kernels onto the current device
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st);
 void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaStream_t st);
+void launch_transpose_blocks(const float* in, float* out, long long nb, cudaStream_t st);
 void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_panel_rhs(const PanelDev& p, const double* rhs, const int32_t* orb2pad, int n_orb, int ncols,
                       cudaStream_t st);

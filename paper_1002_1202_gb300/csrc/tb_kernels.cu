@@ -179,6 +179,17 @@ __global__ void k_split_f64(const double* __restrict__ v, float* __restrict__ hi
 }
 
 // r_0 = b = e_j, r_{-1} = 0, inner right-hand side = b
+// out[b] = in[b]^T for every 4 x 4 FP32 block (the Chebyshev step reads the
+// columns of S_IJ as rows)
+__global__ void k_transpose_blocks(const float* __restrict__ in, float* __restrict__ out, long long nb) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 16 * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i >> 4;
+        const int a = (int)(i >> 2) & 3, e = (int)i & 3;
+        out[16 * b + 4 * e + a] = in[i];
+    }
+}
+
 __global__ void k_panel_init(PanelDev p) {
     const long long items = (long long)p.npad * p.P;
     for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
@@ -1229,6 +1240,107 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelD
     }
 }
 
+// The same Chebyshev step with four complex columns per thread and packed
+// FP32 FMAs: thread t0 of a block row (P / 4 threads per row) takes the
+// column pairs (2 t0, 2 t0 + 1) and (P/2 + 2 t0, P/2 + 2 t0 + 1), so each of
+// its two loads per gathered row is part of a contiguous 512-byte warp
+// access.  The block product runs over the rows e of the gathered d_k: row e
+// of the transposed block (column e of S_IJ, from S32T) gives S[a][e] for
+// the four output rows a, each broadcast into both lanes of a packed FMA
+// against the (re, im) pairs of the thread's columns.  Against two columns
+// per thread this halves the S loads and the FMA instructions per column
+// (ncu at P = 128: 7.3 M instead of 15.5 M warp instructions per launch).
+// Compiled for three CTAs per SM (80 registers): at four (64 registers) the
+// 32 accumulators spill.  Measured on the benchmark workload, four panels in
+// flight: 17.2 M shift*RHS*iterations/s against 15.8 M with two columns per
+// thread; eight columns per thread (two CTAs per SM), staging the next
+// block's rows in shared memory, and L1 / L2 prefetches of them all measured
+// slower.
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+template <int PW, bool LAST>
+__global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4(DevSystem s, PanelDev p, const float2* __restrict__ cur,
+                                                             float2* io, float omega, float gamma, int mode) {
+    constexpr int CPT = 4, NP = 2;   // columns, column pairs per thread
+    if (*(volatile int*)&p.flags[4] == 0) return;
+    const int P = PW > 0 ? PW : p.P;
+    const int TPR = P / CPT;
+    const int pstride = P / NP;
+    const int t0 = threadIdx.x % TPR;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) live |= cheb_live(p, k * pstride + 2 * t0) || cheb_live(p, k * pstride + 2 * t0 + 1);
+    if (!live) return;
+    const long long items = (long long)s.n_atoms * TPR;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const int I = (int)(idx / TPR);
+        float2 acc[4][CPT];   // [output row a][column 2k, 2k + 1 of pair k] (re, im)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) acc[a][q] = make_float2(0.f, 0.f);
+        const int b0 = s.brow[I], b1 = s.brow[I + 1];
+        int Jn = __ldg(s.bcol + b0);
+        for (int bb = b0; bb < b1; ++bb) {
+            const int J = Jn;
+            if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
+            const float2* xb = cur + (size_t)(4 * J) * P + 2 * t0;
+            const float4* St = reinterpret_cast<const float4*>(s.S32T + 16 * (size_t)bb);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float4 xq[NP];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) xq[k] = *reinterpret_cast<const float4*>(xb + (size_t)e * P + k * pstride);
+                const float4 sc = __ldg(St + e);     // S[0][e], S[1][e], S[2][e], S[3][e]
+                const float sv[4] = {sc.x, sc.y, sc.z, sc.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float2 s2 = make_float2(sv[a], sv[a]);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        acc[a][2 * k] = __ffma2_rn(s2, lo2(xq[k]), acc[a][2 * k]);
+                        acc[a][2 * k + 1] = __ffma2_rn(s2, hi2(xq[k]), acc[a][2 * k + 1]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const size_t row = (size_t)(4 * I + a) * P;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const int c = k * pstride + 2 * t0;
+                const size_t e = row + c;
+                const float4 f4 = *reinterpret_cast<const float4*>(p.r32 + e);
+                const float4 c4 = *reinterpret_cast<const float4*>(cur + e);
+                const float4 p4 = mode == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(io + e);
+                const float2 y0 = acc[a][2 * k], y1 = acc[a][2 * k + 1];
+                const float f[4] = {f4.x, f4.y, f4.z, f4.w}, dc[4] = {c4.x, c4.y, c4.z, c4.w};
+                const float dp[4] = {p4.x, p4.y, p4.z, p4.w}, y[4] = {y0.x, y0.y, y1.x, y1.y};
+                float dn[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - y[q]) + dc[q] - dp[q]);
+                if (LAST) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const InnerState i0 = p.inner32[2 * (c + j)], i1 = p.inner32[2 * (c + j) + 1];
+                        const bool ca = p.col[c + j].active != 0;
+                        double2 x = p.Rp[e + j];
+                        if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] / i0.scale;
+                        if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] / i1.scale;
+                        p.Rp[e + j] = x;
+                        p.RpS[e + j] = df_split(x);
+                    }
+                } else {
+                    *reinterpret_cast<float4*>(io + e) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+                }
+            }
+        }
+    }
+}
+
 // rho_{n+1} = r_{n+1}^T r'_{n+1} (unconjugated); also clears the count of
 // active columns that the shift step rebuilds.
 __global__ void __launch_bounds__(THREADS) k_finish(PanelDev p) {
@@ -2171,6 +2283,10 @@ void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaSt
     LaunchScope ls_(K_OTHER, st);
     k_split_f64<<<grid_for(n), THREADS, 0, st>>>(v, hi, lo, n);
 }
+void launch_transpose_blocks(const float* in, float* out, long long nb, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_transpose_blocks<<<grid_for(16 * nb), THREADS, 0, st>>>(in, out, nb);
+}
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st) {
     {
         LaunchScope ls_(K_OTHER, st);
@@ -2278,9 +2394,33 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
     else
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
 }
+// TB_CHEB_CPT=2 selects the two-columns-per-thread form of the Chebyshev
+// step; the default is four columns per thread with packed FMAs (panels of
+// at least 4 columns; narrower ones take the two-column form)
+static const int g_cheb_cpt = [] {
+    const char* e = std::getenv("TB_CHEB_CPT");
+    return e ? std::atoi(e) : 4;
+}();
+
+template <bool LAST>
+static void cheb4_launch(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
+                         float gamma, int mode, cudaStream_t st) {
+    const int g = std::min(grid_for((long long)s.n_atoms * (p.P / 4)), 3 * (gmax() / 4));
+    switch (p.P) {
+        case 256: k_inner32_cheb4<256, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+        case 128: k_inner32_cheb4<128, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+        case 64: k_inner32_cheb4<64, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+        default: k_inner32_cheb4<0, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+    }
+}
+
 template <bool LAST>
 static void cheb_launch(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
                         float gamma, int mode, cudaStream_t st) {
+    if (g_cheb_cpt == 4 && p.P >= 4) {
+        cheb4_launch<LAST>(s, p, cur, io, omega, gamma, mode, st);
+        return;
+    }
     if (p.P >= 2) {
         const int g = grid_for((long long)s.n_atoms * (p.P / 2));
         switch (p.P) {

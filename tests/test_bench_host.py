@@ -13,11 +13,11 @@ def _fake_system(n_atoms=4096, nb=69024):
 
 
 def test_kernel_hash_covers_the_kernel_text():
-    h = bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_cheb")
+    h = bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_cheb4")
     assert h is not None and len(h) == 64
-    assert bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_cheb") == h
+    assert bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_cheb4") == h
     assert bench.kernel_source_sha256("tb_kernels.cu", "k_no_such_kernel") is None
-    assert h != bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_spmv")
+    assert h != bench.kernel_source_sha256("tb_kernels.cu", "k_inner32_cheb")
 
 
 def test_stored_traffic_is_per_panel_and_hash_guarded(monkeypatch, tmp_path):
@@ -62,7 +62,7 @@ def test_roofline_of_the_chebyshev_step(panel):
     flops = 2.0 * nnz * 2 * panel + 5.0 * s.n_orb * 2 * panel
     nbytes = nnz * 4 + 4 * s.nb + 4 * (s.n_atoms + 1) + 4 * s.n_orb * panel * 8
     avg_s = busy_ms / launches / 1e3
-    assert rec["kernel"] == "k_inner32_cheb"
+    assert rec["kernel"] == "k_inner32_cheb4"
     assert rec["flops_per_launch"] == pytest.approx(flops)
     assert rec["algorithmic_bytes_per_launch"] == int(nbytes)
     assert rec["avg_launch_us"] == pytest.approx(avg_s * 1e6)
