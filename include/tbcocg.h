@@ -190,6 +190,19 @@ typedef struct {
                                  TB_INNER_CG: FP32 CG in every round.  Either way the
                                  FP64 residual of each round decides convergence, so both
                                  reach the same inner_tol.  Ignored for TB_FP64 (CG).   */
+    int64_t state_bytes;      /* energy-point checkpointing: device bytes allowed for the
+                                 full-vector state of the shifts (x^k and p^k of every
+                                 shift for the columns in flight, plus the device copy of
+                                 the full solutions; tb_shifted_cocg and tb_mulliken_vjp).
+                                 When all K shifts would exceed it, the shifts are taken
+                                 in chunks, each a separate shifted solve of the same
+                                 columns whose seed sequence is recomputed (its seed is
+                                 the chunk's own first shift, or opts->seed inside the
+                                 chunk that holds it); each chunk's solutions go to the
+                                 caller's output -- host memory included -- before the
+                                 next chunk starts, so state_bytes bounds device memory
+                                 whatever K.  Every shift's solution is the same to tol
+                                 as in one call.  0 = 8 GiB (default).                    */
 } tb_solve_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -383,6 +396,33 @@ tb_status tb_csc_loop(tb_handle *h, int32_t K, const double *z, const double *w,
                       const double *gamma, const double *q_ref, const double *dq_init,
                       const tb_csc_opts *copts, const tb_solve_opts *opts, double *q_out, double *dq_out,
                       tb_csc_stats *stats, void *stream);
+
+/*
+ * Forces of the charge-self-consistent model (Section 2.2, Eq. Hap-CSC; the
+ * paper cites the second-order charge-transfer energy but prints no total
+ * energy).  With the quadrature (z_k, w_k) the occupation is smeared, and
+ * the functional whose H-derivative is exactly the density matrix is the
+ * contour grand potential Omega(H, S) = (g_s/pi) Im sum_k w_k Tr ln(z_k S - H);
+ * the free energy A(dq) = Omega(H0 + H^CSC(dq), S) - V^T (dq + q_ref)
+ * + 1/2 dq^T gamma dq (V = gamma dq) has dA/d dq = gamma (q_out - q_in), so at
+ * a self-consistent dq (tb_csc_loop's dq_out) the forces need no charge
+ * response:
+ *     F_I = -dA/dR_I = -sum_ab [rho_ba dH0_ab/dR_I + (dOmega/dS_ab
+ *           + rho_ba (V_a + V_b)/2) dS_ab/dR_I] - dq_I sum_k (dgamma_Ik/dR_I) dq_k,
+ * rho = -(g_s/pi) Im sum_k w_k G(z_k), dOmega/dS_ab = (g_s/pi) Im sum_k
+ * w_k z_k G_ba(z_k), H0 by Eq. Hap-1 (handles built from eps and K only, else
+ * TB_ERR_INVALID_ARG).  The call sets the handle's H to H0 + H^CSC(dq) (as
+ * tb_csc_hamiltonian, and leaves it there), solves every column with the
+ * rows of its block column projected, and applies the force kernels of
+ * tb_forces plus the Coulomb-gradient term.  gamma: double [n_atoms][n_atoms];
+ * dgamma: double [n_atoms][n_atoms][3], d gamma_Ik / d R_I; dq: double
+ * [n_atoms]; dS_dd: double [3][n_values] as in tb_forces; F_out: double
+ * [n_atoms][3]; all host or device.  Status as tb_shifted_cocg; a batch
+ * handle of more than one system is TB_ERR_INVALID_ARG.
+ */
+tb_status tb_csc_forces(tb_handle *h, int32_t K, const double *z, const double *w, double g_s,
+                        const double *gamma, const double *dgamma, const double *dq, const double *dS_dd,
+                        const tb_solve_opts *opts, double *F_out, tb_stats *stats, void *stream);
 
 /*
  * Generalized Lanczos process (Section 3.2, Eqs. 1.13 and 1.18) for the

@@ -186,7 +186,20 @@ tb_status check_opts(const tb_solve_opts* o) {
     if (o->precision != TB_FP64 && o->precision != TB_MIXED) return TB_ERR_INVALID_ARG;
     if (o->precision == TB_MIXED && !(o->inner_lo_tol > 0.0 && o->inner_lo_tol < 1.0)) return TB_ERR_INVALID_ARG;
     if (o->inner_method != TB_INNER_CHEBYSHEV && o->inner_method != TB_INNER_CG) return TB_ERR_INVALID_ARG;
+    if (o->state_bytes < 0) return TB_ERR_INVALID_ARG;
     return TB_OK;
+}
+
+// Device bytes allowed for the full-vector shift state of a call
+// (tb_solve_opts::state_bytes; 0 = 8 GiB).
+int64_t state_budget(const tb_solve_opts* o) { return o->state_bytes > 0 ? o->state_bytes : (int64_t)8 << 30; }
+
+// The options of one chunk of shifts [k0, k0 + kc): the seed is opts->seed
+// when it lies inside the chunk, else the chunk's first shift.
+tb_solve_opts chunk_opts(const tb_solve_opts* o, int k0, int kc) {
+    tb_solve_opts c = *o;
+    c.seed = (o->seed >= k0 && o->seed < k0 + kc) ? o->seed - k0 : 0;
+    return c;
 }
 
 // ---- spectrum of S for the Chebyshev corrections ---------------------------
@@ -676,8 +689,10 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
     int P = o->panel ? o->panel : 64;
     P = std::min(P, next_pow2(R));
     if (q.proj == PROJ_NONE) {
-        // keep the full-mode x^k, p^k within 8 GiB
-        while (P > 1 && (double)K * npad * P * 32.0 > 8.0 * (1 << 30)) P >>= 1;
+        // keep the full-mode x^k, p^k within the state budget (the callers
+        // chunk the shifts first; a single shift that still does not fit
+        // takes narrower panels)
+        while (P > 1 && (double)K * npad * P * 32.0 > (double)state_budget(o)) P >>= 1;
     }
     int M = 0;
     if (q.proj == PROJ_ROWS) {
@@ -1256,6 +1271,7 @@ void tb_default_opts(tb_solve_opts* o) {
     o->precision = TB_FP64;
     o->inner_lo_tol = 1e-6;
     o->inner_method = TB_INNER_CHEBYSHEV;
+    o->state_bytes = 0;
 }
 
 int64_t tb_launch_count(void) { return launch_count(); }
@@ -1643,15 +1659,63 @@ tb_status tb_shifted_cocg(tb_handle* h, int32_t K, const double* z, int32_t R, c
     if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
     if ((s = check_cols(h, R, cols)) != TB_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // energy-point checkpointing: shifts per chunk so that x^k, p^k of the
+    // panels in flight and the device copy of the chunk's solutions fit the
+    // state budget (x_out is [K][R][N]: a chunk of shifts is one contiguous
+    // slice of it)
+    const int64_t N = h->n_orb;
+    const bool host_out = !is_device_ptr(x_out);
+    const int Pw = std::min(opts->panel ? opts->panel : 64, next_pow2(R));
+    const int inflight = std::min<int64_t>(workers_for(h), (R + Pw - 1) / Pw);
+    const double per_shift = 32.0 * (double)h->ds.npad * Pw * inflight + (host_out ? 16.0 * (double)R * N : 0.0);
+    const int Kc = (int)std::max<double>(1.0, std::min<double>(K, std::floor((double)state_budget(opts) / per_shift)));
     Cleanup cl;
     cl.st = st;
     OutBuf ob;
-    if ((s = out_prepare(cl, ob, x_out, sizeof(double2) * (size_t)K * R * h->n_orb)) != TB_OK) return s;
-    Solve q;
-    q.K = K; q.z = z; q.R = R; q.cols = cols; q.proj = PROJ_NONE;
-    q.x_out = static_cast<double2*>(ob.dev);
-    const tb_status run = run_solve(h, q, opts, stats, st);
-    return merge(run, out_finish(ob, st));
+    if ((s = out_prepare(cl, ob, x_out, sizeof(double2) * (size_t)Kc * R * N)) != TB_OK) return s;
+    const auto t0 = std::chrono::steady_clock::now();
+    tb_stats agg{};
+    std::vector<int32_t> conv;
+    bool unconverged = false;
+    for (int k0 = 0; k0 < K; k0 += Kc) {
+        const int kc = std::min(Kc, K - k0);
+        const tb_solve_opts oc = chunk_opts(opts, k0, kc);
+        Solve q;
+        q.K = kc; q.z = z + 2 * (size_t)k0; q.R = R; q.cols = cols; q.proj = PROJ_NONE;
+        q.x_out = ob.host ? static_cast<double2*>(ob.dev) : reinterpret_cast<double2*>(x_out) + (size_t)k0 * R * N;
+        tb_stats ts{};
+        if (stats && stats->conv_iter) {
+            conv.assign((size_t)R * kc, -1);
+            ts.conv_iter = conv.data();
+        }
+        const tb_status run = run_solve(h, q, &oc, stats ? &ts : nullptr, st);
+        if (run == TB_ERR_NOT_CONVERGED) unconverged = true;
+        else if (run != TB_OK) return run;
+        if (ob.host) {
+            // the chunk's solutions to the caller's host memory before the next chunk reuses the device copy
+            TB_CK(cudaMemcpyAsync(reinterpret_cast<double2*>(x_out) + (size_t)k0 * R * N, ob.dev,
+                                  sizeof(double2) * (size_t)kc * R * N, cudaMemcpyDeviceToHost, st));
+        }
+        TB_CK(cudaStreamSynchronize(st));
+        if (stats) {
+            if (stats->conv_iter)
+                for (int c = 0; c < R; ++c)
+                    for (int k = 0; k < kc; ++k) stats->conv_iter[(size_t)c * K + k0 + k] = conv[(size_t)c * kc + k];
+            agg.outer_iterations += ts.outer_iterations;
+            agg.inner_iterations += ts.inner_iterations;
+            agg.max_column_iterations = std::max(agg.max_column_iterations, ts.max_column_iterations);
+            agg.switches += ts.switches;
+            agg.unconverged += ts.unconverged;
+            agg.inner_redos += ts.inner_redos;
+        }
+    }
+    if (stats) {
+        int32_t* ci = stats->conv_iter;
+        *stats = agg;
+        stats->conv_iter = ci;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return unconverged ? TB_ERR_NOT_CONVERGED : TB_OK;
 }
 
 tb_status tb_green_elements(tb_handle* h, int32_t K, const double* z, int32_t R, const int32_t* cols,
@@ -1765,10 +1829,15 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
         if (vh[o] != 0.0) supp.push_back((int32_t)o);
     }
     const int64_t ns = (int64_t)supp.size();
-    // columns per chunk: the two full-solution panels X, Y ([K][Rc][N]) within ~2 GiB
-    const int64_t per_col = 2 * (int64_t)K * N * (int64_t)sizeof(double2);
-    const int Rc = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ns, 1),
-                                                                (int64_t)2 * 1024 * 1024 * 1024 / per_col));
+    // columns and shifts per chunk (energy-point checkpointing): the two
+    // full-solution panels X, Y ([Kc][Rc][N]) and the solver's x^k, p^k of
+    // the same shifts and columns, ~64 N bytes per (column, shift), within
+    // the state budget; all K shifts at once while one column fits, else
+    // chunks of shifts, each solved again from its own seed sequence
+    const double per_cs = 64.0 * (double)N;
+    const double budget = (double)state_budget(opts);
+    const int Rc = (int)std::max<double>(1.0, std::min<double>(std::max<int64_t>(ns, 1), std::floor(budget / (per_cs * K))));
+    const int Kc = (int)std::max<double>(1.0, std::min<double>(K, std::floor(budget / (per_cs * Rc))));
     Cleanup cl;
     cl.st = st;
     int32_t *ead, *ebd, *cpos;
@@ -1781,8 +1850,8 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
     if ((s = dalloc(cl, &gH, (size_t)nvals)) != TB_OK) return s;
     if ((s = dalloc(cl, &gS, (size_t)nvals)) != TB_OK) return s;
     if ((s = dalloc(cl, &Sc, (size_t)Rc * N)) != TB_OK) return s;
-    if ((s = dalloc(cl, &X, (size_t)K * Rc * N)) != TB_OK) return s;
-    if ((s = dalloc(cl, &Y, (size_t)K * Rc * N)) != TB_OK) return s;
+    if ((s = dalloc(cl, &X, (size_t)Kc * Rc * N)) != TB_OK) return s;
+    if ((s = dalloc(cl, &Y, (size_t)Kc * Rc * N)) != TB_OK) return s;
     if ((s = dalloc(cl, &zd, (size_t)K)) != TB_OK) return s;
     if ((s = dalloc(cl, &wd, (size_t)K)) != TB_OK) return s;
     TB_CK(cudaMemcpyAsync(ead, ea.data(), sizeof(int32_t) * nvals, cudaMemcpyHostToDevice, st));
@@ -1821,24 +1890,29 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
         TB_CK(cudaMemcpyAsync(Sc, Sh.data(), sizeof(double) * (size_t)rc * N, cudaMemcpyHostToDevice, st));
         TB_CK(cudaMemcpyAsync(cpos, cposh.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
         TB_CK(cudaMemcpyAsync(vc, vch.data(), sizeof(double) * rc, cudaMemcpyHostToDevice, st));
-        for (int pass = 0; pass < 2; ++pass) {
-            Solve q;
-            q.K = K; q.z = z; q.R = rc; q.cols = cols.data(); q.proj = PROJ_NONE;
-            q.x_out = pass == 0 ? X : Y;
-            if (pass == 1) q.rhs = Sc;
-            tb_stats ts{};
-            const tb_status run = run_view(vw, q, opts, &ts, st);
-            if (run == TB_ERR_NOT_CONVERGED) unconverged = true;
-            else if (run != TB_OK) return run;
-            agg.outer_iterations += ts.outer_iterations;
-            agg.inner_iterations += ts.inner_iterations;
-            agg.max_column_iterations = std::max(agg.max_column_iterations, ts.max_column_iterations);
-            agg.switches += ts.switches;
-            agg.unconverged += ts.unconverged;
-            agg.inner_redos += ts.inner_redos;
+        for (int k0 = 0; k0 < K; k0 += Kc) {
+            const int kc = std::min(Kc, K - k0);
+            const tb_solve_opts oc = chunk_opts(opts, k0, kc);
+            for (int pass = 0; pass < 2; ++pass) {
+                Solve q;
+                q.K = kc; q.z = z + 2 * (size_t)k0; q.R = rc; q.cols = cols.data(); q.proj = PROJ_NONE;
+                q.x_out = pass == 0 ? X : Y;
+                if (pass == 1) q.rhs = Sc;
+                tb_stats ts{};
+                const tb_status run = run_view(vw, q, &oc, &ts, st);
+                if (run == TB_ERR_NOT_CONVERGED) unconverged = true;
+                else if (run != TB_OK) return run;
+                agg.outer_iterations += ts.outer_iterations;
+                agg.inner_iterations += ts.inner_iterations;
+                agg.max_column_iterations = std::max(agg.max_column_iterations, ts.max_column_iterations);
+                agg.switches += ts.switches;
+                agg.unconverged += ts.unconverged;
+                agg.inner_redos += ts.inner_redos;
+            }
+            // this chunk's shifts add their terms of the k sums
+            launch_vjp_accumulate(X, Y, kc, rc, N, cpos, vc, ead, ebd, nvals, zd + k0, wd + k0, g_s, gH, gS, st);
+            TB_CK(cudaGetLastError());
         }
-        launch_vjp_accumulate(X, Y, K, rc, N, cpos, vc, ead, ebd, nvals, zd, wd, g_s, gH, gS, st);
-        TB_CK(cudaGetLastError());
         TB_CK(cudaStreamSynchronize(st));   // the host staging arrays are refilled for the next chunk
     }
     OutBuf oH, oS;
@@ -1858,6 +1932,49 @@ tb_status tb_mulliken_vjp(tb_handle* h, int32_t K, const double* z, const double
     return unconverged ? TB_ERR_NOT_CONVERGED : TB_OK;
 }
 
+// Every column b of the H/S pattern with the rows a of its block column, in
+// caller orbital order; element e = (a, b) also names the value index
+// val[e] of H_ab / S_ab in the caller's block layout, S_el[e] = S_ab, and the
+// atoms of a and b.
+struct PatternElems {
+    std::vector<int32_t> cols, rows, atom_a, atom_b;
+    std::vector<int64_t> row_ptr, val;
+    std::vector<double> S_el;
+};
+
+static tb_status pattern_elements(const tb_handle* h, PatternElems& pe) {
+    const int n = h->n_atoms;
+    const int64_t N = h->n_orb;
+    std::vector<int64_t> ooff(n + 1, 0);
+    for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + h->orb_per_atom[i];
+    pe.cols.assign(N, 0);
+    pe.row_ptr.assign(N + 1, 0);
+    for (int J = 0; J < n; ++J) {
+        const int nj = h->orb_per_atom[J];
+        for (int bo = 0; bo < nj; ++bo) {
+            const int64_t b = ooff[J] + bo;
+            pe.cols[b] = (int32_t)b;
+            // block column J = block row J by symmetry of the pattern
+            for (int64_t blk = h->brow_h[J]; blk < h->brow_h[J + 1]; ++blk) {
+                const int I = h->bcol_h[blk];
+                const int ni = h->orb_per_atom[I];
+                const int64_t bt = h->btrans_h[blk];       // block (I, J)
+                for (int ao = 0; ao < ni; ++ao) {
+                    pe.rows.push_back((int32_t)(ooff[I] + ao));
+                    const int64_t v = h->boff_h[bt] + (int64_t)ao * nj + bo;
+                    pe.val.push_back(v);
+                    pe.S_el.push_back(h->S_h[v]);
+                    pe.atom_a.push_back(I);
+                    pe.atom_b.push_back(J);
+                }
+            }
+            pe.row_ptr[b + 1] = (int64_t)pe.rows.size();
+            if (pe.row_ptr[b + 1] - pe.row_ptr[b] > MAX_M) return TB_ERR_INVALID_ARG;
+        }
+    }
+    return TB_OK;
+}
+
 tb_status tb_band_energy(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,
                          const tb_solve_opts* opts, double* E_out, double* dE_dH, double* dE_dS, tb_stats* stats,
                          void* stream) {
@@ -1867,37 +1984,14 @@ tb_status tb_band_energy(tb_handle* h, int32_t K, const double* z, const double*
     if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
     for (int k = 0; k < 2 * K; ++k)
         if (!std::isfinite(w[k])) return TB_ERR_INVALID_ARG;
-    // every column b with the rows a of its block column (the H/S pattern),
-    // in caller orbital order; element e = (a, b) also names value
-    // index val[e] of H_ab / S_ab in the caller's block layout
-    const int n = h->n_atoms;
     const int64_t N = h->n_orb;
-    std::vector<int64_t> ooff(n + 1, 0);
-    for (int i = 0; i < n; ++i) ooff[i + 1] = ooff[i] + h->orb_per_atom[i];
-    std::vector<int32_t> cols(N), rows;
-    std::vector<int64_t> row_ptr(N + 1, 0), val;
-    std::vector<double> S_el;
-    for (int J = 0; J < n; ++J) {
-        const int nj = h->orb_per_atom[J];
-        for (int bo = 0; bo < nj; ++bo) {
-            const int64_t b = ooff[J] + bo;
-            cols[b] = (int32_t)b;
-            // block column J = block row J by symmetry of the pattern
-            for (int64_t blk = h->brow_h[J]; blk < h->brow_h[J + 1]; ++blk) {
-                const int I = h->bcol_h[blk];
-                const int ni = h->orb_per_atom[I];
-                const int64_t bt = h->btrans_h[blk];       // block (I, J)
-                for (int ao = 0; ao < ni; ++ao) {
-                    rows.push_back((int32_t)(ooff[I] + ao));
-                    const int64_t v = h->boff_h[bt] + (int64_t)ao * nj + bo;
-                    val.push_back(v);
-                    S_el.push_back(h->S_h[v]);
-                }
-            }
-            row_ptr[b + 1] = (int64_t)rows.size();
-            if (row_ptr[b + 1] - row_ptr[b] > MAX_M) return TB_ERR_INVALID_ARG;
-        }
-    }
+    PatternElems pe;
+    if ((s = pattern_elements(h, pe)) != TB_OK) return s;
+    const std::vector<int32_t>& cols = pe.cols;
+    const std::vector<int32_t>& rows = pe.rows;
+    const std::vector<int64_t>& row_ptr = pe.row_ptr;
+    const std::vector<int64_t>& val = pe.val;
+    const std::vector<double>& S_el = pe.S_el;
     const int64_t ne = (int64_t)rows.size();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Cleanup cl;
@@ -2017,6 +2111,75 @@ tb_status tb_csc_hamiltonian(tb_handle* h, const double* gamma, const double* dq
     TB_CK(cudaGetLastError());
     TB_CK(cudaStreamSynchronize(st));
     return TB_OK;
+}
+
+tb_status tb_csc_forces(tb_handle* h, int32_t K, const double* z, const double* w, double g_s, const double* gamma,
+                        const double* dgamma, const double* dq, const double* dS_dd, const tb_solve_opts* opts,
+                        double* F_out, tb_stats* stats, void* stream) {
+    if (!h || !w || !gamma || !dgamma || !dq || !dS_dd || !F_out || !std::isfinite(g_s)) return TB_ERR_INVALID_ARG;
+    if (!h->ased) return TB_ERR_INVALID_ARG;                       // dH0/dR by Eq. Hap-1 needs eps and K
+    if (h->sys_atom_off.size() > 2) return TB_ERR_INVALID_ARG;     // one system per handle
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(w[k])) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = h->n_atoms;
+    // H = H0 + H^CSC(dq) on the handle (left there, as tb_csc_hamiltonian)
+    if ((s = tb_csc_hamiltonian(h, gamma, dq, stream)) != TB_OK) return s;
+    PatternElems pe;
+    if ((s = pattern_elements(h, pe)) != TB_OK) return s;
+    const int64_t ne = (int64_t)pe.rows.size();
+    const int64_t nvals = h->boff_h.back();
+    Cleanup cl;
+    cl.st = st;
+    const double *gd = nullptr, *dqd = nullptr, *dgd = nullptr;
+    if ((s = device_view(cl, gamma, (size_t)n * n, &gd, st)) != TB_OK) return s;
+    if ((s = device_view(cl, dq, (size_t)n, &dqd, st)) != TB_OK) return s;
+    if ((s = device_view(cl, dgamma, (size_t)n * n * 3, &dgd, st)) != TB_OK) return s;
+    double2 *G, *zd, *wd;
+    double *V, *gHe, *gSe, *gHv, *gSv, *F;
+    int32_t *aa, *ab;
+    int64_t* vald;
+    if ((s = dalloc(cl, &G, (size_t)ne * K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &zd, (size_t)K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &wd, (size_t)K)) != TB_OK) return s;
+    if ((s = dalloc(cl, &V, (size_t)n)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gHe, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gSe, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gHv, (size_t)nvals)) != TB_OK) return s;
+    if ((s = dalloc(cl, &gSv, (size_t)nvals)) != TB_OK) return s;
+    if ((s = dalloc(cl, &F, (size_t)3 * n)) != TB_OK) return s;
+    if ((s = dalloc(cl, &aa, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &ab, (size_t)ne)) != TB_OK) return s;
+    if ((s = dalloc(cl, &vald, (size_t)ne)) != TB_OK) return s;
+    TB_CK(cudaMemcpyAsync(zd, z, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(wd, w, sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(aa, pe.atom_a.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(ab, pe.atom_b.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, st));
+    TB_CK(cudaMemcpyAsync(vald, pe.val.data(), sizeof(int64_t) * ne, cudaMemcpyHostToDevice, st));
+    launch_csc_potential(gd, dqd, n, V, st);
+    Solve q;
+    q.K = K; q.z = z; q.R = (int)h->n_orb; q.cols = pe.cols.data(); q.proj = PROJ_ROWS;
+    q.row_ptr = pe.row_ptr.data(); q.rows = pe.rows.data(); q.g_out = G;
+    const tb_status run = run_solve(h, q, opts, stats, st);
+    if (run != TB_OK && run != TB_ERR_NOT_CONVERGED) return run;
+    launch_csc_force_terms(G, ne, K, zd, wd, g_s, V, aa, ab, gHe, gSe, st);
+    TB_CK(cudaMemsetAsync(gHv, 0, sizeof(double) * nvals, st));
+    TB_CK(cudaMemsetAsync(gSv, 0, sizeof(double) * nvals, st));
+    launch_scatter_values(gHe, vald, ne, gHv, st);
+    launch_scatter_values(gSe, vald, ne, gSv, st);
+    TB_CK(cudaGetLastError());
+    // the force blocks of Eq. Hap-1 with gH = rho^T and gS as above, then
+    // the Coulomb-gradient term
+    if ((s = tb_forces(h, gHv, gSv, dS_dd, nullptr, F, stream)) != TB_OK) return s;
+    launch_csc_force_coulomb(n, dgd, dqd, F, st);
+    TB_CK(cudaGetLastError());
+    OutBuf ob;
+    if ((s = out_prepare(cl, ob, F_out, sizeof(double) * 3 * (size_t)n)) != TB_OK) return s;
+    TB_CK(cudaMemcpyAsync(ob.dev, F, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    return merge(run, out_finish(ob, st));
 }
 
 tb_status tb_csc_loop(tb_handle* h, int32_t K, const double* z, const double* w, double g_s, const double* gamma,

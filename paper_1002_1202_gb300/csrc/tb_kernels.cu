@@ -1685,6 +1685,51 @@ __global__ void k_band_energy_terms(const double2* __restrict__ G, const double2
     }
 }
 
+// Per projected element e = (a, b) of the pattern (G[e K + k] = G_ab(z_k)),
+// the gradients of the charge-self-consistent free energy at fixed dq
+// (Section 2.2, Eq. Hap-CSC; the contour grand potential Omega of the
+// quadrature, whose H-derivative is the density matrix):
+//   gH_e = rho_ab = -(g_s/pi) Im sum_k w_k G_ab(z_k)
+//   gS_e = dOmega/dS_ab + rho_ab (V_I + V_J) / 2,
+//   dOmega/dS_ab = (g_s/pi) Im sum_k w_k z_k G_ab(z_k),
+// with V = gamma dq and I, J the atoms of orbitals a, b.
+__global__ void k_csc_force_terms(const double2* __restrict__ G, int64_t n, int K, const double2* __restrict__ z,
+                                  const double2* __restrict__ w, double g_s, const double* __restrict__ V,
+                                  const int32_t* __restrict__ atom_a, const int32_t* __restrict__ atom_b,
+                                  double* __restrict__ gH, double* __restrict__ gS) {
+    const double f = g_s / 3.14159265358979323846;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double ar = 0.0, az = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double2 g = G[e * K + k];
+            ar += cmul(w[k], g).y;
+            az += cmul(cmul(w[k], z[k]), g).y;
+        }
+        const double rho = -f * ar;
+        gH[e] = rho;
+        gS[e] = f * az + 0.5 * rho * (V[atom_a[e]] + V[atom_b[e]]);
+    }
+}
+
+// Coulomb-gradient part of the charge-self-consistent forces:
+// F_I -= dq_I sum_k (d gamma_Ik / d R_I) dq_k, dgamma [n][n][3]; one thread
+// per atom, the k sum in index order.
+__global__ void k_csc_force_coulomb(int n, const double* __restrict__ dgamma, const double* __restrict__ dq,
+                                    double* __restrict__ F) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        const double* row = dgamma + (size_t)i * n * 3;
+        for (int k = 0; k < n; ++k) {
+            g0 += row[3 * k] * dq[k];
+            g1 += row[3 * k + 1] * dq[k];
+            g2 += row[3 * k + 2] * dq[k];
+        }
+        F[3 * i] -= dq[i] * g0;
+        F[3 * i + 1] -= dq[i] * g1;
+        F[3 * i + 2] -= dq[i] * g2;
+    }
+}
+
 // out[0] = sum of v[0..n) in a fixed order (one CTA: strided partial sums,
 // then a tree): deterministic whatever the launch history
 __global__ void k_sum_fixed(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
@@ -2547,6 +2592,16 @@ void launch_band_energy_terms(const double2* G, const double2* dG, const double*
                               double* gS, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
     k_band_energy_terms<<<grid_for(n), THREADS, 0, st>>>(G, dG, S_el, n, K, z, w, g_s, e_terms, gH, gS);
+}
+void launch_csc_force_terms(const double2* G, int64_t n, int K, const double2* z, const double2* w, double g_s,
+                            const double* V, const int32_t* atom_a, const int32_t* atom_b, double* gH, double* gS,
+                            cudaStream_t st) {
+    LaunchScope ls_(K_CSC, st);
+    k_csc_force_terms<<<grid_for(n), THREADS, 0, st>>>(G, n, K, z, w, g_s, V, atom_a, atom_b, gH, gS);
+}
+void launch_csc_force_coulomb(int n, const double* dgamma, const double* dq, double* F, cudaStream_t st) {
+    LaunchScope ls_(K_CSC, st);
+    k_csc_force_coulomb<<<grid_for(n), THREADS, 0, st>>>(n, dgamma, dq, F);
 }
 void launch_sum_fixed(const double* v, int64_t n, double* out, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);

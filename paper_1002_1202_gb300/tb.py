@@ -65,6 +65,7 @@ class SolveOpts(C.Structure):
         ("precision", C.c_int32),
         ("inner_lo_tol", C.c_double),
         ("inner_method", C.c_int32),
+        ("state_bytes", C.c_int64),
     ]
 
 
@@ -144,6 +145,8 @@ SIGNATURES = [
     ("tb_generalized_lanczos_batch", C.c_int, [_VP, C.c_int32, _I32P, C.c_int32, C.POINTER(SolveOpts), _VP, _VP,
                                                _VP, _VP]),
     ("tb_generalized_lanczos_noalloc", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
+    ("tb_csc_forces", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, _VP, _VP, _VP, C.POINTER(SolveOpts),
+                                _VP, C.POINTER(Stats), _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
     ("tb_launch_count", C.c_int64, []),
     ("tb_profile_enable", None, [C.c_int32]),
@@ -520,6 +523,28 @@ def tb_mulliken_charges(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None,
     return out, _stats_dict(st, None, h.n_orb, K, s)
 
 
+def tb_csc_forces(h: Handle, z, w, gamma, dgamma, dq, dS_dd, g_s=2.0, opts: SolveOpts | None = None, out=None,
+                  stream=None, allow_unconverged=False):
+    """Forces (n_atoms, 3) of the charge-self-consistent model at the
+    self-consistent dq (tb_csc_loop's dq_out): gamma (n, n), dgamma (n, n, 3)
+    = d gamma_Ik / d R_I, dS_dd (3, n_values); returns (F, stats)."""
+    keep = []
+    zz = _complex_host(z)
+    ww = _complex_host(w)
+    K = len(zz) // 2
+    n = h.n_atoms
+    if out is None:
+        out = np.zeros((n, 3))
+    opts = opts or tb_default_opts()
+    st, _ = _stats(h.n_orb, K, False)
+    s = load_library().tb_csc_forces(h.ptr, K, _ptr(zz, C.c_double), _ptr(ww, C.c_double), float(g_s),
+                                     _in_ptr(gamma, n * n, keep), _in_ptr(dgamma, n * n * 3, keep),
+                                     _in_ptr(dq, n, keep), _in_ptr(dS_dd, _numel(dS_dd), keep), C.byref(opts),
+                                     _out_ptr(out), C.byref(st), _stream(stream))
+    _check(s, "tb_csc_forces", allow_unconverged)
+    return out, _stats_dict(st, None, h.n_orb, K, s)
+
+
 def tb_default_csc_opts(**kw) -> CscOpts:
     """tb_csc_opts with the library defaults, fields overridden by keyword."""
     o = CscOpts()
@@ -529,6 +554,10 @@ def tb_default_csc_opts(**kw) -> CscOpts:
             raise AttributeError(k)
         setattr(o, k, v)
     return o
+
+
+def _numel(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") else int(np.asarray(a).size)
 
 
 def _in_ptr(a, n: int, keep: list):

@@ -20,6 +20,7 @@ int main(void) {
     F(tb_solve_opts, tol); F(tb_solve_opts, inner_tol); F(tb_solve_opts, max_iter); F(tb_solve_opts, inner_max_iter);
     F(tb_solve_opts, panel); F(tb_solve_opts, seed); F(tb_solve_opts, switching); F(tb_solve_opts, force_switch_every);
     F(tb_solve_opts, precision); F(tb_solve_opts, inner_lo_tol); F(tb_solve_opts, inner_method);
+    F(tb_solve_opts, state_bytes);
     Z(tb_stats);
     F(tb_stats, conv_iter); F(tb_stats, outer_iterations); F(tb_stats, inner_iterations);
     F(tb_stats, max_column_iterations); F(tb_stats, switches); F(tb_stats, unconverged); F(tb_stats, seconds);

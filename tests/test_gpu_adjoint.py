@@ -287,22 +287,18 @@ def test_slab_cutout_adjoint_vs_dense(P, slab, prec):
     assert np.abs(_dense_blocks(c, vS)[mask] - rS[mask]).max() <= 1e-7 * np.abs(rS).max()
 
 
-@pytest.mark.slow
-@pytest.mark.skipif(not __import__("os").environ.get("TB_SLAB_FD"),
-                    reason="128 full-slab solves; run with TB_SLAB_FD=1")
-def test_slab_mulliken_vjp_finite_differences(P, slab):
-    """L = sum_a v_a q_a with weights on 16 orbitals of the atoms nearest the
-    crack tip; dL/dH and dL/dS from the device VJP (mixed precision) at 32
-    stored H entries and 32 stored S entries of blocks within 6 A of the
-    tip, each against a central difference (h = 1e-5) of L recomputed on the
-    whole slab (FP64, outer tol 1e-12) with the entry and its transpose
-    perturbed together.  Error bound: the central difference's truncation
-    (O(h^2)) plus 2 eps / (2 h) for populations accurate to
-    eps = 1e-12 sum |v|; the test asserts 1e-5 of the largest gradient
+def _slab_vjp_finite_differences(P, s, n_each):
+    """L = sum_a v_a q_a with weights on the 16 orbitals of the 4 atoms
+    nearest the crack tip; dL/dH and dL/dS from the device VJP (mixed
+    precision) at n_each stored H entries and n_each stored S entries of
+    blocks within 6 A of the tip, each against a central difference
+    (h = 1e-5) of L recomputed on the whole slab (FP64, outer tol 1e-12) with
+    the entry and its transpose perturbed together.  Error bound: the central
+    difference's truncation (O(h^2)) plus 2 eps / (2 h) for populations
+    accurate to eps = 1e-12 sum |v|; asserted: 1e-5 of the largest gradient
     plus that rounding term.  Every solve is capped at 5000 outer
-    iterations."""
+    iterations.  128 Gauss-Legendre shifts on [-20, 5] eV + 1i eV."""
     from tbinputs import gauss_legendre_grid
-    s = slab
     z, w = gauss_legendre_grid(128, -20.0, 5.0, 1.0)
     tip = np.asarray(s.meta["tip"])
     d = s.positions - tip
@@ -330,7 +326,7 @@ def test_slab_mulliken_vjp_finite_differences(P, slab):
     rows = np.repeat(np.arange(s.n_atoms), np.diff(s.brow_ptr))
     r2 = np.einsum("ij,ij->i", d, d)
     cand = np.nonzero((rows != s.bcol) & (r2[rows] < 36.0) & (r2[s.bcol] < 36.0))[0]
-    blocks = rng.choice(cand, 64, replace=False)
+    blocks = rng.choice(cand, 2 * n_each, replace=False)
     step = 1e-5
     errs, scale = [], max(np.abs(gH).max(), np.abs(gS).max())
     for k, b in enumerate(blocks):
@@ -338,7 +334,7 @@ def test_slab_mulliken_vjp_finite_differences(P, slab):
         t = int(np.nonzero((rows == j) & (s.bcol == i))[0][0])
         ai, bj = rng.integers(0, 4, size=2)
         e, et = 16 * b + 4 * ai + bj, 16 * t + 4 * bj + ai
-        which = "H" if k < 32 else "S"
+        which = "H" if k < n_each else "S"
         D = np.zeros(len(s.S_vals))
         D[e] += 1.0
         D[et] += 1.0
@@ -351,3 +347,66 @@ def test_slab_mulliken_vjp_finite_differences(P, slab):
         errs.append((abs(fd - an), abs(an), which, fd, an))
     worst = max(errs)
     assert worst[0] <= 1e-5 * scale + 2e-12 * np.abs(v).sum() / (2 * step), worst
+
+
+def test_small_slab_mulliken_vjp_finite_differences(P):
+    """The finite-difference check of the cracked-slab workload at a bounded
+    size that runs by default: the same crack (2 A wide at the tip, opening
+    10 degrees, 0.1 A displacements) in a slab of 5 x 5 x 5 diamond cells
+    (1000 sites before the crack is cut), 8 H and 8 S entries near the tip."""
+    from tbinputs import si_slab_system
+    _slab_vjp_finite_differences(P, si_slab_system(cells=(5, 5, 5)), 8)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not __import__("os").environ.get("TB_SLAB_FD"),
+                    reason="128 full-slab solves; run with TB_SLAB_FD=1")
+def test_slab_mulliken_vjp_finite_differences(P, slab):
+    """The full cracked slab (10 x 10 x 10 cells, 7680 atoms): 32 H and 32 S
+    entries (opt-in: 128 full-slab solves)."""
+    _slab_vjp_finite_differences(P, slab, 32)
+
+
+def _block_values(s, M):
+    """The entries of a dense (N, N) matrix at the stored positions of the
+    block layout of S_vals (the inverse of _dense_blocks on the pattern)."""
+    oo = s.orb_offset()
+    bo = s.block_offsets()
+    out = np.zeros(len(s.S_vals))
+    for i in range(s.n_atoms):
+        ni = s.orb_per_atom[i]
+        for b in range(s.brow_ptr[i], s.brow_ptr[i + 1]):
+            j = s.bcol[b]
+            nj = s.orb_per_atom[j]
+            out[bo[b]:bo[b + 1]] = M[oo[i]:oo[i] + ni, oo[j]:oo[j] + nj].ravel()
+    return out
+
+
+@pytest.mark.parametrize("per_orbital", [False, True], ids=["atoms", "orbitals"])
+def test_mulliken_autograd_function(P, per_orbital):
+    """The torch.autograd Function of the Mulliken populations: forward
+    against the oracle's dense populations, backward (a random incoming
+    gradient) against the dense G S D_v G contraction with v the incoming
+    gradient spread over each atom's orbitals (or taken per orbital), on
+    every stored entry; water with ragged 4x1 / 1x4 / 1x1 blocks."""
+    import torch
+    from paper_1002_1202_gb300.autograd import mulliken_charges
+    s = water_system(8, seed=4, cutoff=3.0, excess_proton=True)
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    z, w = linspace_grid(16, -40.0, -8.0, 1.0)
+    Sv = torch.tensor(s.S_vals, dtype=torch.float64, device="cuda", requires_grad=True)
+    Hv = torch.tensor(_block_values(s, H), dtype=torch.float64, device="cuda", requires_grad=True)
+    q = mulliken_charges((s.orb_per_atom, s.brow_ptr, s.bcol), Sv, Hv, z, w, per_orbital=per_orbital)
+    q_orb = dense.mulliken_orbital(H, S, z, w, 2.0)
+    qd = q_orb if per_orbital else dense.mulliken_atom(q_orb, s.orbital_atom(), s.n_atoms)
+    assert np.abs(q.detach().cpu().numpy() - qd).max() <= 1e-8 * np.abs(qd).max()
+    u = np.random.default_rng(12).standard_normal(len(qd))
+    (q * torch.tensor(u, device="cuda")).sum().backward()
+    v = u if per_orbital else np.repeat(u, s.orb_per_atom)
+    gHd, gSd = dense.mulliken_vjp(H, S, z, w, v)
+    mask = _dense_blocks(s, np.ones(len(s.S_vals))) > 0
+    gH = _dense_blocks(s, Hv.grad.cpu().numpy())
+    gS = _dense_blocks(s, Sv.grad.cpu().numpy())
+    assert np.abs(gH[mask] - gHd[mask]).max() <= 1e-7 * np.abs(gHd).max()
+    assert np.abs(gS[mask] - gSd[mask]).max() <= 1e-7 * np.abs(gSd).max()

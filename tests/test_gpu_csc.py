@@ -101,3 +101,43 @@ def test_csc_invalid_arguments(P, w8):
             P.tb_csc_loop(h, z[:4], w[:4], gamma, q_ref, copts=P.tb_default_csc_opts(**kw))
     with pytest.raises(ValueError):
         P.tb_csc_hamiltonian(h, gamma[:3], np.zeros(s.n_atoms))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_csc_forces_match_oracle(P, w8, w8_loop, prec):
+    """Forces of the charge-self-consistent model on the device
+    (tb_csc_forces) against the oracle's scc_forces at the oracle loop's
+    self-consistent dq: every component to 1e-7 of the largest, zero net
+    force; the handle is left at H0 + H^CSC(dq)."""
+    from tbinputs import overlap_bond_derivatives, klopman_ohno_gamma_gradient
+    s, S, oa, H0, gamma, q_ref, z, w = w8
+    dq = w8_loop["dq"]
+    dS = overlap_bond_derivatives(s)
+    dg = 0.25 * klopman_ohno_gamma_gradient(s)
+    ref = csc.scc_forces(H0, S, oa, gamma, dg, q_ref, dq, z, w, dS, s.orb_per_atom, s.brow_ptr, s.bcol, s.eps, s.K)
+    h = P.tb_create_system(s)
+    F, st = P.tb_csc_forces(h, z, w, gamma, dg, dq, dS, opts=P.tb_default_opts(precision=prec))
+    assert st["status"] == "TB_OK"
+    scale = np.abs(ref).max()
+    assert np.abs(F - ref).max() <= 1e-7 * scale
+    assert np.abs(F.sum(axis=0)).max() <= 1e-8 * scale
+    q, _ = P.tb_mulliken_charges(h, z, w, opts=P.tb_default_opts(precision=prec))
+    assert np.abs(q.cpu().numpy() - w8_loop["q"]).max() <= 1e-7
+
+
+def test_csc_forces_without_coulomb_gradient_differ(P, w8, w8_loop):
+    """The Coulomb-gradient term matters: with dgamma = 0 the device forces
+    equal the oracle's forces without that term and differ from the full
+    ones."""
+    from tbinputs import overlap_bond_derivatives, klopman_ohno_gamma_gradient
+    s, S, oa, H0, gamma, q_ref, z, w = w8
+    dq = w8_loop["dq"]
+    dS = overlap_bond_derivatives(s)
+    dg = 0.25 * klopman_ohno_gamma_gradient(s)
+    h = P.tb_create_system(s)
+    F0, _ = P.tb_csc_forces(h, z, w, gamma, np.zeros_like(dg), dq, dS)
+    ref0 = csc.scc_forces(H0, S, oa, gamma, np.zeros_like(dg), q_ref, dq, z, w, dS, s.orb_per_atom, s.brow_ptr,
+                          s.bcol, s.eps, s.K)
+    full = csc.scc_forces(H0, S, oa, gamma, dg, q_ref, dq, z, w, dS, s.orb_per_atom, s.brow_ptr, s.bcol, s.eps, s.K)
+    assert np.abs(F0 - ref0).max() <= 1e-7 * np.abs(ref0).max()
+    assert np.abs(F0 - full).max() > 1e-4 * np.abs(full).max()
