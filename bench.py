@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--panel", type=int, default=0, help="RHS per panel; 0 = autotune over 64/128/256")
+    ap.add_argument("--panel", type=int, default=0,
+                    help="RHS per panel; 0 = the library autotuner (tb_autotune) picks panel width, panels in "
+                         "flight and Chebyshev-step form")
     ap.add_argument("--iters", type=int, default=40, help="outer iterations per step")
     ap.add_argument("--panels-per-step", type=int, default=4,
                     help="panels of columns per step; the library keeps up to four panels of one system in flight")
@@ -426,11 +428,18 @@ KERNEL_INFO = {
 }
 
 
-def cheb_kernel_name(panel):
-    """The Chebyshev step's kernel: four columns per thread with packed FMAs
-    for panels of 4 columns or more, else (or with TB_CHEB_CPT=2) the
-    two-columns-per-thread form."""
-    if os.environ.get("TB_CHEB_CPT") == "2" or panel < 4:
+# columns per thread of the Chebyshev step that the autotuner chose (None:
+# the library default)
+CHEB_CPT = None
+
+
+def cheb_kernel_name(panel, n_atoms):
+    """The Chebyshev step's kernel, as the library picks it: the autotuner's
+    choice, else TB_CHEB_CPT, else four columns per thread with packed FMAs
+    (panels narrower than 4 columns: two)."""
+    env = os.environ.get("TB_CHEB_CPT")
+    cpt = CHEB_CPT if CHEB_CPT else (int(env) if env else 4)
+    if cpt == 2 or panel < 4:
         return "k_inner32_cheb"
     return "k_inner32_cheb4"
 
@@ -451,7 +460,7 @@ def roofline_for(kname, ms, launches, s, panel, peaks, mixed=False, busy_ms=None
     FP32 lane-instruction), not against the FP64 units they do not use."""
     kern, mb, vb, fp64 = KERNEL_INFO[kname]
     if kname == "inner32_cheb":
-        kern = cheb_kernel_name(panel)
+        kern = cheb_kernel_name(panel, s.n_atoms)
     double_float = mixed and kname in ("outer_spmm", "refine_residual")
     nnz = 16 * s.nb
     mats = 2 if kname == "outer_spmm" else 1
@@ -524,28 +533,25 @@ def run_ours(args):
     prec = 1 if args.precision == "mixed" else 0
     inner_method = P.tb.TB_INNER_CG if args.inner_method == "cg" else P.tb.TB_INNER_CHEBYSHEV
     tune = None
+    run_panel = args.panel
     if args.panel == 0:
-        # panel-width autotune: 3 outer iterations per candidate, best rate wins
-        tune = {}
-        for cand in (64, 128, 256):
-            o_t = P.tb_default_opts(max_iter=3, panel=cand, tol=args.tol, precision=prec, inner_tol=args.inner_tol,
-                                    inner_method=inner_method)
-            c_t = rank_columns(s.n_orb, cand * args.panels_per_step, rank)
-            P.tb_mulliken_orbital(h, z, w, c_t, 2.0, opts=o_t, allow_unconverged=True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            P.tb_mulliken_orbital(h, z, w, c_t, 2.0, opts=o_t, allow_unconverged=True)
-            torch.cuda.synchronize()
-            tune[cand] = K_SHIFTS * len(c_t) * 3 / (time.perf_counter() - t0)
-        best = max(tune, key=tune.get)
+        # the library's autotuner: panel width, panels in flight and the
+        # Chebyshev-step form, 3 outer iterations per candidate; the best is
+        # kept in the handle and used by the calls below (panel 0)
+        o_t = P.tb_default_opts(tol=args.tol, precision=prec, inner_tol=args.inner_tol, inner_method=inner_method)
+        tune = P.tb_autotune(h, z, w, 2.0, opts=o_t, iters=3)
+        best = tune[0]["panel"]
+        global CHEB_CPT
+        CHEB_CPT = tune[0]["cheb_cpt"] or None
         if world > 1:
             t = torch.tensor([best], device="cuda", dtype=torch.int64)
             dist.broadcast(t, 0)
             best = int(t.item())
+            run_panel = best       # ranks agree on one explicit width
         args.panel = best
     cols = rank_columns(s.n_orb, args.panel * args.panels_per_step, rank)
     ncols = len(cols)
-    opts = P.tb_default_opts(max_iter=args.iters, panel=args.panel, tol=args.tol, precision=prec,
+    opts = P.tb_default_opts(max_iter=args.iters, panel=run_panel, tol=args.tol, precision=prec,
                              inner_tol=args.inner_tol, inner_method=inner_method)
     q_dev = torch.empty(ncols, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -669,7 +675,7 @@ def run_ours(args):
         "config": config_dict(args, s), "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "roofline": roofline, "roofline_other_kernels": others, "active_shift_value": active_value,
         "kernel_ms": share, "spmm_hbm": spmm_hbm, "other_precision": compare, "peaks": peaks,
-        "panel_autotune": {str(k): v for k, v in tune.items()} if tune else None,
+        "autotune": tune,
         "inner_redos": sum(st["inner_redos"] for st in stats),
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
                                        / max(1, sum(st["max_column_iterations"] + 1 for st in stats))),

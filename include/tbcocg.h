@@ -237,6 +237,38 @@ tb_status tb_shifted_cocg(tb_handle *h, int32_t K, const double *z, int32_t R, c
                           const tb_solve_opts *opts, double *x_out, tb_stats *stats, void *stream);
 
 /*
+ * Launch autotuner (no counterpart in the paper: a choice of how the work of
+ * a call is laid out on the GPU, not of what it computes).  For this
+ * handle's system and the shift set z (K shifts) it times, for
+ * `iters` outer iterations of Mulliken-projected solves with weights w
+ * (tb_mulliken_orbital's work), every candidate of
+ *   panel width P in {32, 64, 128, 256} (not above the orbital count),
+ *   panels in flight (worker streams) in {2, 4}, and, on the mixed path
+ *   with Chebyshev corrections, the Chebyshev-step form: 4 complex columns
+ *   per thread at 3 resident CTAs per SM, or 2 at 4 CTAs per SM,
+ * on P x (panels in flight) columns spread evenly over the system (an
+ * untimed call first builds the graphs and the spectrum bounds; CUDA events
+ * on `stream` time the second).  The best choice is kept in the handle for
+ * the size class (opts->precision, opts->inner_method, K rounded up to a
+ * power of two): later calls with opts->panel == 0 use its panel width,
+ * panels in flight and step form.  out[0 .. *n_out) receives the candidates
+ * ordered by rate, best first (at most max_out).  Other fields of opts
+ * (tolerances, precision) apply to the trial solves; max_iter is replaced by
+ * iters.  Status as tb_mulliken_orbital (not converging within iters is
+ * expected and not an error).
+ */
+typedef struct {
+    int32_t panel;        /* right-hand sides per panel                          */
+    int32_t streams;      /* panels in flight                                    */
+    int32_t cheb_cpt;     /* complex columns per thread of the Chebyshev step (0: not used) */
+    int32_t ctas_per_sm;  /* resident CTAs per SM of that step (0: not used)     */
+    double rate;          /* measured shift*RHS*iterations per second            */
+} tb_tune;
+tb_status tb_autotune(tb_handle *h, int32_t K, const double *z, const double *w, double g_s,
+                      const tb_solve_opts *opts, int32_t iters, tb_tune *out, int32_t max_out, int32_t *n_out,
+                      void *stream);
+
+/*
  * Selected Green's-function elements (Eq. GreensFunc) with the shifted
  * solutions projected on the requested rows (no full solution is stored).
  * Column c (orbital cols[c]) asks for rows rows[row_ptr[c] .. row_ptr[c+1]-1]

@@ -60,6 +60,15 @@ struct tb_handle {
     int32_t* orb2pad_local = nullptr;      // device copy
     int32_t* bcol_local = nullptr;         // device [nb]: block column local to its system
     int* flags_pool = nullptr;             // pinned [NPOOL][NFLAGS]: status words of the worker threads
+    // tb_autotune's choices, per size class (precision, correction method,
+    // shift count rounded up to a power of two)
+    struct Tuned {
+        int prec, method, kb;
+        int panel, streams, cpt;
+        double rate;
+    };
+    std::mutex tune_mu;
+    std::vector<Tuned> tuned;
     // spectrum of S (Chebyshev corrections of TB_MIXED): bounds [s_lo, s_hi]
     // from a Lanczos run on the host, computed once on first use
     std::once_flag s_once;
@@ -163,6 +172,9 @@ struct Solve {
     const double* rhs = nullptr;        // device [R][N] real right-hand sides (caller order) instead
                                         // of e_j; whole-system views only
     double* q_out = nullptr;            // srow, per column
+    // launch choices (0: the handle's tuned value, else the default)
+    int streams = 0;                    // panels in flight
+    int cheb_cpt = 0;                   // columns per thread of the Chebyshev step
 };
 
 // What one solve sees of a system: the device arrays (a whole handle, or one
@@ -492,18 +504,25 @@ static const bool g_graphs = [] {
     return !(e && std::atoi(e) == 0);
 }();
 
+// first_round > 0 continues a solve whose first rounds already ran (their
+// residual and right-hand side of the next round in place).  capture: only
+// enqueue the planned rounds (Chebyshev rounds, whose steps are launched
+// one by one into the caller's capture) and return before the host reads
+// the status -- the caller reads it after the captured graph ran.
 tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_max, int& pred32,
                       int& rounds_pred, int64_t& inner_total, const ChebPlan& cp, cudaGraphExec_t* graph,
-                      cudaStream_t st) {
+                      cudaStream_t st, int first_round = 0, bool capture = false) {
     // Chebyshev corrections for the first rounds (no host round trip); a
     // solve that needs more rounds than that finishes with FP32 CG
     auto cheb_round = [&](int round) { return cp.n > 0 && round < 3; };
-    launch_refine_start(v.ds, p, b, st);
-    launch_refine_scale(v.ds, p, b, cheb_round(0) ? cp.gamma : 0.f, st);   // f and d_1
-    for (int round = 0;; ++round) {
+    if (first_round == 0) {
+        launch_refine_start(v.ds, p, b, st);
+        launch_refine_scale(v.ds, p, b, cheb_round(0) ? cp.gamma : 0.f, st);   // f and d_1
+    }
+    for (int round = first_round;; ++round) {
         if (cheb_round(round)) {
             const int n = cp.steps(round);
-            cudaGraphExec_t* gr = graph ? &graph[n == cp.n ? 0 : 1] : nullptr;
+            cudaGraphExec_t* gr = graph && !capture ? &graph[n == cp.n ? 0 : 1] : nullptr;
             if (g_graphs && gr && !*gr && n > 2) cheb_graph_build(v.ds, p, cp.omega.data(), n, cp.gamma, gr);
             if (gr && *gr) {
                 cheb_graph_launch(*gr, n - 1, st);
@@ -571,6 +590,7 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
                          v.flags_host[5], smin, smax);
         }
         if (round + 1 >= rounds_pred) {
+            if (capture) return TB_OK;
             TB_CK(cudaGetLastError());
             TB_CK(cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st));
             TB_CK(cudaStreamSynchronize(st));
@@ -615,13 +635,23 @@ tb_status inner_ctx_init(const View& v, const tb_solve_opts* o, InnerCtx& ic) {
     return TB_OK;
 }
 
+tb_status inner_redo(View& v, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic, cudaStream_t st);
+
+// first_round > 0: the mixed solve's first rounds already ran (a captured
+// outer step) and their status said that more are needed.
 tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic,
-                      cudaStream_t st) {
+                      cudaStream_t st, int first_round = 0) {
     ic.res_exact = false;
     if (!p.mixed) return inner_cg(v, p, inner_max, ic.pred, ic.total, st);
-    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, ic.cheb_graph, st);
+    tb_status s = mixed_inner(v, p, b, inner_max, ic.pred32, ic.rounds, ic.total, ic.cheb, ic.cheb_graph, st,
+                              first_round);
     if (s == TB_OK) ic.res_exact = b == p.Rcur;
     if (s != TB_ERR_BREAKDOWN && s != TB_ERR_NOT_CONVERGED) return s;
+    return inner_redo(v, p, b, inner_max, ic, st);
+}
+
+tb_status inner_redo(View& v, const PanelDev& p, const double2* b, int inner_max, InnerCtx& ic, cudaStream_t st) {
+    ic.res_exact = false;
     ic.cheb.n = 0;   // the rest of this solve uses the FP32 CG corrections
     // The FP32 corrections failed to converge (or produced a non-finite
     // residual): redo this inner solve with the FP64 CG, on the device.
@@ -633,7 +663,7 @@ tb_status inner_solve(View& v, const PanelDev& p, const double2* b, int inner_ma
     const int keep = v.flags_host[0] & ~ERR_INNER;
     TB_CK(cudaMemcpyAsync(p.flags, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
     TB_CK(cudaMemcpyAsync(p.Rin, b, sizeof(double2) * (size_t)p.npad * p.P, cudaMemcpyDeviceToDevice, st));
-    s = inner_cg(v, p, inner_max, ic.pred, ic.total, st);
+    const tb_status s = inner_cg(v, p, inner_max, ic.pred, ic.total, st);
     if (s != TB_OK) return s;
     launch_split_panel(p, st);
     TB_CK(cudaGetLastError());
@@ -682,6 +712,77 @@ tb_status alloc_inner_workspace(Cleanup& cl, PanelDev& p, cudaStream_t st) {
     return TB_OK;
 }
 
+// TB_STEP_GRAPHS=0 in the environment runs the outer steps launch by launch
+static const bool g_step_graphs = [] {
+    const char* e = std::getenv("TB_STEP_GRAPHS");
+    return !(e && std::atoi(e) == 0);
+}();
+
+// One outer step of a panel on the mixed path with Chebyshev corrections as
+// a CUDA graph: the end of step n-1 (rho_{n+1}, the shift step with seed
+// switching, and in full mode the x^k, p^k update) and step n up to its
+// inner solve (the seed SpMM, r_{n+1}, the planned refinement rounds with
+// their Chebyshev steps), then the read of the panel's status words into
+// pinned host memory.  Every argument of every launch is fixed for the
+// panel (the kernels take the step's scalars from device memory), so the
+// graph is captured once and replayed each step with one launch and one
+// host synchronisation.  Each captured launch has its own event pair inside
+// the graph (external event nodes), so kernel classes are timed per launch
+// as with direct launches.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    GraphProf prof;
+    int rounds = 0;          // planned refinement rounds the graph holds
+    int64_t inner_steps = 0; // their Chebyshev steps
+    bool failed = false;     // capture failed once: launch directly
+    StepGraph() = default;
+    StepGraph(const StepGraph&) = delete;
+    StepGraph& operator=(const StepGraph&) = delete;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        graph_prof_release(prof);
+    }
+    ~StepGraph() { reset(); }
+};
+
+bool step_graph_build(View& v, PanelDev& p, InnerCtx& ic, int proj, int inner_max, StepGraph& sg) {
+    sg.reset();
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        graph_prof_begin(&sg.prof);
+        launch_finish(v.ds, p, cs);
+        launch_shift_step(v.ds, p, cs);
+        if (proj == PROJ_NONE) launch_full_update(v.ds, p, cs);
+        launch_outer_spmm(v.ds, p, true, cs);
+        launch_outer_update(v.ds, p, cs);
+        int pred32 = ic.pred32, rounds = ic.rounds;
+        int64_t steps = 0;
+        mixed_inner(v, p, p.Rcur, inner_max, pred32, rounds, steps, ic.cheb, nullptr, cs, 0, true);
+        cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, cs);
+        graph_prof_end();
+        ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g != nullptr;
+        sg.inner_steps = steps;
+    }
+    if (ok) ok = cudaGraphInstantiate(&sg.exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+        cudaGetLastError();
+        sg.reset();
+        sg.failed = true;
+        return false;
+    }
+    sg.rounds = ic.rounds;
+    return true;
+}
+
 tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
     const auto t0 = std::chrono::steady_clock::now();
     const int K = q.K, R = q.R;
@@ -716,6 +817,7 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
     p.force_switch_every = o->force_switch_every;
     p.mixed = o->precision == TB_MIXED ? 1 : 0;
     p.inner_lo_tol = o->inner_lo_tol;
+    p.cheb_cpt = q.cheb_cpt;
     const size_t nv = (size_t)npad * P;
     tb_status s;
     if ((s = alloc_inner_workspace(cl, p, st)) != TB_OK) return s;
@@ -761,6 +863,7 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
     int switches = 0, unconverged = 0, errbits = 0;
     InnerCtx ic;
     if ((s = inner_ctx_init(v, o, ic)) != TB_OK) return s;
+    StepGraph sg;
     tb_status final_status = TB_OK;
 
     for (int c0 = 0; c0 < R; c0 += P) {
@@ -806,16 +909,53 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
         launch_shift_init(v.ds, p, st);
         TB_CK(cudaGetLastError());
 
+        // step n: the end of step n-1 (rho, the shift step, full-mode
+        // update: the "tail"), the seed SpMM and r_{n+1}, the inner solve;
+        // then the host reads how many columns are still active.  On the
+        // mixed path with Chebyshev corrections a step after the first is
+        // one replay of the panel's step graph.
         int active = ncols;
-        for (int n = 0; n < o->max_iter && active > 0; ++n) {
-            launch_outer_spmm(v.ds, p, ic.res_exact, st);
-            launch_outer_update(v.ds, p, st);
-            s = inner_solve(v, p, p.Rcur, o->inner_max_iter, ic, st);
-            if (s != TB_OK) return s;
+        bool tail_pending = false;
+        for (int n = 0; n < o->max_iter; ++n) {
+            const bool use_graph = tail_pending && g_graphs && g_step_graphs && !g_trace && p.mixed &&
+                                   ic.cheb.n > 0 && ic.rounds <= 3 && ic.res_exact && !sg.failed;
+            if (use_graph && (!sg.exec || sg.rounds != ic.rounds))
+                step_graph_build(v, p, ic, q.proj, o->inner_max_iter, sg);
+            if (use_graph && sg.exec) {
+                graph_prof_launched(sg.prof);
+                TB_CK(cudaGraphLaunch(sg.exec, st));
+                TB_CK(cudaStreamSynchronize(st));
+                prof_harvest();
+                ic.total += sg.inner_steps;
+                // the planned rounds ran: what the inner solve does after its
+                // host check (redo in FP64 after a non-finite residual, more
+                // rounds while some real column is above inner_tol)
+                if (v.flags_host[0] & ERR_INNER) s = inner_redo(v, p, p.Rcur, o->inner_max_iter, ic, st);
+                else if (v.flags_host[4] > 0) s = inner_solve(v, p, p.Rcur, o->inner_max_iter, ic, st, ic.rounds);
+                else {
+                    ic.res_exact = true;
+                    s = TB_OK;
+                }
+                if (s != TB_OK) return s;
+            } else {
+                if (tail_pending) {
+                    launch_finish(v.ds, p, st);
+                    launch_shift_step(v.ds, p, st);
+                    if (q.proj == PROJ_NONE) launch_full_update(v.ds, p, st);
+                }
+                launch_outer_spmm(v.ds, p, ic.res_exact, st);
+                launch_outer_update(v.ds, p, st);
+                s = inner_solve(v, p, p.Rcur, o->inner_max_iter, ic, st);
+                if (s != TB_OK) return s;
+            }
+            tail_pending = false;
             active = v.flags_host[2];     // columns still active after step n-1
             errbits |= v.flags_host[0];
             if (errbits & ERR_NOT_SPD) return TB_ERR_S_NOT_SPD;
             if (active == 0) break;
+            tail_pending = true;
+        }
+        if (tail_pending) {   // max_iter ran out: the last step's tail
             launch_finish(v.ds, p, st);
             launch_shift_step(v.ds, p, st);
             if (q.proj == PROJ_NONE) launch_full_update(v.ds, p, st);
@@ -1069,14 +1209,30 @@ int workers_for(const tb_handle* h) {
     return h->sys_ds.empty() ? 4 : 8;
 }
 
-tb_status run_solve(tb_handle* h, const Solve& q, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
-    const int Pw = std::min(o->panel ? o->panel : 64, next_pow2(q.R));
-    const int nw = workers_for(h);
+// The tuned choices of this handle for a call (nullptr: none).
+const tb_handle::Tuned* tuned_for(tb_handle* h, const tb_solve_opts* o, int K) {
+    std::lock_guard<std::mutex> lk(h->tune_mu);
+    const int kb = next_pow2(K);
+    for (const auto& t : h->tuned)
+        if (t.prec == o->precision && t.method == o->inner_method && t.kb == kb) return &t;
+    return nullptr;
+}
+
+tb_status run_solve(tb_handle* h, const Solve& q0, const tb_solve_opts* o, tb_stats* stats, cudaStream_t st) {
+    // automatic choices: the handle's tuned panel width, panels in flight and
+    // Chebyshev-step form for this size class, else the defaults
+    Solve q = q0;
+    tb_solve_opts oe = *o;
+    const tb_handle::Tuned* t = o->panel == 0 ? tuned_for(h, o, q.K) : nullptr;
+    if (t) oe.panel = t->panel;
+    if (q.cheb_cpt == 0 && t) q.cheb_cpt = t->cpt;
+    const int nw = q.streams ? q.streams : (t ? t->streams : workers_for(h));
+    const int Pw = std::min(oe.panel ? oe.panel : 64, next_pow2(q.R));
     if (h->sys_ds.empty() && (nw == 1 || q.R <= Pw)) {
         View v = whole_view(h);
-        return run_view(v, q, o, stats, st);
+        return run_view(v, q, &oe, stats, st);
     }
-    return run_jobs(h, q, o, stats, st, nw);
+    return run_jobs(h, q, &oe, stats, st, nw);
 }
 
 tb_status check_cols(const tb_handle* h, int R, const int32_t* cols) {
@@ -1648,6 +1804,95 @@ tb_status tb_batch_offsets(const tb_handle* h, int64_t* atom_off, int64_t* orb_o
     if (!h) return TB_ERR_INVALID_ARG;
     if (atom_off) std::memcpy(atom_off, h->sys_atom_off.data(), sizeof(int64_t) * h->sys_atom_off.size());
     if (orb_off) std::memcpy(orb_off, h->sys_orb_off.data(), sizeof(int64_t) * h->sys_orb_off.size());
+    return TB_OK;
+}
+
+tb_status tb_autotune(tb_handle* h, int32_t K, const double* z, const double* w, double g_s,
+                      const tb_solve_opts* opts, int32_t iters, tb_tune* out, int32_t max_out, int32_t* n_out,
+                      void* stream) {
+    if (!h || !w || !out || max_out < 1 || iters < 1 || !std::isfinite(g_s)) return TB_ERR_INVALID_ARG;
+    tb_status s;
+    if ((s = check_opts(opts)) != TB_OK) return s;
+    if ((s = check_shifts(K, z, opts)) != TB_OK) return s;
+    for (int k = 0; k < 2 * K; ++k)
+        if (!std::isfinite(w[k])) return TB_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t N = h->n_orb;
+    const bool cheb = opts->precision == TB_MIXED && opts->inner_method == TB_INNER_CHEBYSHEV;
+    std::vector<tb_tune> cand;
+    for (int P : {32, 64, 128, 256}) {
+        if (P > next_pow2((int)std::min<int64_t>(N, 1 << 30)) && P > 32) continue;
+        for (int nw : {2, 4})
+            for (int cpt : {4, 2}) {
+                if (!cheb && cpt == 2) continue;
+                tb_tune t;
+                t.panel = P;
+                t.streams = nw;
+                t.cheb_cpt = cheb ? cpt : 0;
+                t.ctas_per_sm = cheb ? (cpt == 4 ? 3 : 4) : 0;
+                t.rate = 0.0;
+                cand.push_back(t);
+            }
+    }
+    Cleanup cl;
+    cl.st = st;
+    double* qd = nullptr;
+    const int Rmax = (int)std::min<int64_t>(N, 4 * 256);
+    if ((s = dalloc(cl, &qd, (size_t)Rmax)) != TB_OK) return s;
+    cudaEvent_t e0, e1;
+    TB_CK(cudaEventCreate(&e0));
+    TB_CK(cudaEventCreate(&e1));
+    for (auto& t : cand) {
+        // as many panels as are kept in flight, columns spread over the system
+        const int R = (int)std::min<int64_t>(N, (int64_t)t.panel * t.streams);
+        std::vector<int32_t> cols(R);
+        for (int c = 0; c < R; ++c) cols[c] = (int32_t)(((int64_t)c * N) / R);
+        tb_solve_opts oc = *opts;
+        oc.panel = t.panel;
+        oc.max_iter = iters;
+        Solve q;
+        q.K = K; q.z = z; q.R = R; q.cols = cols.data(); q.proj = PROJ_SROW; q.w = w; q.g_s = g_s; q.q_out = qd;
+        q.streams = t.streams;
+        q.cheb_cpt = t.cheb_cpt;
+        // the first call builds the graphs and the spectrum bounds; the second is timed
+        tb_status r = run_solve(h, q, &oc, nullptr, st);
+        if (r != TB_OK && r != TB_ERR_NOT_CONVERGED) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return r;
+        }
+        TB_CK(cudaEventRecord(e0, st));
+        r = run_solve(h, q, &oc, nullptr, st);
+        TB_CK(cudaEventRecord(e1, st));
+        TB_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TB_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (r != TB_OK && r != TB_ERR_NOT_CONVERGED) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return r;
+        }
+        t.rate = ms > 0.f ? (double)K * R * iters / (ms * 1e-3) : 0.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::stable_sort(cand.begin(), cand.end(), [](const tb_tune& a, const tb_tune& b) { return a.rate > b.rate; });
+    const tb_tune& best = cand.front();
+    {
+        std::lock_guard<std::mutex> lk(h->tune_mu);
+        const int kb = next_pow2(K);
+        tb_handle::Tuned t{opts->precision, opts->inner_method, kb, best.panel, best.streams, best.cheb_cpt, best.rate};
+        bool found = false;
+        for (auto& x : h->tuned)
+            if (x.prec == t.prec && x.method == t.method && x.kb == t.kb) {
+                x = t;
+                found = true;
+            }
+        if (!found) h->tuned.push_back(t);
+    }
+    const int n = std::min<int>(max_out, (int)cand.size());
+    for (int i = 0; i < n; ++i) out[i] = cand[i];
+    if (n_out) *n_out = n;
     return TB_OK;
 }
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace tb {
 
 constexpr int THREADS = 256;   // every kernel runs 256-thread CTAs
@@ -91,6 +93,7 @@ struct PanelDev {
     int P = 0, K = 0, npad = 0, M = 0, proj = PROJ_NONE;
     int grid = 0;                 // CTAs of the grid-stride kernels
     int mixed = 0;                // 1: inner S^-1 by FP32 corrections inside FP64 refinement
+    int cheb_cpt = 0;             // host side: columns per thread of the Chebyshev step (2 or 4; 0 = default)
     double tol = 1e-10, inner_tol = 1e-13, inner_lo_tol = 1e-6;
     int switching = 1, force_switch_every = 0;
     // panel vectors, [npad][P] complex
@@ -135,6 +138,18 @@ enum { K_INNER_SPMV = 0, K_INNER_UPDATE, K_OUTER_SPMM, K_OUTER_UPDATE, K_FINISH,
        K_COUNT };
 void profile_enable(bool on);
 void prof_harvest();
+// launch accounting of a captured graph: the event pairs recorded by its
+// nodes (one per captured launch) and the kernels each launch runs
+struct GraphProf {
+    std::vector<size_t> pairs;          // timed launches (profiling on at capture)
+    std::vector<int> counts;
+    std::vector<int> untimed_kid;       // launches captured with profiling off
+    std::vector<int> untimed_counts;
+};
+void graph_prof_begin(GraphProf* gp);   // this thread's next captured launches get pairs in gp
+void graph_prof_end();
+void graph_prof_launched(const GraphProf& gp);
+void graph_prof_release(GraphProf& gp);
 void profile_read(int id, int64_t* launches, double* ms);
 double profile_busy(int id);
 int64_t launch_count();

@@ -2142,6 +2142,7 @@ struct Profiler {
     std::vector<std::thread::id> owner;   // thread that recorded the pair
     std::vector<size_t> free_pairs;
     std::vector<size_t> stopped;          // recorded, not yet harvested
+    std::vector<char> in_graph;           // the pair is recorded by nodes of a captured graph
     std::atomic<int64_t> launches[K_COUNT] = {};
     double ms[K_COUNT] = {};
     std::atomic<int64_t> total{0};
@@ -2156,31 +2157,62 @@ Profiler g_prof;
 // set while this thread captures launches into a CUDA graph: they run (and
 // are counted and timed) when the graph is launched
 thread_local bool g_capturing = false;
+// set while this thread captures an outer step (capture_step_*): every
+// captured launch gets its own event pair, recorded by event nodes inside
+// the graph, and is counted and timed at each launch of the graph
+thread_local GraphProf* g_cap_prof = nullptr;
+thread_local bool g_cap_timed = false;
+
+static size_t new_pair_locked() {
+    if (g_prof.free_pairs.empty()) {
+        cudaEvent_t e[2];
+        if (cudaEventCreate(&e[0]) != cudaSuccess || cudaEventCreate(&e[1]) != cudaSuccess) {
+            cudaGetLastError();
+            return (size_t)-1;
+        }
+        g_prof.ev.push_back(e[0]);
+        g_prof.ev.push_back(e[1]);
+        g_prof.kid.push_back(0);
+        g_prof.owner.push_back(std::thread::id());
+        g_prof.in_graph.push_back(0);
+        g_prof.free_pairs.push_back(g_prof.kid.size() - 1);
+    }
+    const size_t pr = g_prof.free_pairs.back();
+    g_prof.free_pairs.pop_back();
+    return pr;
+}
 
 struct LaunchScope {
     cudaStream_t st;
     size_t pair = (size_t)-1;
+    bool graph_pair = false;
     // count: kernels this launch runs (a graph launch runs several)
     LaunchScope(int id, cudaStream_t s, int count = 1) : st(s) {
-        if (g_capturing) return;
+        if (g_capturing) {
+            if (!g_cap_prof) return;
+            if (!g_cap_timed) {
+                g_cap_prof->untimed_kid.push_back(id);
+                g_cap_prof->untimed_counts.push_back(count);
+                return;
+            }
+            std::lock_guard<std::mutex> lk(g_prof.mu);
+            pair = new_pair_locked();
+            if (pair == (size_t)-1) return;
+            graph_pair = true;
+            g_prof.kid[pair] = id;
+            g_prof.in_graph[pair] = 1;
+            g_cap_prof->pairs.push_back(pair);
+            g_cap_prof->counts.push_back(count);
+            // an external event node: the timestamp is taken at every replay
+            cudaEventRecordWithFlags(g_prof.ev[2 * pair], st, cudaEventRecordExternal);
+            return;
+        }
         g_prof.total.fetch_add(count, std::memory_order_relaxed);
         g_prof.launches[id].fetch_add(count, std::memory_order_relaxed);
         if (!g_prof.on) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
-        if (g_prof.free_pairs.empty()) {
-            cudaEvent_t e[2];
-            if (cudaEventCreate(&e[0]) != cudaSuccess || cudaEventCreate(&e[1]) != cudaSuccess) {
-                cudaGetLastError();
-                return;
-            }
-            g_prof.ev.push_back(e[0]);
-            g_prof.ev.push_back(e[1]);
-            g_prof.kid.push_back(0);
-            g_prof.owner.push_back(std::thread::id());
-            g_prof.free_pairs.push_back(g_prof.kid.size() - 1);
-        }
-        pair = g_prof.free_pairs.back();
-        g_prof.free_pairs.pop_back();
+        pair = new_pair_locked();
+        if (pair == (size_t)-1) return;
         g_prof.kid[pair] = id;
         g_prof.owner[pair] = std::this_thread::get_id();
         cudaEventRecord(g_prof.ev[2 * pair], st);
@@ -2188,6 +2220,10 @@ struct LaunchScope {
     ~LaunchScope() {
         if (pair == (size_t)-1) return;
         std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (graph_pair) {
+            cudaEventRecordWithFlags(g_prof.ev[2 * pair + 1], st, cudaEventRecordExternal);
+            return;
+        }
         cudaEventRecord(g_prof.ev[2 * pair + 1], st);
         g_prof.stopped.push_back(pair);
     }
@@ -2215,7 +2251,7 @@ void harvest_locked(bool all) {
             g_prof.iv[g_prof.kid[i]].push_back({(double)a, (double)b});
         else
             cudaGetLastError();
-        g_prof.free_pairs.push_back(i);
+        if (!g_prof.in_graph[i]) g_prof.free_pairs.push_back(i);
     }
     g_prof.stopped.swap(keep);
 }
@@ -2245,6 +2281,54 @@ void prof_harvest() {
     if (!g_prof.on) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     harvest_locked(false);
+}
+
+void graph_prof_begin(GraphProf* gp) {
+    g_capturing = true;
+    // event pairs only while timing is on: otherwise the graph's launches are
+    // counted (GraphProf::counts) but carry no event nodes
+    g_cap_prof = gp;
+    g_cap_timed = g_prof.on;
+}
+void graph_prof_end() {
+    g_capturing = false;
+    g_cap_prof = nullptr;
+}
+
+// At each launch of a graph captured with a GraphProf: its kernels are
+// counted, and with profiling on its event pairs are queued for this
+// thread's next harvest (after it synchronised the stream; a graph is
+// launched again only after that).
+void graph_prof_launched(const GraphProf& gp) {
+    for (size_t i = 0; i < gp.pairs.size(); ++i) {
+        g_prof.total.fetch_add(gp.counts[i], std::memory_order_relaxed);
+        g_prof.launches[g_prof.kid[gp.pairs[i]]].fetch_add(gp.counts[i], std::memory_order_relaxed);
+    }
+    for (size_t i = 0; i < gp.untimed_kid.size(); ++i) {
+        g_prof.total.fetch_add(gp.untimed_counts[i], std::memory_order_relaxed);
+        g_prof.launches[gp.untimed_kid[i]].fetch_add(gp.untimed_counts[i], std::memory_order_relaxed);
+    }
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    const std::thread::id me = std::this_thread::get_id();
+    for (size_t pr : gp.pairs) {
+        g_prof.owner[pr] = me;
+        g_prof.stopped.push_back(pr);
+    }
+}
+
+// The graph is gone: its pairs return to the pool (harvested first).
+void graph_prof_release(GraphProf& gp) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    harvest_locked(true);
+    for (size_t pr : gp.pairs) {
+        g_prof.in_graph[pr] = 0;
+        g_prof.free_pairs.push_back(pr);
+    }
+    gp.pairs.clear();
+    gp.counts.clear();
+    gp.untimed_kid.clear();
+    gp.untimed_counts.clear();
 }
 
 void profile_read(int id, int64_t* launches, double* ms) {
@@ -2439,12 +2523,12 @@ void launch_inner32_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStre
     else
         k_inner32_spmv<1><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, it);
 }
-// TB_CHEB_CPT=2 selects the two-columns-per-thread form of the Chebyshev
-// step; the default is four columns per thread with packed FMAs (panels of
-// at least 4 columns; narrower ones take the two-column form)
-static const int g_cheb_cpt = [] {
+// TB_CHEB_CPT=2 / 4 forces the two- or four-columns-per-thread form of the
+// Chebyshev step (panels narrower than 4 columns always take the two-column
+// form); tb_autotune's choice for the call's size class comes first
+static const int g_cheb_cpt_env = [] {
     const char* e = std::getenv("TB_CHEB_CPT");
-    return e ? std::atoi(e) : 4;
+    return e ? std::atoi(e) : 0;
 }();
 
 template <bool LAST>
@@ -2462,7 +2546,12 @@ static void cheb4_launch(const DevSystem& s, const PanelDev& p, const float2* cu
 template <bool LAST>
 static void cheb_launch(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
                         float gamma, int mode, cudaStream_t st) {
-    if (g_cheb_cpt == 4 && p.P >= 4) {
+    // default form: four columns per thread (measured best on the silicon
+    // benchmark and on ragged water batches, whose concurrent systems fill
+    // the GPU; a small system solved alone runs faster with two, which
+    // tb_autotune finds for its size class)
+    const int cpt = p.cheb_cpt ? p.cheb_cpt : g_cheb_cpt_env ? g_cheb_cpt_env : 4;
+    if (cpt == 4 && p.P >= 4) {
         cheb4_launch<LAST>(s, p, cur, io, omega, gamma, mode, st);
         return;
     }

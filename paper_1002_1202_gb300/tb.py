@@ -69,6 +69,16 @@ class SolveOpts(C.Structure):
     ]
 
 
+class Tune(C.Structure):
+    _fields_ = [
+        ("panel", C.c_int32),
+        ("streams", C.c_int32),
+        ("cheb_cpt", C.c_int32),
+        ("ctas_per_sm", C.c_int32),
+        ("rate", C.c_double),
+    ]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("conv_iter", C.POINTER(C.c_int32)),
@@ -145,6 +155,8 @@ SIGNATURES = [
     ("tb_generalized_lanczos_batch", C.c_int, [_VP, C.c_int32, _I32P, C.c_int32, C.POINTER(SolveOpts), _VP, _VP,
                                                _VP, _VP]),
     ("tb_generalized_lanczos_noalloc", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP, _VP, _VP]),
+    ("tb_autotune", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, C.POINTER(SolveOpts), C.c_int32,
+                              C.POINTER(Tune), C.c_int32, C.POINTER(C.c_int32), _VP]),
     ("tb_csc_forces", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, _VP, _VP, _VP, C.POINTER(SolveOpts),
                                 _VP, C.POINTER(Stats), _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
@@ -543,6 +555,23 @@ def tb_csc_forces(h: Handle, z, w, gamma, dgamma, dq, dS_dd, g_s=2.0, opts: Solv
                                      _out_ptr(out), C.byref(st), _stream(stream))
     _check(s, "tb_csc_forces", allow_unconverged)
     return out, _stats_dict(st, None, h.n_orb, K, s)
+
+
+def tb_autotune(h: Handle, z, w, g_s=2.0, opts: SolveOpts | None = None, iters=3, stream=None) -> list:
+    """Time the launch choices (panel width, panels in flight, Chebyshev-step
+    form) for this handle and shift set; the best is kept in the handle for
+    later calls with panel 0.  Returns the candidates as dicts, best first."""
+    zz = _complex_host(z)
+    ww = _complex_host(w)
+    K = len(zz) // 2
+    opts = opts or tb_default_opts()
+    out = (Tune * 32)()
+    n = C.c_int32(0)
+    s = load_library().tb_autotune(h.ptr, K, _ptr(zz, C.c_double), _ptr(ww, C.c_double), float(g_s), C.byref(opts),
+                                   int(iters), out, 32, C.byref(n), _stream(stream))
+    _check(s, "tb_autotune", False)
+    return [{"panel": out[i].panel, "streams": out[i].streams, "cheb_cpt": out[i].cheb_cpt,
+             "ctas_per_sm": out[i].ctas_per_sm, "rate": out[i].rate} for i in range(n.value)]
 
 
 def tb_default_csc_opts(**kw) -> CscOpts:

@@ -25,6 +25,8 @@ int main(void) {
     F(tb_stats, conv_iter); F(tb_stats, outer_iterations); F(tb_stats, inner_iterations);
     F(tb_stats, max_column_iterations); F(tb_stats, switches); F(tb_stats, unconverged); F(tb_stats, seconds);
     F(tb_stats, inner_redos);
+    Z(tb_tune);
+    F(tb_tune, panel); F(tb_tune, streams); F(tb_tune, cheb_cpt); F(tb_tune, ctas_per_sm); F(tb_tune, rate);
     Z(tb_csc_opts);
     F(tb_csc_opts, max_scf); F(tb_csc_opts, scf_tol); F(tb_csc_opts, mix);
     Z(tb_csc_stats);

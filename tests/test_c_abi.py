@@ -68,7 +68,7 @@ def test_struct_layouts_match_the_binding(tmp_path):
     assert r.returncode == 0, r.stderr
     lines = subprocess.run([out], capture_output=True, text=True, check=True).stdout.split("\n")
     mirrors = {"tb_system_desc": tb.SystemDesc, "tb_solve_opts": tb.SolveOpts, "tb_stats": tb.Stats,
-               "tb_csc_opts": tb.CscOpts, "tb_csc_stats": tb.CscStats}
+               "tb_csc_opts": tb.CscOpts, "tb_csc_stats": tb.CscStats, "tb_tune": tb.Tune}
     seen = set()
     for ln in filter(None, lines):
         name, field, value = ln.split()

@@ -107,3 +107,65 @@ def test_batch_green_elements_and_stats(P, systems, grid):
         _, sts = P.tb_shifted_cocg(P.tb_create_system(systems[sys]), z, [j - int(hb.orb_off[sys])])
         # same recurrences; rounding order differs with the panel width (+-1 step)
         assert np.abs(conv[c] - np.asarray(sts["conv_iter"]).reshape(1, len(z))[0]).max() <= 1
+
+
+def _batch_case():
+    systems = [water_system(8, seed=4, cutoff=3.0, excess_proton=False),
+               si_system((2, 2, 2), sigma=0.05, seed=1),
+               water_system(16, seed=7, cutoff=3.0)]
+    z, w = gauss_legendre_grid(32, -40.0, 0.0, 1.0)
+    return systems, z, w
+
+
+def test_step_graphs_on_a_ragged_batch(P, tmp_path):
+    """Mixed path on a ragged batch (water with 4x1 / 1x1 blocks, silicon):
+    outer steps replayed as one CUDA graph per panel (default) and launched
+    one by one (TB_STEP_GRAPHS=0, in a child process) give bit-identical
+    populations -- the same kernels with the same arguments in the same
+    order -- and both equal the dense definition on the first system."""
+    import os
+    import subprocess
+    import sys
+    systems, z, w = _batch_case()
+    hb = P.tb_create_batch(systems)
+    q, st = P.tb_mulliken_charges(hb, z, w, opts=P.tb_default_opts(precision=1))
+    assert st["status"] == "TB_OK"
+    q = q.cpu().numpy()
+    s = systems[0]
+    S = s.dense_S()
+    H = dense.ased_hamiltonian(S, s.eps, s.K, s.orbital_atom())
+    ref = dense.mulliken_atom(dense.mulliken_orbital(H, S, z, w), s.orbital_atom(), s.n_atoms)
+    assert np.abs(q[:s.n_atoms] - ref).max() <= 1e-8
+    out = tmp_path / "q.npy"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = (
+        "import numpy as np, paper_1002_1202_gb300 as P\n"
+        "from tests.test_gpu_batch import _batch_case\n"
+        "systems, z, w = _batch_case()\n"
+        "hb = P.tb_create_batch(systems)\n"
+        "q, st = P.tb_mulliken_charges(hb, z, w, opts=P.tb_default_opts(precision=1))\n"
+        f"np.save({str(out)!r}, q.cpu().numpy())\n")
+    env = dict(os.environ, TB_STEP_GRAPHS="0", PYTHONPATH=root)
+    subprocess.run([sys.executable, "-c", child], env=env, cwd=root, check=True, timeout=600)
+    assert np.array_equal(np.load(out), q)
+
+
+def test_autotune_choice_is_used(P):
+    """tb_autotune times the launch candidates on the handle's own system,
+    orders them by rate and keeps the best for its size class; a later call
+    with panel 0 then runs with it and gives the populations of an explicit
+    call with the same choice."""
+    s = si_system((4, 4, 2), sigma=0.05, seed=1)
+    z, w = gauss_legendre_grid(32, -20.0, 5.0, 1.0)
+    h = P.tb_create_system(s)
+    base = P.tb_default_opts(precision=1)
+    cands = P.tb_autotune(h, z, w, opts=base, iters=2)
+    rates = [c["rate"] for c in cands]
+    assert len(cands) >= 8 and rates == sorted(rates, reverse=True) and rates[-1] > 0
+    assert {c["ctas_per_sm"] for c in cands} == {3, 4}
+    best = cands[0]
+    cols = np.arange(0, s.n_orb, 5, dtype=np.int32)
+    q_auto, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1, panel=0))
+    assert st["status"] == "TB_OK"
+    q_ref, _ = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1, panel=best["panel"]))
+    assert np.abs(q_auto.cpu().numpy() - q_ref.cpu().numpy()).max() <= 1e-9
