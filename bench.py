@@ -42,8 +42,29 @@ UNIT = "shift*RHS*iterations/s"
 CELLS = (8, 8, 8)
 SEED = 3
 K_SHIFTS = 256
+# ALU peaks for the roofline of ALU-bound kernels: measured on the device
+# by the library's FMA microbenchmark at the start of a run (tb_measure_fma_peak);
+# these nominal figures stand only until then (or if it fails)
 FP64_PEAK_TFLOPS = 1.25       # GB300 FP64 (vector and tensor), nominal
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x clock
+ALU_PEAK_SOURCE = "nominal"
+
+
+def measure_alu_peaks(P):
+    """FP32 (best of scalar and packed FMA) and FP64 FMA throughput of this
+    device, measured; they replace the nominal peaks for this run."""
+    global FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, ALU_PEAK_SOURCE
+    try:
+        f32 = P.tb_measure_fma_peak(0)
+        f32p = P.tb_measure_fma_peak(1)
+        f64 = P.tb_measure_fma_peak(2)
+    except Exception as e:  # noqa: BLE001 -- keep the nominal figures, say why
+        return {"source": "nominal", "error": str(e)}
+    FP32_PEAK_TFLOPS = max(f32, f32p)
+    FP64_PEAK_TFLOPS = f64
+    ALU_PEAK_SOURCE = "measured (tb_measure_fma_peak)"
+    return {"source": ALU_PEAK_SOURCE, "fp32_fma_tflops": f32, "fp32_packed_fma_tflops": f32p,
+            "fp64_fma_tflops": f64}
 
 
 def parse():
@@ -77,6 +98,9 @@ def parse():
     ap.add_argument("--batch-full", action="store_true",
                     help="instead of the benchmark step: 64 liquid-water boxes of 512-1536 molecules (+H3O+) as one "
                          "ragged batch, 64 columns per box, 128 shifts, 20 outer iterations per call")
+    ap.add_argument("--to-solution", type=int, default=32,
+                    help="columns (one panel) run to the 1e-8 residual in every shift after the timed steps "
+                         "(0: skip)")
     ap.add_argument("--csc-scf", type=int, default=1,
                     help="timed SCF iterations of the charge-self-consistency measurement (0: skip)")
     return ap.parse_args()
@@ -285,15 +309,70 @@ def oracle_sample(s, z, w, n_iter, col):
     return t, cores
 
 
+def host_cpu_info():
+    """Host cores and CPU model (lscpu, else /proc/cpuinfo)."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        info["affinity_cores"] = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        pass
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = dict(ln.split(":", 1) for ln in out.splitlines() if ":" in ln)
+        model = " ".join(x.strip() for x in (fields.get("Vendor ID", ""), fields.get("Model name", "")) if x.strip())
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    info["model"] = model or "unknown"
+    return info
+
+
+_SINGLE = """
+import os, sys, json
+sys.path.insert(0, {root!r})
+import bench
+s, z, w = bench.workload()
+t, c = bench.oracle_sample(s, z, w, {n}, 1234)
+print(json.dumps({{"t": t, "cores": c}}))
+"""
+
+
 def cpu_baseline(s, z, w, target_s):
+    """The oracle's method on one column of the workload, bounded to about
+    target_s seconds: threaded (numpy / scipy as installed, all host cores)
+    and, in a child process with the BLAS and OpenMP pools set to one
+    thread, single-threaded on a shorter sample."""
     col = 1234
     t1, _ = oracle_sample(s, z, w, 2, col)
     per = t1 / 2.0
     n = int(max(2, min(400, target_s / max(per, 1e-6))))
     t, cores = oracle_sample(s, z, w, n, col)
-    return {"value": K_SHIFTS * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle.method.generalized_shifted_cocg (numpy + scipy.sparse CSR, inner CG to 1e-12), "
-                       f"1 column x {n} outer iterations x {K_SHIFTS} shifts of the same workload, {t:.1f} s")}
+    rec = {"value": K_SHIFTS * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": (f"oracle.method.generalized_shifted_cocg (numpy + scipy.sparse CSR, inner CG to 1e-12), "
+                      f"1 column x {n} outer iterations x {K_SHIFTS} shifts of the same workload, {t:.1f} s"),
+           "cores_basis": "process CPU time / wall time of the threaded sample",
+           "host": host_cpu_info()}
+    n1 = max(2, n // 3)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", _SINGLE.format(root=ROOT, n=n1)], env=env, capture_output=True,
+                           text=True, timeout=max(120.0, 4 * target_s))
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        rec["single_thread"] = {"value": K_SHIFTS * n1 / one["t"], "unit": UNIT, "cores": 1,
+                                "sample": f"1 column x {n1} outer iterations, {one['t']:.1f} s, BLAS/OpenMP pools "
+                                          "of one thread"}
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
+        rec["single_thread"] = {"error": str(e)}
+    return rec
 
 
 def run_reference(args):
@@ -481,12 +560,12 @@ def roofline_for(kname, ms, launches, s, panel, peaks, mixed=False, busy_ms=None
         tf32 = flops / 2 * DF_INSTR_PER_MAC * 2 / avg_s / 1e12
         rec = {"bound": "alu", "achieved": tf32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": tf32 / FP32_PEAK_TFLOPS, "fp64_equivalent_tflops": tf,
-               "peak_source": "FP32 issue peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; double-float "
+               "peak_source": "FP32 FMA peak (" + ALU_PEAK_SOURCE + "); double-float "
                               "products counted as 12 FP32 instructions per FP64 multiply-add"}
     elif fp64:
         rec = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": tf / FP64_PEAK_TFLOPS,
-               "peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s (no measured FP64 peak on file)"}
+               "peak_source": "FP64 FMA peak (" + ALU_PEAK_SOURCE + ")"}
     else:
         f_alu = tf / FP32_PEAK_TFLOPS
         f_mem = gbs / peaks["hbm_gbs"]
@@ -495,7 +574,7 @@ def roofline_for(kname, ms, launches, s, panel, peaks, mixed=False, busy_ms=None
                    "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"}
         else:
             rec = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
-                   "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+                   "peak_source": "FP32 FMA peak (" + ALU_PEAK_SOURCE + ")"}
     rec.update({"kernel": kern, "launches": launches, "avg_launch_us": avg_s * 1e6,
                 "avg_launch_us_basis": "busy time (union of launch intervals on all streams) / launches",
                 "mean_launch_duration_us": mean_s * 1e6,
@@ -530,6 +609,7 @@ def run_ours(args):
     P.build()
     s, z, w = workload()
     h = P.tb_create_system(s)
+    alu_peaks = measure_alu_peaks(P)
     prec = 1 if args.precision == "mixed" else 0
     inner_method = P.tb.TB_INNER_CG if args.inner_method == "cg" else P.tb.TB_INNER_CHEBYSHEV
     tune = None
@@ -674,7 +754,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32" if prec else "f64", "data": "synthetic",
         "config": config_dict(args, s), "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "roofline": roofline, "roofline_other_kernels": others, "active_shift_value": active_value,
-        "kernel_ms": share, "spmm_hbm": spmm_hbm, "other_precision": compare, "peaks": peaks,
+        "kernel_ms": share, "spmm_hbm": spmm_hbm, "other_precision": compare, "peaks": dict(peaks, alu=alu_peaks),
         "autotune": tune,
         "inner_redos": sum(st["inner_redos"] for st in stats),
         "inner_iterations_per_outer": (sum(st["inner_iterations"] for st in stats)
@@ -688,6 +768,8 @@ def run_ours(args):
         line["batch"] = batch_measure(P, prec, args.panel)
     if world == 1 and args.csc_scf > 0:
         line["csc"] = csc_measure(P, prec, args.csc_scf, args.panel)
+    if world == 1 and args.to_solution > 0:
+        line["to_solution"] = to_solution_measure(P, h, s, z, w, prec, inner_method, n_cols=args.to_solution)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, z, w, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -695,6 +777,39 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def to_solution_measure(P, h, s, z, w, prec, inner_method, n_cols=4, max_iter=100000):
+    """n_cols seeded columns of the benchmark workload run until every one of
+    the K shifts meets the 1e-8 residual (one panel, Mulliken projection, the
+    benchmark's precision and inner tolerance): outer iterations to
+    convergence per column, wall time, and shift*RHS*iterations/s with
+    n_j = the iterations column j ran (all K shifts counted until the
+    column's last converges) and with only the unconverged shifts counted.
+    The true residuals of such solutions are checked against the dense
+    definition by the GPU test of the same configuration."""
+    import torch
+    cols = rank_columns(s.n_orb, n_cols, 0, seed=77)
+    opts = P.tb_default_opts(max_iter=max_iter, panel=n_cols, tol=1e-8, precision=prec, inner_tol=1e-12,
+                             inner_method=inner_method)
+    P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(max_iter=3, panel=n_cols, precision=prec),
+                          allow_unconverged=True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    _, st = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=opts, allow_unconverged=True)
+    ev1.record()
+    ev1.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    ci = np.asarray(st["conv_iter"]).reshape(n_cols, -1)
+    K = ci.shape[1]
+    per_col = [int(r.max()) + 1 if np.all(r >= 0) else max_iter for r in ci]
+    return {"workload": "%d seeded columns of the benchmark system to the 1e-8 residual in every one of %d shifts, "
+                        "one panel" % (n_cols, K),
+            "status": st["status"], "all_converged": bool(np.all(ci >= 0)), "seconds": t,
+            "outer_iterations_per_column": per_col,
+            "value": K * sum(per_col) / t, "unit": UNIT,
+            "active_shift_value": float(np.sum(np.where(ci >= 0, ci + 1, max_iter))) / t}
 
 
 def run_large(args):

@@ -567,6 +567,16 @@ enum {
                               S d and the update of d in one kernel)          */
     TB_K_COUNT = 14
 };
+/*
+ * FMA throughput of the current device, measured (no counterpart in the
+ * paper: the denominator of the roofline fractions of ALU-bound kernels).
+ * mode 0: scalar FP32 FMA, 1: packed FP32 FMA (two lanes per instruction),
+ * 2: FP64 FMA; 8 independent register chains per thread, 64 warps per SM,
+ * one timed launch after a warm-up (CUDA events on `stream`).  Writes
+ * TFLOP/s (2 flop per multiply-add) to *tflops_out.
+ */
+tb_status tb_measure_fma_peak(int32_t mode, double *tflops_out, void *stream);
+
 int64_t tb_launch_count(void);
 void tb_profile_enable(int32_t enable);
 tb_status tb_profile_read(int32_t kernel, int64_t *launches, double *total_ms);

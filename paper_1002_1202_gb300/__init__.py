@@ -13,7 +13,7 @@ from .tb import (  # noqa: F401
     tb_mulliken_orbital, tb_mulliken_charges, tb_generalized_lanczos, tb_generalized_lanczos_noalloc,
     tb_generalized_lanczos_batch, tb_lanczos_green_batch,
     tb_default_csc_opts, tb_csc_hamiltonian, tb_csc_loop, tb_csc_forces, tb_autotune, CscOpts, tb_lanczos_green,
-    tb_status_string,
+    tb_status_string, tb_measure_fma_peak,
     tb_launch_count, tb_profile_enable, tb_profile_read, tb_profile_busy,
 )
 from ._build_lib import build  # noqa: F401

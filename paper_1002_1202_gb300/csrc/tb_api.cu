@@ -1430,6 +1430,32 @@ void tb_default_opts(tb_solve_opts* o) {
     o->state_bytes = 0;
 }
 
+tb_status tb_measure_fma_peak(int32_t mode, double* tflops_out, void* stream) {
+    if (!tflops_out || mode < 0 || mode > 2) return TB_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    TB_CK(cudaGetDevice(&dev));
+    TB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int threads = 256, blocks = 8 * sms;          // 64 warps per SM
+    const int iters = mode == 2 ? 1 << 11 : 1 << 13;
+    cudaEvent_t e0, e1;
+    TB_CK(cudaEventCreate(&e0));
+    TB_CK(cudaEventCreate(&e1));
+    launch_fma_peak(mode, blocks, threads, iters / 16, nullptr, nullptr, st);   // warm-up
+    TB_CK(cudaEventRecord(e0, st));
+    launch_fma_peak(mode, blocks, threads, iters, nullptr, nullptr, st);
+    TB_CK(cudaEventRecord(e1, st));
+    TB_CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    TB_CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // 8 chains x 2 flop per FMA (x 2 lanes for the packed form) per round
+    const double flops = (double)blocks * threads * iters * 8 * 2 * (mode == 1 ? 2 : 1);
+    *tflops_out = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+    return TB_OK;
+}
+
 int64_t tb_launch_count(void) { return launch_count(); }
 
 void tb_profile_enable(int32_t enable) { profile_enable(enable != 0); }

@@ -198,6 +198,7 @@ void launch_band_energy_terms(const double2* G, const double2* dG, const double*
                               const double2* z, const double2* w, double g_s, double* e_terms, double* gH,
                               double* gS, cudaStream_t st);
 void launch_sum_fixed(const double* v, int64_t n, double* out, cudaStream_t st);
+void launch_fma_peak(int mode, int blocks, int threads, int iters, float* out32, double* out64, cudaStream_t st);
 // charge-self-consistent forces: per-element gradients at fixed dq, and the Coulomb-gradient term
 void launch_csc_force_terms(const double2* G, int64_t n, int K, const double2* z, const double2* w, double g_s,
                             const double* V, const int32_t* atom_a, const int32_t* atom_b, double* gH, double* gS,

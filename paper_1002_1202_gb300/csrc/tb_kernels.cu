@@ -1730,6 +1730,56 @@ __global__ void k_csc_force_coulomb(int n, const double* __restrict__ dgamma, co
     }
 }
 
+// FMA throughput microbenchmark (measurement only): every thread runs
+// `iters` rounds of 8 independent multiply-add chains on values that stay
+// in registers (mode 0: scalar FP32 FMA, 1: packed FP32 FMA on float2, 2:
+// FP64 FMA); the result is stored only if a run-time flag says so, which
+// keeps the chains live without memory traffic.
+__global__ void k_fma_peak(int mode, int iters, float a32, double a64, int store, float* out32, double* out64) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode == 2) {
+        double v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 1.0 + 1e-3 * (t + j);
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = fma(v[j], a64, 1e-7);
+        if (store) {
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc += v[j];
+            out64[t] = acc;
+        }
+    } else if (mode == 1) {
+        float2 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = make_float2(1.f + 1e-3f * j, 1.f - 1e-3f * j);
+        const float2 a2 = make_float2(a32, a32), c2 = make_float2(1e-7f, 1e-7f);
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = __ffma2_rn(v[j], a2, c2);
+        if (store) {
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc += v[j].x + v[j].y;
+            out32[t] = acc;
+        }
+    } else {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 1.f + 1e-3f * (t + j);
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = fmaf(v[j], a32, 1e-7f);
+        if (store) {
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc += v[j];
+            out32[t] = acc;
+        }
+    }
+}
+
 // out[0] = sum of v[0..n) in a fixed order (one CTA: strided partial sums,
 // then a tree): deterministic whatever the launch history
 __global__ void k_sum_fixed(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
@@ -2691,6 +2741,10 @@ void launch_csc_force_terms(const double2* G, int64_t n, int K, const double2* z
 void launch_csc_force_coulomb(int n, const double* dgamma, const double* dq, double* F, cudaStream_t st) {
     LaunchScope ls_(K_CSC, st);
     k_csc_force_coulomb<<<grid_for(n), THREADS, 0, st>>>(n, dgamma, dq, F);
+}
+void launch_fma_peak(int mode, int blocks, int threads, int iters, float* out32, double* out64, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_fma_peak<<<blocks, threads, 0, st>>>(mode, iters, 0.999999f, 0.999999999, 0, out32, out64);
 }
 void launch_sum_fixed(const double* v, int64_t n, double* out, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);

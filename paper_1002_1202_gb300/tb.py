@@ -159,6 +159,7 @@ SIGNATURES = [
                               C.POINTER(Tune), C.c_int32, C.POINTER(C.c_int32), _VP]),
     ("tb_csc_forces", C.c_int, [_VP, C.c_int32, _DP, _DP, C.c_double, _VP, _VP, _VP, _VP, C.POINTER(SolveOpts),
                                 _VP, C.POINTER(Stats), _VP]),
+    ("tb_measure_fma_peak", C.c_int, [C.c_int32, _DP, _VP]),
     ("tb_status_string", C.c_char_p, [C.c_int]),
     ("tb_launch_count", C.c_int64, []),
     ("tb_profile_enable", None, [C.c_int32]),
@@ -714,6 +715,14 @@ def tb_generalized_lanczos_noalloc(h: Handle, j: int, n_steps: int, inner_tol=1e
                                                       _out_ptr(a), _out_ptr(b), _out_ptr(nrm), _stream(stream))
     _check(s, "tb_generalized_lanczos_noalloc", False)
     return a, b, nrm
+
+
+def tb_measure_fma_peak(mode: int, stream=None) -> float:
+    """Measured FMA throughput in TFLOP/s: mode 0 scalar FP32, 1 packed FP32,
+    2 FP64."""
+    v = C.c_double()
+    _check(load_library().tb_measure_fma_peak(int(mode), C.byref(v), _stream(stream)), "tb_measure_fma_peak", False)
+    return v.value
 
 
 def tb_status_string(s: int) -> str:
