@@ -515,9 +515,9 @@ CHEB_CPT = None
 def cheb_kernel_name(panel, n_atoms):
     """The Chebyshev step's kernel, as the library picks it: the autotuner's
     choice, else TB_CHEB_CPT, else four columns per thread with packed FMAs
-    (panels narrower than 4 columns: two)."""
+    from 16 columns per panel on and two below that."""
     env = os.environ.get("TB_CHEB_CPT")
-    cpt = CHEB_CPT if CHEB_CPT else (int(env) if env else 4)
+    cpt = CHEB_CPT if CHEB_CPT else (int(env) if env else (4 if panel >= 16 else 2))
     if cpt == 2 or panel < 4:
         return "k_inner32_cheb"
     return "k_inner32_cheb4"

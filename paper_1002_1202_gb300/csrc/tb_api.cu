@@ -59,6 +59,7 @@ struct tb_handle {
     std::vector<int32_t> orb2pad_local_h;  // [N]: padded slot within the orbital's own system
     int32_t* orb2pad_local = nullptr;      // device copy
     int32_t* bcol_local = nullptr;         // device [nb]: block column local to its system
+    int* row_order_local = nullptr;        // device [n_atoms]: per system, its block-row order (local indices)
     int* flags_pool = nullptr;             // pinned [NPOOL][NFLAGS]: status words of the worker threads
     // tb_autotune's choices, per size class (precision, correction method,
     // shift count rounded up to a power of two)
@@ -1485,6 +1486,11 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->ds.S32);
     cudaFree(h->ds.S32lo);
     cudaFree(h->ds.S32T);
+    cudaFree(h->ds.norb);
+    cudaFree(h->ds.row_order);
+    cudaFree(h->ds.S32r);
+    cudaFree(h->ds.roff);
+    cudaFree(h->row_order_local);
     cudaFree(h->ds.H32hi);
     cudaFree(h->ds.H32lo);
     cudaFree(h->ds.grp_ptr);
@@ -1681,6 +1687,34 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     // double-float splits of S and H for the mixed path's FP64-accurate products
     launch_split_f64(h->ds.S, h->ds.S32, h->ds.S32lo, 16 * (long long)nb, st);
     launch_transpose_blocks(h->ds.S32, h->ds.S32T, nb, st);
+    if (std::any_of(d->orb_per_atom, d->orb_per_atom + n, [](int32_t o) { return o == 1; })) {
+        // exact orbital counts for the Chebyshev step: sp atoms first, then s atoms; compact blocks
+        std::vector<unsigned char> no(n);
+        std::vector<int> order;
+        order.reserve(n);
+        for (int i = 0; i < n; ++i) no[i] = (unsigned char)d->orb_per_atom[i];
+        for (int i = 0; i < n; ++i)
+            if (no[i] == 4) order.push_back(i);
+        for (int i = 0; i < n; ++i)
+            if (no[i] == 1) order.push_back(i);
+        std::vector<int64_t> ro(nb);
+        int64_t tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
+                ro[b] = tot;
+                tot += (no[i] == 4 && no[d->bcol[b]] == 4) ? 16 : 4;
+            }
+        if ((e = cudaMalloc(&h->ds.norb, n)) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&h->ds.row_order, sizeof(int) * n)) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&h->ds.roff, sizeof(int64_t) * nb)) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&h->ds.S32r, sizeof(float) * std::max<int64_t>(tot, 4))) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(h->ds.norb, no.data(), n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(h->ds.row_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(h->ds.roff, ro.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+        h->ds.rag = 1;
+        launch_compact_blocks(h->ds, st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);   // host vectors released at scope exit
+    }
     launch_split_f64(h->ds.H, h->ds.H32hi, h->ds.H32lo, 16 * (long long)nb, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
@@ -1771,9 +1805,26 @@ tb_status tb_create_batch(tb_handle** out, const tb_system_desc* descs, int32_t 
     if ((e = cudaMemcpyAsync(h->bcol_local, bl.data(), sizeof(int32_t) * bl.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(h->orb2pad_local, h->orb2pad_local_h.data(), sizeof(int32_t) * ooff.back(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    if (h->ds.rag) {
+        // per system, its own block-row order in local atom indices
+        std::vector<int> lo(aoff.back());
+        for (int q = 0; q < n_systems; ++q) {
+            int k = (int)aoff[q];
+            for (int64_t i = aoff[q]; i < aoff[q + 1]; ++i)
+                if (opa[i] == 4) lo[k++] = (int)(i - aoff[q]);
+            for (int64_t i = aoff[q]; i < aoff[q + 1]; ++i)
+                if (opa[i] == 1) lo[k++] = (int)(i - aoff[q]);
+        }
+        if ((e = cudaMalloc(&h->row_order_local, sizeof(int) * lo.size())) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(h->row_order_local, lo.data(), sizeof(int) * lo.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+    }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
     for (int q = 0; q < n_systems; ++q) {
         DevSystem v = h->ds;
+        if (h->ds.rag) {
+            v.norb = h->ds.norb + aoff[q];
+            v.row_order = h->row_order_local + aoff[q];
+        }
         v.n_atoms = (int)(aoff[q + 1] - aoff[q]);
         v.npad = 4 * v.n_atoms;
         v.nb = brow[aoff[q + 1]] - brow[aoff[q]];

@@ -44,6 +44,19 @@ struct DevSystem {
     float* S32 = nullptr;      // [nb][16] S rounded to FP32 (S_hi of the double-float split)
     float* S32lo = nullptr;    // [nb][16] S - S_hi in FP32
     float* S32T = nullptr;     // [nb][16] S_hi of every block transposed (column e of the block as row e)
+    // Exact orbital counts for the Chebyshev step of systems with s-only
+    // atoms (rag = 1; absent for all-sp systems): the orbital count of every
+    // atom, the block rows in the order sp atoms first, then s atoms (one
+    // run of each kind per system, so a warp's rows are of one kind), and
+    // the FP32 blocks stored with their real entries only, at 16-byte
+    // aligned float offsets: 4x4 transposed (column e as row e), 4x1 as the
+    // column S[0..3][0], 1x4 as the row S[0][0..3], 1x1 as S[0][0] and three
+    // zeros.
+    int rag = 0;
+    unsigned char* norb = nullptr;   // [n_atoms] 1 or 4
+    int* row_order = nullptr;        // [n_atoms] atom of each block-row slot (indices of this view)
+    float* S32r = nullptr;           // compact blocks
+    int64_t* roff = nullptr;         // [nb] float offset of block b in S32r
     float* H32hi = nullptr;    // [nb][16] H rounded to FP32
     float* H32lo = nullptr;    // [nb][16] H - H_hi in FP32
     // atom groups of the grouped FP32 SpMV: group g = atoms [g * grpG, (g + 1) * grpG)
@@ -159,6 +172,7 @@ bool preload_noalloc_kernels();   // loads the allocation-free call's kernels on
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st);
 void launch_split_f64(const double* v, float* hi, float* lo, long long n, cudaStream_t st);
 void launch_transpose_blocks(const float* in, float* out, long long nb, cudaStream_t st);
+void launch_compact_blocks(const DevSystem& s, cudaStream_t st);   // S32 -> S32r (rag systems)
 void launch_panel_init(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_panel_rhs(const PanelDev& p, const double* rhs, const int32_t* orb2pad, int n_orb, int ncols,
                       cudaStream_t st);

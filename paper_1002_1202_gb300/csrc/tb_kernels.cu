@@ -190,6 +190,32 @@ __global__ void k_transpose_blocks(const float* __restrict__ in, float* __restri
     }
 }
 
+// The compact FP32 blocks of a system with s-only atoms (see DevSystem):
+// one thread per block row I, its blocks in order.
+__global__ void k_compact_blocks(int n_atoms, const int* __restrict__ brow, const int* __restrict__ bcol,
+                                 const unsigned char* __restrict__ norb, const float* __restrict__ S32,
+                                 const int64_t* __restrict__ roff, float* __restrict__ out) {
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < n_atoms; I += gridDim.x * blockDim.x) {
+        const int ni = norb[I];
+        for (int b = brow[I]; b < brow[I + 1]; ++b) {
+            const int nj = norb[bcol[b]];
+            const float* S = S32 + 16 * (size_t)b;
+            float* o = out + roff[b];
+            if (ni == 4 && nj == 4) {
+                for (int e = 0; e < 4; ++e)
+                    for (int a = 0; a < 4; ++a) o[4 * e + a] = S[4 * a + e];
+            } else if (ni == 4) {
+                for (int a = 0; a < 4; ++a) o[a] = S[4 * a];
+            } else if (nj == 4) {
+                for (int e = 0; e < 4; ++e) o[e] = S[e];
+            } else {
+                o[0] = S[0];
+                o[1] = o[2] = o[3] = 0.f;
+            }
+        }
+    }
+}
+
 __global__ void k_panel_init(PanelDev p) {
     const long long items = (long long)p.npad * p.P;
     for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
@@ -1308,6 +1334,110 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4(DevSystem s, Panel
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
+            const size_t row = (size_t)(4 * I + a) * P;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const int c = k * pstride + 2 * t0;
+                const size_t e = row + c;
+                const float4 f4 = *reinterpret_cast<const float4*>(p.r32 + e);
+                const float4 c4 = *reinterpret_cast<const float4*>(cur + e);
+                const float4 p4 = mode == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(io + e);
+                const float2 y0 = acc[a][2 * k], y1 = acc[a][2 * k + 1];
+                const float f[4] = {f4.x, f4.y, f4.z, f4.w}, dc[4] = {c4.x, c4.y, c4.z, c4.w};
+                const float dp[4] = {p4.x, p4.y, p4.z, p4.w}, y[4] = {y0.x, y0.y, y1.x, y1.y};
+                float dn[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - y[q]) + dc[q] - dp[q]);
+                if (LAST) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const InnerState i0 = p.inner32[2 * (c + j)], i1 = p.inner32[2 * (c + j) + 1];
+                        const bool ca = p.col[c + j].active != 0;
+                        double2 x = p.Rp[e + j];
+                        if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] / i0.scale;
+                        if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] / i1.scale;
+                        p.Rp[e + j] = x;
+                        p.RpS[e + j] = df_split(x);
+                    }
+                } else {
+                    *reinterpret_cast<float4*>(io + e) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+                }
+            }
+        }
+    }
+}
+
+// The four-column Chebyshev step for systems with s-only atoms (water: O
+// with s, p and H with s): block rows in the order of s.row_order (sp atoms,
+// then s atoms), and every product with the real entries only -- an s atom
+// J contributes one gathered row (not four), an s row atom I one output row
+// -- read from the compact blocks.  The padded slots of the vectors are
+// neither read nor written (the other kernels keep them at zero).
+template <int PW, bool LAST>
+__global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4r(DevSystem s, PanelDev p, const float2* __restrict__ cur,
+                                                              float2* io, float omega, float gamma, int mode) {
+    constexpr int NP = 2;
+    if (*(volatile int*)&p.flags[4] == 0) return;
+    const int P = PW > 0 ? PW : p.P;
+    const int TPR = P / 4;
+    const int pstride = P / NP;
+    const int t0 = threadIdx.x % TPR;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) live |= cheb_live(p, k * pstride + 2 * t0) || cheb_live(p, k * pstride + 2 * t0 + 1);
+    if (!live) return;
+    const long long items = (long long)s.n_atoms * TPR;
+    for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
+         idx += (long long)gridDim.x * THREADS) {
+        const int I = s.row_order[idx / TPR];
+        const int ni = s.norb[I];
+        float2 acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+        const int b0 = s.brow[I], b1 = s.brow[I + 1];
+        int Jn = __ldg(s.bcol + b0);
+        for (int bb = b0; bb < b1; ++bb) {
+            const int J = Jn;
+            if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
+            const int nj = s.norb[J];
+            const float2* xb = cur + (size_t)(4 * J) * P + 2 * t0;
+            const float4* Sr = reinterpret_cast<const float4*>(s.S32r + s.roff[bb]);
+            if (ni == 4) {
+                // nj rows e of the gathered d_k, column e of the block as four rows a
+                for (int e = 0; e < nj; ++e) {
+                    const float4 xa = *reinterpret_cast<const float4*>(xb + (size_t)e * P);
+                    const float4 xq = *reinterpret_cast<const float4*>(xb + (size_t)e * P + pstride);
+                    const float4 sc = __ldg(Sr + e);
+                    const float sv[4] = {sc.x, sc.y, sc.z, sc.w};
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const float2 s2 = make_float2(sv[a], sv[a]);
+                        acc[a][0] = __ffma2_rn(s2, lo2(xa), acc[a][0]);
+                        acc[a][1] = __ffma2_rn(s2, hi2(xa), acc[a][1]);
+                        acc[a][2] = __ffma2_rn(s2, lo2(xq), acc[a][2]);
+                        acc[a][3] = __ffma2_rn(s2, hi2(xq), acc[a][3]);
+                    }
+                }
+            } else {
+                // one output row: row 0 of the block (S[0][0 .. nj))
+                const float4 sr = __ldg(Sr);
+                const float sv[4] = {sr.x, sr.y, sr.z, sr.w};
+                for (int e = 0; e < nj; ++e) {
+                    const float4 xa = *reinterpret_cast<const float4*>(xb + (size_t)e * P);
+                    const float4 xq = *reinterpret_cast<const float4*>(xb + (size_t)e * P + pstride);
+                    const float2 s2 = make_float2(sv[e], sv[e]);
+                    acc[0][0] = __ffma2_rn(s2, lo2(xa), acc[0][0]);
+                    acc[0][1] = __ffma2_rn(s2, hi2(xa), acc[0][1]);
+                    acc[0][2] = __ffma2_rn(s2, lo2(xq), acc[0][2]);
+                    acc[0][3] = __ffma2_rn(s2, hi2(xq), acc[0][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (a >= ni) break;
             const size_t row = (size_t)(4 * I + a) * P;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
@@ -2466,6 +2596,10 @@ void launch_transpose_blocks(const float* in, float* out, long long nb, cudaStre
     LaunchScope ls_(K_OTHER, st);
     k_transpose_blocks<<<grid_for(16 * nb), THREADS, 0, st>>>(in, out, nb);
 }
+void launch_compact_blocks(const DevSystem& s, cudaStream_t st) {
+    LaunchScope ls_(K_OTHER, st);
+    k_compact_blocks<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s.n_atoms, s.brow, s.bcol, s.norb, s.S32, s.roff, s.S32r);
+}
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st) {
     {
         LaunchScope ls_(K_OTHER, st);
@@ -2581,10 +2715,25 @@ static const int g_cheb_cpt_env = [] {
     return e ? std::atoi(e) : 0;
 }();
 
+// TB_CHEB_RAG=0: systems with s-only atoms also take the padded form
+static const bool g_cheb_rag = [] {
+    const char* e = std::getenv("TB_CHEB_RAG");
+    return !(e && std::atoi(e) == 0);
+}();
+
 template <bool LAST>
 static void cheb4_launch(const DevSystem& s, const PanelDev& p, const float2* cur, float2* io, float omega,
                          float gamma, int mode, cudaStream_t st) {
     const int g = std::min(grid_for((long long)s.n_atoms * (p.P / 4)), 3 * (gmax() / 4));
+    if (s.rag && g_cheb_rag) {
+        switch (p.P) {
+            case 256: k_inner32_cheb4r<256, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 128: k_inner32_cheb4r<128, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            case 64: k_inner32_cheb4r<64, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+            default: k_inner32_cheb4r<0, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
+        }
+        return;
+    }
     switch (p.P) {
         case 256: k_inner32_cheb4<256, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
         case 128: k_inner32_cheb4<128, LAST><<<g, THREADS, 0, st>>>(s, p, cur, io, omega, gamma, mode); break;
@@ -2599,8 +2748,11 @@ static void cheb_launch(const DevSystem& s, const PanelDev& p, const float2* cur
     // default form: four columns per thread (measured best on the silicon
     // benchmark and on ragged water batches, whose concurrent systems fill
     // the GPU; a small system solved alone runs faster with two, which
-    // tb_autotune finds for its size class)
-    const int cpt = p.cheb_cpt ? p.cheb_cpt : g_cheb_cpt_env ? g_cheb_cpt_env : 4;
+    // tb_autotune finds for its size class), two for narrow panels
+    // (measured on the 100 000-atom crystal: at 4 and 8 columns per panel the
+    // two-column form's twice as many threads win, 61 / 69 against 93 /
+    // 100 us per step; from 16 columns on, four columns per thread)
+    const int cpt = p.cheb_cpt ? p.cheb_cpt : g_cheb_cpt_env ? g_cheb_cpt_env : (p.P >= 16 ? 4 : 2);
     if (cpt == 4 && p.P >= 4) {
         cheb4_launch<LAST>(s, p, cur, io, omega, gamma, mode, st);
         return;

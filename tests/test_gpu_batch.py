@@ -169,3 +169,37 @@ def test_autotune_choice_is_used(P):
     assert st["status"] == "TB_OK"
     q_ref, _ = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(precision=1, panel=best["panel"]))
     assert np.abs(q_auto.cpu().numpy() - q_ref.cpu().numpy()).max() <= 1e-9
+
+
+def test_ragged_chebyshev_step_equals_padded(P, tmp_path):
+    """Water (O: s, p; H: s) with exact orbital counts in the Chebyshev step
+    (compact blocks, one gathered row per H neighbour, one output row per H
+    atom; default) against the padded form (TB_CHEB_RAG=0, child process):
+    the padded form only adds exact zeros (padded rows of the vectors) in
+    the same order, so the populations are bit-identical, on one box and on
+    a ragged batch."""
+    import os
+    import subprocess
+    import sys
+    systems, z, w = _batch_case()
+    hb = P.tb_create_batch(systems)
+    q, st = P.tb_mulliken_charges(hb, z, w, opts=P.tb_default_opts(precision=1))
+    assert st["status"] == "TB_OK"
+    h1 = P.tb_create_system(systems[2])
+    q1, _ = P.tb_mulliken_charges(h1, z, w, opts=P.tb_default_opts(precision=1))
+    out = tmp_path / "q.npz"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = (
+        "import numpy as np, paper_1002_1202_gb300 as P\n"
+        "from tests.test_gpu_batch import _batch_case\n"
+        "systems, z, w = _batch_case()\n"
+        "hb = P.tb_create_batch(systems)\n"
+        "q, st = P.tb_mulliken_charges(hb, z, w, opts=P.tb_default_opts(precision=1))\n"
+        "h1 = P.tb_create_system(systems[2])\n"
+        "q1, _ = P.tb_mulliken_charges(h1, z, w, opts=P.tb_default_opts(precision=1))\n"
+        f"np.savez({str(out)!r}, q=q.cpu().numpy(), q1=q1.cpu().numpy())\n")
+    env = dict(os.environ, TB_CHEB_RAG="0", PYTHONPATH=root)
+    subprocess.run([sys.executable, "-c", child], env=env, cwd=root, check=True, timeout=600)
+    ref = np.load(out)
+    assert np.array_equal(ref["q"], q.cpu().numpy())
+    assert np.array_equal(ref["q1"], q1.cpu().numpy())
