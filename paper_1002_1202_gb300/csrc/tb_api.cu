@@ -1489,7 +1489,7 @@ tb_status tb_destroy(tb_handle* h) {
     cudaFree(h->ds.norb);
     cudaFree(h->ds.row_order);
     cudaFree(h->ds.S32r);
-    cudaFree(h->ds.roff);
+    cudaFree(h->ds.bmeta);
     cudaFree(h->row_order_local);
     cudaFree(h->ds.H32hi);
     cudaFree(h->ds.H32lo);
@@ -1697,20 +1697,22 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
             if (no[i] == 4) order.push_back(i);
         for (int i = 0; i < n; ++i)
             if (no[i] == 1) order.push_back(i);
-        std::vector<int64_t> ro(nb);
-        int64_t tot = 0;
+        std::vector<int2> bm(nb);
+        int64_t tot = 0;   // in float4 units
         for (int i = 0; i < n; ++i)
             for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
-                ro[b] = tot;
-                tot += (no[i] == 4 && no[d->bcol[b]] == 4) ? 16 : 4;
+                const int j = d->bcol[b];
+                bm[b] = make_int2(j, (int)tot | (no[j] == 1 ? (int)0x80000000u : 0));
+                tot += (no[i] == 4 && no[j] == 4) ? 4 : 1;
             }
+        if (tot >= ((int64_t)1 << 31)) return fail(cudaErrorMemoryAllocation);
         if ((e = cudaMalloc(&h->ds.norb, n)) != cudaSuccess) return fail(e);
         if ((e = cudaMalloc(&h->ds.row_order, sizeof(int) * n)) != cudaSuccess) return fail(e);
-        if ((e = cudaMalloc(&h->ds.roff, sizeof(int64_t) * nb)) != cudaSuccess) return fail(e);
-        if ((e = cudaMalloc(&h->ds.S32r, sizeof(float) * std::max<int64_t>(tot, 4))) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&h->ds.bmeta, sizeof(int2) * nb)) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&h->ds.S32r, sizeof(float4) * std::max<int64_t>(tot, 1))) != cudaSuccess) return fail(e);
         if ((e = cudaMemcpyAsync(h->ds.norb, no.data(), n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
         if ((e = cudaMemcpyAsync(h->ds.row_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
-        if ((e = cudaMemcpyAsync(h->ds.roff, ro.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(h->ds.bmeta, bm.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
         h->ds.rag = 1;
         launch_compact_blocks(h->ds, st);
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);   // host vectors released at scope exit
@@ -1806,6 +1808,15 @@ tb_status tb_create_batch(tb_handle** out, const tb_system_desc* descs, int32_t 
     if ((e = cudaMemcpyAsync(h->orb2pad_local, h->orb2pad_local_h.data(), sizeof(int32_t) * ooff.back(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
     if (h->ds.rag) {
+        // block metadata with block columns local to their system (the
+        // views' indices); the whole handle, whose indices are global,
+        // keeps the padded form of the Chebyshev step
+        std::vector<int2> bm(bcol.size());
+        if ((e = cudaMemcpyAsync(bm.data(), h->ds.bmeta, sizeof(int2) * bm.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+        for (size_t b = 0; b < bm.size(); ++b) bm[b].x = bl[b];
+        if ((e = cudaMemcpyAsync(h->ds.bmeta, bm.data(), sizeof(int2) * bm.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
         // per system, its own block-row order in local atom indices
         std::vector<int> lo(aoff.back());
         for (int q = 0; q < n_systems; ++q) {
@@ -1833,6 +1844,7 @@ tb_status tb_create_batch(tb_handle** out, const tb_system_desc* descs, int32_t 
         v.grpG = 0;                 // the grouped SpMV's atom groups are built for the whole handle
         h->sys_ds.push_back(v);
     }
+    h->ds.rag = 0;
     return TB_OK;
 }
 

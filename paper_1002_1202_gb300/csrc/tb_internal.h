@@ -56,7 +56,9 @@ struct DevSystem {
     unsigned char* norb = nullptr;   // [n_atoms] 1 or 4
     int* row_order = nullptr;        // [n_atoms] atom of each block-row slot (indices of this view)
     float* S32r = nullptr;           // compact blocks
-    int64_t* roff = nullptr;         // [nb] float offset of block b in S32r
+    int2* bmeta = nullptr;           // [nb] per block: x = block-column atom (index of this view),
+                                     // y = offset of the block in S32r in float4 units, bit 31 set
+                                     // when the column atom has one orbital
     float* H32hi = nullptr;    // [nb][16] H rounded to FP32
     float* H32lo = nullptr;    // [nb][16] H - H_hi in FP32
     // atom groups of the grouped FP32 SpMV: group g = atoms [g * grpG, (g + 1) * grpG)

@@ -194,13 +194,13 @@ __global__ void k_transpose_blocks(const float* __restrict__ in, float* __restri
 // one thread per block row I, its blocks in order.
 __global__ void k_compact_blocks(int n_atoms, const int* __restrict__ brow, const int* __restrict__ bcol,
                                  const unsigned char* __restrict__ norb, const float* __restrict__ S32,
-                                 const int64_t* __restrict__ roff, float* __restrict__ out) {
+                                 const int2* __restrict__ bmeta, float* __restrict__ out) {
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < n_atoms; I += gridDim.x * blockDim.x) {
         const int ni = norb[I];
         for (int b = brow[I]; b < brow[I + 1]; ++b) {
             const int nj = norb[bcol[b]];
             const float* S = S32 + 16 * (size_t)b;
-            float* o = out + roff[b];
+            float* o = out + 4 * (size_t)(bmeta[b].y & 0x7fffffff);
             if (ni == 4 && nj == 4) {
                 for (int e = 0; e < 4; ++e)
                     for (int a = 0; a < 4; ++a) o[4 * e + a] = S[4 * a + e];
@@ -1397,16 +1397,23 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4r(DevSystem s, Pane
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
         const int b0 = s.brow[I], b1 = s.brow[I + 1];
-        int Jn = __ldg(s.bcol + b0);
+        // block metadata (column atom, compact offset, its orbital count)
+        // one block ahead, so the gathers of a block wait on nothing else
+        int2 mn = __ldg(s.bmeta + b0);
         for (int bb = b0; bb < b1; ++bb) {
-            const int J = Jn;
-            if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
-            const int nj = s.norb[J];
+            const int2 m = mn;
+            if (bb + 1 < b1) mn = __ldg(s.bmeta + bb + 1);
+            const int J = m.x;
+            const int nj = (m.y < 0) ? 1 : 4;
             const float2* xb = cur + (size_t)(4 * J) * P + 2 * t0;
-            const float4* Sr = reinterpret_cast<const float4*>(s.S32r + s.roff[bb]);
+            const float4* Sr = reinterpret_cast<const float4*>(s.S32r) + (m.y & 0x7fffffff);
             if (ni == 4) {
-                // nj rows e of the gathered d_k, column e of the block as four rows a
-                for (int e = 0; e < nj; ++e) {
+                // nj rows e of the gathered d_k, column e of the block as four
+                // rows a (unrolled with the row count as a predicate, so the
+                // loads of all rows are issued together)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (e >= nj) break;
                     const float4 xa = *reinterpret_cast<const float4*>(xb + (size_t)e * P);
                     const float4 xq = *reinterpret_cast<const float4*>(xb + (size_t)e * P + pstride);
                     const float4 sc = __ldg(Sr + e);
@@ -1424,7 +1431,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4r(DevSystem s, Pane
                 // one output row: row 0 of the block (S[0][0 .. nj))
                 const float4 sr = __ldg(Sr);
                 const float sv[4] = {sr.x, sr.y, sr.z, sr.w};
-                for (int e = 0; e < nj; ++e) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (e >= nj) break;
                     const float4 xa = *reinterpret_cast<const float4*>(xb + (size_t)e * P);
                     const float4 xq = *reinterpret_cast<const float4*>(xb + (size_t)e * P + pstride);
                     const float2 s2 = make_float2(sv[e], sv[e]);
@@ -2598,7 +2607,8 @@ void launch_transpose_blocks(const float* in, float* out, long long nb, cudaStre
 }
 void launch_compact_blocks(const DevSystem& s, cudaStream_t st) {
     LaunchScope ls_(K_OTHER, st);
-    k_compact_blocks<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s.n_atoms, s.brow, s.bcol, s.norb, s.S32, s.roff, s.S32r);
+    k_compact_blocks<<<grid_for(s.n_atoms), THREADS, 0, st>>>(s.n_atoms, s.brow, s.bcol, s.norb, s.S32, s.bmeta,
+                                                               s.S32r);
 }
 void launch_ased_build(const DevSystem& s, const double* eps_pad, double K, cudaStream_t st) {
     {
