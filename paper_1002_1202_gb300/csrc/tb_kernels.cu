@@ -53,22 +53,28 @@ __device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
 // two-sum of hi + p whose error goes to lo.  The _rn intrinsics keep the
 // compiler from contracting these steps into FMAs, which would break the
 // error terms.  Relative accuracy of a sum of n products ~ n * 2^-46.
-__device__ __forceinline__ void df_mac(float& hi, float& lo, float sh, float sl, float xh, float xl) {
-    const float pr = __fmul_rn(sh, xh);
-    float e = fmaf(sh, xh, -pr);
-    e = fmaf(sh, xl, e);
-    e = fmaf(sl, xh, e);
-    const float t = __fadd_rn(hi, pr);
-    const float bp = __fsub_rn(t, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+// df_mac2 does this for a (re, im) pair that shares s, in packed FP32
+// instructions (two lanes each, round-to-nearest per lane: each lane
+// computes exactly the scalar sequence); a - b is a + (-b), which is exact.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void df_mac2(float2& hi, float2& lo, float sh, float sl, float2 xh, float2 xl) {
+    const float2 s2h = make_float2(sh, sh), s2l = make_float2(sl, sl);
+    const float2 pr = __fmul2_rn(s2h, xh);
+    float2 e = __ffma2_rn(s2h, xh, neg2(pr));
+    e = __ffma2_rn(s2h, xl, e);
+    e = __ffma2_rn(s2l, xh, e);
+    const float2 t = __fadd2_rn(hi, pr);
+    const float2 bp = __fadd2_rn(t, neg2(hi));
+    const float2 err = __fadd2_rn(__fadd2_rn(hi, neg2(__fadd2_rn(t, neg2(bp)))), __fadd2_rn(pr, neg2(bp)));
     hi = t;
-    lo = __fadd_rn(lo, __fadd_rn(err, e));
+    lo = __fadd2_rn(lo, __fadd2_rn(err, e));
 }
 
-// complex double -> (re_hi, re_lo, im_hi, im_lo)
+// complex double -> (re_hi, im_hi, re_lo, im_lo): the hi and lo pairs are
+// the two float2 operands of df_mac2
 __device__ __forceinline__ float4 df_split(double2 v) {
     const float rh = (float)v.x, ih = (float)v.y;
-    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
 }
 
 // Sum NV per-thread values over the threads of a CTA that share a column
@@ -254,12 +260,13 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
             const int I = (int)(idx / P);
             double2 aS[4], aH[4];
             if (DF) {
-                // double-float products: S_hi/S_lo, H_hi/H_lo times the split r'
-                float sh[4][2], sl[4][2], hh[4][2], hl[4][2];
+                // double-float products: S_hi/S_lo, H_hi/H_lo times the split r',
+                // the real and imaginary parts in the two lanes of packed FP32 ops
+                float2 sh[4], sl[4], hh[4], hl[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) { sh[a][q] = 0.f; sl[a][q] = 0.f; hh[a][q] = 0.f; hl[a][q] = 0.f; }
+                for (int a = 0; a < 4; ++a) {
+                    sh[a] = sl[a] = hh[a] = hl[a] = make_float2(0.f, 0.f);
+                }
                 for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
                     const int J = s.bcol[b];
                     const float4* xr = p.RpS + (size_t)4 * J * P + c;
@@ -276,16 +283,14 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
                             const float4 s4h = __ldg(Sh + a), s4l = __ldg(Sl + a);
                             const float svh[4] = {s4h.x, s4h.y, s4h.z, s4h.w}, svl[4] = {s4l.x, s4l.y, s4l.z, s4l.w};
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                df_mac(sh[a][0], sl[a][0], svh[e], svl[e], x[e].x, x[e].y);
-                                df_mac(sh[a][1], sl[a][1], svh[e], svl[e], x[e].z, x[e].w);
-                            }
+                            for (int e = 0; e < 4; ++e)
+                                df_mac2(sh[a], sl[a], svh[e], svl[e], make_float2(x[e].x, x[e].y),
+                                        make_float2(x[e].z, x[e].w));
                         }
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            df_mac(hh[a][0], hl[a][0], hvh[e], hvl[e], x[e].x, x[e].y);
-                            df_mac(hh[a][1], hl[a][1], hvh[e], hvl[e], x[e].z, x[e].w);
-                        }
+                        for (int e = 0; e < 4; ++e)
+                            df_mac2(hh[a], hl[a], hvh[e], hvl[e], make_float2(x[e].x, x[e].y),
+                                    make_float2(x[e].z, x[e].w));
                     }
                 }
 #pragma unroll
@@ -294,9 +299,9 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
                         const size_t e = (size_t)(4 * I + a) * P + c;
                         aS[a] = csub(p.Rcur[e], p.Rin[e]);
                     } else {
-                        aS[a] = cmk((double)sh[a][0] + (double)sl[a][0], (double)sh[a][1] + (double)sl[a][1]);
+                        aS[a] = cmk((double)sh[a].x + (double)sl[a].x, (double)sh[a].y + (double)sl[a].y);
                     }
-                    aH[a] = cmk((double)hh[a][0] + (double)hl[a][0], (double)hh[a][1] + (double)hl[a][1]);
+                    aH[a] = cmk((double)hh[a].x + (double)hl[a].x, (double)hh[a].y + (double)hl[a].y);
                 }
             } else {
 #pragma unroll
@@ -571,9 +576,9 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
             const int I = (int)(idx / P);
             double2 acc[4];
             if (DF) {
-                float ah[4][2], al[4][2];
+                float2 ah[4], al[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) { ah[a][0] = ah[a][1] = al[a][0] = al[a][1] = 0.f; }
+                for (int a = 0; a < 4; ++a) ah[a] = al[a] = make_float2(0.f, 0.f);
                 for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
                     const int J = s.bcol[bb];
                     const float4* xr = p.RpS + (size_t)4 * J * P + c;
@@ -585,15 +590,14 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
                         const float4 s4h = __ldg(Sh + a), s4l = __ldg(Sl + a);
                         const float svh[4] = {s4h.x, s4h.y, s4h.z, s4h.w}, svl[4] = {s4l.x, s4l.y, s4l.z, s4l.w};
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            df_mac(ah[a][0], al[a][0], svh[e], svl[e], x[e].x, x[e].y);
-                            df_mac(ah[a][1], al[a][1], svh[e], svl[e], x[e].z, x[e].w);
-                        }
+                        for (int e = 0; e < 4; ++e)
+                            df_mac2(ah[a], al[a], svh[e], svl[e], make_float2(x[e].x, x[e].y),
+                                    make_float2(x[e].z, x[e].w));
                     }
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
-                    acc[a] = cmk((double)ah[a][0] + (double)al[a][0], (double)ah[a][1] + (double)al[a][1]);
+                    acc[a] = cmk((double)ah[a].x + (double)al[a].x, (double)ah[a].y + (double)al[a].y);
             } else {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) acc[a] = cmk(0.0, 0.0);
@@ -2767,6 +2771,7 @@ static void cheb_launch(const DevSystem& s, const PanelDev& p, const float2* cur
         cheb4_launch<LAST>(s, p, cur, io, omega, gamma, mode, st);
         return;
     }
+
     if (p.P >= 2) {
         const int g = grid_for((long long)s.n_atoms * (p.P / 2));
         switch (p.P) {
