@@ -243,7 +243,44 @@ __global__ void k_panel_init(PanelDev p) {
 // the refinement's last double-float residual (in Rin), so only H r'_n is
 // formed here -- half the double-float products.
 // ---------------------------------------------------------------------------
-template <bool DF, bool SX = false>
+// One block row of a double-float SpMV (M = Mh + Ml, FP32 hi / lo blocks,
+// times the split r') with exact orbital counts (systems with s-only atoms):
+// only the ni real rows of atom I and, per block, the real rows of the
+// column atom (one for an s atom, read with the column S[.][0]) -- the
+// padded entries would only add exact zeros.
+__device__ __forceinline__ void df_row_ragged(const DevSystem& s, const float* __restrict__ Mh,
+                                              const float* __restrict__ Ml, int I, int ni,
+                                              const float4* __restrict__ RpS, int P, int c, float2 (&hi)[4],
+                                              float2 (&lo)[4]) {
+    for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
+        const int2 m = __ldg(s.bmeta + bb);
+        const float4* xr = RpS + (size_t)4 * m.x * P + c;
+        if (m.y >= 0) {
+            const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
+            const float4* Bh = reinterpret_cast<const float4*>(Mh + 16 * (size_t)bb);
+            const float4* Bl = reinterpret_cast<const float4*>(Ml + 16 * (size_t)bb);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (a >= ni) break;
+                const float4 v4h = __ldg(Bh + a), v4l = __ldg(Bl + a);
+                const float vh[4] = {v4h.x, v4h.y, v4h.z, v4h.w}, vl[4] = {v4l.x, v4l.y, v4l.z, v4l.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    df_mac2(hi[a], lo[a], vh[e], vl[e], make_float2(x[e].x, x[e].y), make_float2(x[e].z, x[e].w));
+            }
+        } else {
+            const float4 x0 = xr[0];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (a >= ni) break;
+                df_mac2(hi[a], lo[a], __ldg(Mh + 16 * (size_t)bb + 4 * a), __ldg(Ml + 16 * (size_t)bb + 4 * a),
+                        make_float2(x0.x, x0.y), make_float2(x0.z, x0.w));
+            }
+        }
+    }
+}
+
+template <bool DF, bool SX = false, bool RAG = false>
 __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p) {
     __shared__ double smem[2 * THREADS];
     const int P = p.P;
@@ -267,7 +304,12 @@ __global__ void __launch_bounds__(THREADS) k_outer_spmm(DevSystem s, PanelDev p)
                 for (int a = 0; a < 4; ++a) {
                     sh[a] = sl[a] = hh[a] = hl[a] = make_float2(0.f, 0.f);
                 }
-                for (int b = s.brow[I]; b < s.brow[I + 1]; ++b) {
+                if (RAG) {
+                    const int ni = s.norb[I];
+                    df_row_ragged(s, s.H32hi, s.H32lo, I, ni, p.RpS, P, c, hh, hl);
+                    if (!SX) df_row_ragged(s, s.S32, s.S32lo, I, ni, p.RpS, P, c, sh, sl);
+                }
+                for (int b = RAG ? s.brow[I + 1] : s.brow[I]; b < s.brow[I + 1]; ++b) {
                     const int J = s.bcol[b];
                     const float4* xr = p.RpS + (size_t)4 * J * P + c;
                     const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
@@ -562,7 +604,7 @@ __global__ void __launch_bounds__(THREADS) k_refine_start(PanelDev p, const doub
 
 // res = b - S x in FP64 (x = r') into Rin; columns already within inner_tol
 // are marked to skip the next round, the others get scale = 1 / ||res||.
-template <bool DF>
+template <bool DF, bool RAG = false>
 __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelDev p, const double2* __restrict__ b) {
     __shared__ double smem[2 * THREADS];
     const int P = p.P;
@@ -579,7 +621,8 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
                 float2 ah[4], al[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) ah[a] = al[a] = make_float2(0.f, 0.f);
-                for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
+                if (RAG) df_row_ragged(s, s.S32, s.S32lo, I, s.norb[I], p.RpS, P, c, ah, al);
+                for (int bb = RAG ? s.brow[I + 1] : s.brow[I]; bb < s.brow[I + 1]; ++bb) {
                     const int J = s.bcol[bb];
                     const float4* xr = p.RpS + (size_t)4 * J * P + c;
                     const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
@@ -2555,6 +2598,12 @@ double profile_busy(int id) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// TB_DF_RAG=0: systems with s-only atoms take the padded double-float SpMVs
+static const bool g_df_rag = [] {
+    const char* e = std::getenv("TB_DF_RAG");
+    return !(e && std::atoi(e) == 0);
+}();
+
 static int gmax() {
     static const int g = [] {
         int dev = 0, sms = 0;
@@ -2629,8 +2678,13 @@ void launch_panel_init(const DevSystem&, const PanelDev& p, cudaStream_t st) {
 void launch_outer_spmm(const DevSystem& s, const PanelDev& p, bool sx_from_residual, cudaStream_t st) {
     {
         LaunchScope ls_(K_OUTER_SPMM, st);
-        if (p.mixed && sx_from_residual)
+        const bool rag = s.rag && g_df_rag;
+        if (p.mixed && sx_from_residual && rag)
+            k_outer_spmm<true, true, true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+        else if (p.mixed && sx_from_residual)
             k_outer_spmm<true, true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
+        else if (p.mixed && rag)
+            k_outer_spmm<true, false, true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
         else if (p.mixed)
             k_outer_spmm<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p);
         else
@@ -2667,7 +2721,10 @@ void launch_refine_start(const DevSystem&, const PanelDev& p, const double2* b, 
 }
 void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_RESIDUAL, st);
-    k_refine_residual<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
+    if (s.rag && g_df_rag)
+        k_refine_residual<true, true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
+    else
+        k_refine_residual<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
 }
 void launch_refine_scale(const DevSystem&, const PanelDev& p, const double2* src, float cheb_gamma, cudaStream_t st) {
     LaunchScope ls_(K_REFINE_AUX, st);

@@ -174,10 +174,10 @@ def test_autotune_choice_is_used(P):
 def test_ragged_chebyshev_step_equals_padded(P, tmp_path):
     """Water (O: s, p; H: s) with exact orbital counts in the Chebyshev step
     (compact blocks, one gathered row per H neighbour, one output row per H
-    atom; default) against the padded form (TB_CHEB_RAG=0, child process):
-    the padded form only adds exact zeros (padded rows of the vectors) in
-    the same order, so the populations are bit-identical, on one box and on
-    a ragged batch."""
+    atom) and in the double-float SpMVs (default) against the padded forms
+    (TB_CHEB_RAG=0, TB_DF_RAG=0, child process): the padded forms only add
+    exact zeros (padded rows of the vectors) in the same order, so the
+    populations are bit-identical, on one box and on a ragged batch."""
     import os
     import subprocess
     import sys
@@ -198,7 +198,7 @@ def test_ragged_chebyshev_step_equals_padded(P, tmp_path):
         "h1 = P.tb_create_system(systems[2])\n"
         "q1, _ = P.tb_mulliken_charges(h1, z, w, opts=P.tb_default_opts(precision=1))\n"
         f"np.savez({str(out)!r}, q=q.cpu().numpy(), q1=q1.cpu().numpy())\n")
-    env = dict(os.environ, TB_CHEB_RAG="0", PYTHONPATH=root)
+    env = dict(os.environ, TB_CHEB_RAG="0", TB_DF_RAG="0", PYTHONPATH=root)
     subprocess.run([sys.executable, "-c", child], env=env, cwd=root, check=True, timeout=600)
     ref = np.load(out)
     assert np.array_equal(ref["q"], q.cpu().numpy())
