@@ -142,3 +142,48 @@ def test_lanczos_continued_fraction_vs_exact(si64_dense):
     g = method.lanczos_green(a, b, nrm2, z)
     ref = dense.green_columns(H, S, z, [j])[:, j, 0]
     assert np.abs(g - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+class _RoundedFP32:
+    """A matrix whose products with a vector are taken in FP32 (matrix and
+    vector rounded to FP32 / complex64, the product accumulated there and
+    widened again): the literal FP32 reading of the mixed-precision
+    direction applied to every product of the method, outer and inner."""
+
+    def __init__(self, M):
+        self.M = np.asarray(M, dtype=np.float32)
+        self.shape = self.M.shape
+
+    def __matmul__(self, v):
+        if np.iscomplexobj(v):
+            return (self.M @ v.astype(np.complex64)).astype(np.complex128)
+        return (self.M @ v.astype(np.float32)).astype(np.float64)
+
+
+@pytest.mark.slow
+def test_fp32_products_miss_the_population_bar(si64, si64_dense):
+    """Why the mixed path keeps the outer recurrence at FP64 accuracy: on the
+    64-atom case with eta = 0.01 eV, the method with every H and S product in
+    FP32 (above) misses the 1e-6 e bar on the Mulliken populations -- it stops
+    converging or converges to the wrong populations -- while the same
+    method in FP64 meets it.  FP32 roundings enter a Krylov recurrence whose
+    matrix has cond ~ 1e4."""
+    import math
+    H, S = si64_dense
+    z, w = linspace_grid(32)
+    ref = dense.mulliken_orbital(H, S, z, w, 2.0)
+    worst64, worst32, conv32 = 0.0, 0.0, True
+    for j in (3, 130):
+        F = S[j][None, :]
+        for mats, tag in (((H, S), 64), ((_RoundedFP32(H), _RoundedFP32(S)), 32)):
+            out = method.generalized_shifted_cocg(mats[0], mats[1], z, j, tol=1e-10, inner_tol=1e-13,
+                                                  max_iter=3000, keep_full=False, functionals=F)
+            q = -(2.0 / math.pi) * np.imag(np.sum(w * out["t"][:, 0]))
+            if tag == 64:
+                assert out["converged"]
+                worst64 = max(worst64, abs(q - ref[j]))
+            else:
+                conv32 = conv32 and out["converged"]
+                worst32 = max(worst32, abs(q - ref[j]))
+    assert worst64 <= 1e-8
+    assert (not conv32) or worst32 > 1e-6, (conv32, worst32)
