@@ -97,6 +97,8 @@ def parse():
                          "time and HBM fraction per panel width, mixed vs FP64 calls and their populations")
     ap.add_argument("--adjoint-full", action="store_true",
                     help="measure the band-energy adjoint and forces on the cracked 7680-atom Si slab instead")
+    ap.add_argument("--adjoint-cells", type=int, default=10,
+                    help="diamond cells per edge of the cracked slab of --adjoint-full (10: the 7680-atom workload)")
     ap.add_argument("--batch-full", action="store_true",
                     help="instead of the benchmark step: 64 liquid-water boxes of 512-1536 molecules (+H3O+) as one "
                          "ragged batch, 64 columns per box, 128 shifts, 20 outer iterations per call")
@@ -830,9 +832,12 @@ def run_adjoint_full(args):
     P = __import__("paper_1002_1202_gb300")
     P.build()
     t0 = time.time()
-    s = si_slab_system()
+    c = args.adjoint_cells
+    s = si_slab_system(cells=(c, c, c))
     dS = overlap_bond_derivatives(s)
     build_s = time.time() - t0
+    print("slab %d atoms, N=%d, %d blocks built in %.1f s" % (s.n_atoms, s.n_orb, s.nb, build_s),
+          file=sys.stderr, flush=True)
     z, w = gauss_legendre_grid(128, -20.0, 5.0, 1.0)
     h = P.tb_create_system(s)
     opts = P.tb_default_opts(tol=1e-8, precision=1)
@@ -849,9 +854,9 @@ def run_adjoint_full(args):
     t_e = ev[0].elapsed_time(ev[1]) / 1e3
     print(json.dumps({
         "metric": "adjoint_full", "unit": UNIT,
-        "workload": "cracked Si slab 10x10x10 cells, %d atoms, N=%d, %d blocks; 128 GL shifts on [-20,5] eV + 1i eV; "
+        "workload": "cracked Si slab %dx%dx%d cells, %d atoms, N=%d, %d blocks; 128 GL shifts on [-20,5] eV + 1i eV; "
                     "band energy, dE/dH and dE/dS at every stored entry, forces; mixed precision" % (
-                        s.n_atoms, s.n_orb, s.nb),
+                        c, c, c, s.n_atoms, s.n_orb, s.nb),
         "host_build_s": build_s, "band_energy_s": t_e, "forces_ms": ev[1].elapsed_time(ev[2]),
         "status": st["status"], "E_eV": E, "outer_iterations": st["outer_iterations"],
         "value": 128 * st["outer_iterations"] / t_e, "gradient_entries": int(len(s.S_vals)),

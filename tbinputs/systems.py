@@ -290,23 +290,31 @@ def overlap_bond_derivatives(system, h=1e-5) -> np.ndarray:
     s = system
     pos = np.asarray(s.positions, dtype=np.float64)
     box = np.asarray(s.box, dtype=np.float64)
-    bo = s.block_offsets()
+    bo = np.asarray(s.block_offsets())
     out = np.zeros((3, len(s.S_vals)))
     rows = np.repeat(np.arange(s.n_atoms), np.diff(s.brow_ptr))
-    for b in range(s.nb):
-        i, j = rows[b], s.bcol[b]
-        if i == j:
-            continue
-        d = pos[j] - pos[i]
-        for ax in range(3):
-            if s.pbc[ax]:
-                d[ax] -= box[ax] * np.round(d[ax] / box[ax])
-        A, B = s.species[i], s.species[j]
+    cols = np.asarray(s.bcol)
+    off = np.flatnonzero(rows != cols)
+    d = pos[cols[off]] - pos[rows[off]]
+    for ax in range(3):
+        if s.pbc[ax]:
+            d[:, ax] -= box[ax] * np.round(d[:, ax] / box[ax])
+    # one vectorised call per species pair and axis
+    kind = {}
+    for b, i, j in zip(off, rows[off], cols[off]):
+        kind.setdefault((id(s.species[i]), id(s.species[j])), (s.species[i], s.species[j], []))[2].append(b)
+    pos_in_off = np.empty(s.nb, dtype=np.int64)
+    pos_in_off[off] = np.arange(len(off))
+    for A, B, blocks in kind.values():
+        blocks = np.asarray(blocks)
+        D = d[pos_in_off[blocks]]
+        n_e = A.n_orb * B.n_orb
+        idx = bo[blocks][:, None] + np.arange(n_e)[None, :]
         for ax in range(3):
             e = np.zeros(3)
             e[ax] = h
-            diff = (bond_blocks(A, B, d + e) - bond_blocks(A, B, d - e))[0] / (2 * h)
-            out[ax, bo[b]:bo[b + 1]] = diff.ravel()
+            diff = (bond_blocks(A, B, D + e) - bond_blocks(A, B, D - e)) / (2 * h)
+            out[ax, idx] = diff.reshape(len(blocks), n_e)
     return out
 
 
