@@ -99,6 +99,8 @@ def parse():
                     help="measure the band-energy adjoint and forces on the cracked 7680-atom Si slab instead")
     ap.add_argument("--adjoint-cells", type=int, default=10,
                     help="diamond cells per edge of the cracked slab of --adjoint-full (10: the 7680-atom workload)")
+    ap.add_argument("--adjoint-profile", action="store_true",
+                    help="with --adjoint-full: per-kernel device time of the band-energy call (library CUDA events)")
     ap.add_argument("--batch-full", action="store_true",
                     help="instead of the benchmark step: 64 liquid-water boxes of 512-1536 molecules (+H3O+) as one "
                          "ragged batch, 64 columns per box, 128 shifts, 20 outer iterations per call")
@@ -843,6 +845,8 @@ def run_adjoint_full(args):
     opts = P.tb_default_opts(tol=1e-8, precision=1)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    if args.adjoint_profile:
+        P.tb_profile_enable(True)
     torch.cuda.synchronize()
     ev[0].record(stream)
     E, gH, gS, st = P.tb_band_energy(h, z, w, opts=opts, n_values=len(s.S_vals))
@@ -850,6 +854,11 @@ def run_adjoint_full(args):
     F = P.tb_forces(h, gH, gS, dS)
     ev[2].record(stream)
     ev[2].synchronize()
+    kernel_ms = None
+    if args.adjoint_profile:
+        kernel_ms = {k: [v[0], round(v[1], 3)] for k, v in ((k, P.tb_profile_read(k)) for k in P.tb.KERNELS)
+                     if v[0] > 0}
+        P.tb_profile_enable(False)
     F = np.asarray(F.cpu().numpy() if hasattr(F, "cpu") else F)
     t_e = ev[0].elapsed_time(ev[1]) / 1e3
     print(json.dumps({
@@ -860,7 +869,8 @@ def run_adjoint_full(args):
         "host_build_s": build_s, "band_energy_s": t_e, "forces_ms": ev[1].elapsed_time(ev[2]),
         "status": st["status"], "E_eV": E, "outer_iterations": st["outer_iterations"],
         "value": 128 * st["outer_iterations"] / t_e, "gradient_entries": int(len(s.S_vals)),
-        "net_force_over_max": float(np.abs(F.sum(axis=0)).max() / max(np.abs(F).max(), 1e-300))}))
+        "net_force_over_max": float(np.abs(F.sum(axis=0)).max() / max(np.abs(F).max(), 1e-300)),
+        "kernel_launches_ms": kernel_ms}))
     return 0
 
 

@@ -150,6 +150,10 @@ tb_status tb_overlap_bounds_desc(const tb_system_desc *d, double *lo, double *hi
  * recurrence d_{k+1} = d_{k-1} + omega[k] (gamma (f - S d_k) + d_k - d_{k-1}),
  * d_0 = 0, d_1 = gamma f.  omega: float [omega_len] or NULL.  *n = 0 when
  * lo <= 0, hi <= lo or n > cap (the FP32 CG corrections are used then).
+ * A column that ends the planned rounds above inner_tol (the double-float
+ * residual of the refinement is only good to ~2^-47 |S| |x|) runs up to two
+ * more rounds of n_last steps, each checked by a residual with FP64
+ * products, then FP32 CG rounds.
  */
 tb_status tb_chebyshev_plan(double lo, double hi, double lo_tol, double inner_tol, int32_t cap, int32_t *n,
                             int32_t *n_last, int32_t *rounds, double *gamma, float *omega, int32_t omega_len);

@@ -387,13 +387,25 @@ tb_status s_bounds(tb_handle* h, double& lo, double& hi) {
 // reduction reaches inner_tol; the last one needs only that remainder
 // (with a factor 2 to spare) and takes n_last <= n steps.  The recurrence
 // coefficients do not depend on where it stops, so both share omega.
+// A column can end the planned rounds above inner_tol although its true
+// residual is below: the double-float residual carries S and x to ~48 bits,
+// so its own error is ~2^-47 |S| |x|, which on a cracked Si slab (lambda_min
+// of S 0.146, |x| up to ~7 |b|) is ~2e-13 |b|, above inner_tol = 1e-13.  Such
+// a column takes up to SPARE more rounds of n_last steps, each followed by
+// the residual with FP64 products (only the columns still open do work), and
+// only then the FP32 CG.
 struct ChebPlan {
+    static constexpr int SPARE = 2;
     int n = 0;                 // 0: FP32 CG corrections
-    int n_last = 0;            // steps of round R - 1
+    int n_last = 0;            // steps of round R - 1 and of the spare rounds
     int R = 1;                 // rounds planned
     float gamma = 0.f;
     std::vector<float> omega;  // omega[k] multiplies step k (1 <= k < n)
-    int steps(int round) const { return round == R - 1 ? n_last : n; }
+    int steps(int round) const { return round >= R - 1 ? n_last : n; }
+    bool chebyshev(int round) const { return n > 0 && round < R + SPARE; }
+    // the residual after this round in FP64 (spare rounds; with FP32 CG
+    // corrections, from the third round on)
+    bool fp64_residual(int round) const { return round >= (n > 0 ? R : 2); }
 };
 
 static int cheb_steps(double sigma, double tol) {
@@ -513,9 +525,10 @@ static const bool g_graphs = [] {
 tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_max, int& pred32,
                       int& rounds_pred, int64_t& inner_total, const ChebPlan& cp, cudaGraphExec_t* graph,
                       cudaStream_t st, int first_round = 0, bool capture = false) {
-    // Chebyshev corrections for the first rounds (no host round trip); a
-    // solve that needs more rounds than that finishes with FP32 CG
-    auto cheb_round = [&](int round) { return cp.n > 0 && round < 3; };
+    // Chebyshev corrections for the planned and the spare rounds (no host
+    // round trip); a solve that needs more rounds than that finishes with
+    // FP32 CG
+    auto cheb_round = [&](int round) { return cp.chebyshev(round); };
     if (first_round == 0) {
         launch_refine_start(v.ds, p, b, st);
         launch_refine_scale(v.ds, p, b, cheb_round(0) ? cp.gamma : 0.f, st);   // f and d_1
@@ -575,7 +588,7 @@ tb_status mixed_inner(View& v, const PanelDev& p, const double2* b, int inner_ma
         }
         launch_refine_add(v.ds, p, st);
         }
-        launch_refine_residual(v.ds, p, b, st);
+        launch_refine_residual(v.ds, p, b, st, cp.fp64_residual(round));
         launch_refine_scale(v.ds, p, p.Rin, cheb_round(round + 1) ? cp.gamma : 0.f, st);
         if (g_trace) {
             cudaMemcpyAsync(v.flags_host, p.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -919,7 +932,7 @@ tb_status run_view(View& v, const Solve& q, const tb_solve_opts* o, tb_stats* st
         bool tail_pending = false;
         for (int n = 0; n < o->max_iter; ++n) {
             const bool use_graph = tail_pending && g_graphs && g_step_graphs && !g_trace && p.mixed &&
-                                   ic.cheb.n > 0 && ic.rounds <= 3 && ic.res_exact && !sg.failed;
+                                   ic.cheb.n > 0 && ic.cheb.chebyshev(ic.rounds - 1) && ic.res_exact && !sg.failed;
             if (use_graph && (!sg.exec || sg.rounds != ic.rounds))
                 step_graph_build(v, p, ic, q.proj, o->inner_max_iter, sg);
             if (use_graph && sg.exec) {

@@ -188,7 +188,10 @@ void launch_inner_spmv(const DevSystem& s, const PanelDev& p, int it, cudaStream
 void launch_inner_update(const DevSystem& s, const PanelDev& p, int it, cudaStream_t st);
 void launch_finish(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_refine_start(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st);
-void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st);
+// fp64: the residual with FP64 products (below the ~2^-47 relative floor of
+// the double-float form) for the columns still above inner_tol
+void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st,
+                            bool fp64 = false);
 void launch_refine_add(const DevSystem& s, const PanelDev& p, cudaStream_t st);
 void launch_refine_scale(const DevSystem& s, const PanelDev& p, const double2* src, float cheb_gamma, cudaStream_t st);
 void launch_split_panel(const PanelDev& p, cudaStream_t st);

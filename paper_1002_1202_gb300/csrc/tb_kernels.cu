@@ -2719,9 +2719,11 @@ void launch_refine_start(const DevSystem&, const PanelDev& p, const double2* b, 
     LaunchScope ls_(K_REFINE_AUX, st);
     k_refine_start<<<grid_for((long long)p.npad * p.P), THREADS, 0, st>>>(p, b);
 }
-void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st) {
+void launch_refine_residual(const DevSystem& s, const PanelDev& p, const double2* b, cudaStream_t st, bool fp64) {
     LaunchScope ls_(K_REFINE_RESIDUAL, st);
-    if (s.rag && g_df_rag)
+    if (fp64)   // FP64 products; columns already within inner_tol exit at once
+        k_refine_residual<false><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
+    else if (s.rag && g_df_rag)
         k_refine_residual<true, true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
     else
         k_refine_residual<true><<<grid_for((long long)s.n_atoms * p.P), THREADS, 0, st>>>(s, p, b);
