@@ -287,6 +287,24 @@ def test_slab_cutout_adjoint_vs_dense(P, slab, prec):
     assert np.abs(_dense_blocks(c, vS)[mask] - rS[mask]).max() <= 1e-7 * np.abs(rS).max()
 
 
+def test_slab_mixed_inner_solves_need_no_fp64_redo(P):
+    """The band energy of a 4 x 4 x 4-cell cracked slab (480 atoms, all 1920
+    columns, 128 shifts) in mixed precision: every inner solve reaches
+    inner_tol on the mixed path.  Here lambda_min(S) = 0.146, so the
+    double-float residual's own error (~2^-47 |S| |x|) can sit above
+    inner_tol = 1e-13 for a column whose true residual is below; such a
+    column must be settled by the FP64-checked spare rounds, not by an FP64
+    CG redo of its panel (14 redos on this system before they existed)."""
+    from tbinputs import si_slab_system, gauss_legendre_grid
+    s = si_slab_system(cells=(4, 4, 4))
+    z, w = gauss_legendre_grid(128, -20.0, 5.0, 1.0)
+    h = P.tb_create_system(s)
+    E, gH, gS, st = P.tb_band_energy(h, z, w, opts=P.tb_default_opts(tol=1e-8, precision=1),
+                                     n_values=len(s.S_vals))
+    assert st["unconverged"] == 0 and np.isfinite(E)
+    assert st["inner_redos"] == 0, st
+
+
 def _slab_vjp_finite_differences(P, s, n_each):
     """L = sum_a v_a q_a with weights on the 16 orbitals of the 4 atoms
     nearest the crack tip; dL/dH and dL/dS from the device VJP (mixed
