@@ -1621,6 +1621,20 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
                 for (int a = ni; a < 4; ++a) Sp[16 * b + 5 * a] = 1.0;   // padded slot: S = 1, H = 0
         }
     }
+    // identity diagonal blocks of S (padded slots included); TB_UNIT_DIAG=0
+    // keeps the diagonal blocks in the FP32 products
+    const char* ud_env = std::getenv("TB_UNIT_DIAG");
+    bool unit_diag = !(ud_env && std::atoi(ud_env) == 0);
+    for (int i = 0; i < n && unit_diag; ++i) {
+        int ndiag = 0;
+        for (int64_t b = d->brow_ptr[i]; b < d->brow_ptr[i + 1]; ++b) {
+            if (d->bcol[b] != i) continue;
+            ++ndiag;
+            for (int q = 0; q < 16; ++q)
+                if (Sp[16 * b + q] != (q % 5 == 0 ? 1.0 : 0.0)) unit_diag = false;
+        }
+        if (ndiag != 1) unit_diag = false;
+    }
     std::vector<double> epsp((size_t)4 * n, 0.0);
     std::vector<int32_t> o2p(N);
     for (int i = 0; i < n; ++i)
@@ -1645,6 +1659,7 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     h->ds.n_atoms = n;
     h->ds.nb = nb;
     h->ds.npad = 4 * n;
+    h->ds.unit_diag = unit_diag ? 1 : 0;
     cudaGetDevice(&h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [&](cudaError_t e) {

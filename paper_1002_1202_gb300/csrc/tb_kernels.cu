@@ -251,9 +251,10 @@ __global__ void k_panel_init(PanelDev p) {
 __device__ __forceinline__ void df_row_ragged(const DevSystem& s, const float* __restrict__ Mh,
                                               const float* __restrict__ Ml, int I, int ni,
                                               const float4* __restrict__ RpS, int P, int c, float2 (&hi)[4],
-                                              float2 (&lo)[4]) {
+                                              float2 (&lo)[4], int skip_atom = -1) {
     for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
         const int2 m = __ldg(s.bmeta + bb);
+        if (m.x == skip_atom) continue;
         const float4* xr = RpS + (size_t)4 * m.x * P + c;
         if (m.y >= 0) {
             const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
@@ -621,9 +622,12 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
                 float2 ah[4], al[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) ah[a] = al[a] = make_float2(0.f, 0.f);
-                if (RAG) df_row_ragged(s, s.S32, s.S32lo, I, s.norb[I], p.RpS, P, c, ah, al);
+                // an identity diagonal block is left out: its product is x_I,
+                // taken exactly from the FP64 solution below
+                if (RAG) df_row_ragged(s, s.S32, s.S32lo, I, s.norb[I], p.RpS, P, c, ah, al, s.unit_diag ? I : -1);
                 for (int bb = RAG ? s.brow[I + 1] : s.brow[I]; bb < s.brow[I + 1]; ++bb) {
                     const int J = s.bcol[bb];
+                    if (s.unit_diag && J == I) continue;
                     const float4* xr = p.RpS + (size_t)4 * J * P + c;
                     const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
                     const float4* Sh = reinterpret_cast<const float4*>(s.S32 + 16 * (size_t)bb);
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const size_t e = (size_t)(4 * I + a) * P + c;
-                const double2 r = csub(b[e], acc[a]);
+                const double2 r = (DF && s.unit_diag) ? csub(csub(b[e], p.Rp[e]), acc[a]) : csub(b[e], acc[a]);
                 p.Rin[e] = r;
                 v[0] += r.x * r.x;
                 v[1] += r.y * r.y;
@@ -1225,7 +1229,10 @@ __device__ __forceinline__ bool cheb_live(const PanelDev& p, int c) {
 // read).  mode 2 (the LAST instance): the last step, which adds its result
 // to the FP64 solution of the refinement instead of storing it
 // (x += d_n / scale and the double-float split, as k_refine_add; a
-// non-finite value is dropped).
+// non-finite value is dropped).  When every diagonal block of S is the
+// identity (s.unit_diag: orthonormal orbitals on one atom), the gather skips
+// it and S cur = (S - 1) cur + cur takes the own rows of cur, which the
+// update reads anyway: one block of ~17 per block row fewer to gather.
 template <int CPT, int PW = 0, bool LAST = false>
 __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelDev p, const float2* __restrict__ cur,
                                                             float2* io, float omega, float gamma, int mode) {
@@ -1252,6 +1259,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelD
         for (int bb = b0; bb < b1; ++bb) {
             const int J = Jn;
             if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
+            if (s.unit_diag && J == I) continue;   // S_II = 1: d_I is added in the update
             float xv[4][2 * CPT];
             const float2* xb = cur + (size_t)(4 * J) * P + c0;
 #pragma unroll
@@ -1291,7 +1299,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelD
             }
             float dn[2 * CPT];
 #pragma unroll
-            for (int q = 0; q < 2 * CPT; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - acc[a][q]) + dc[q] - dp[q]);
+            for (int q = 0; q < 2 * CPT; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - (s.unit_diag ? acc[a][q] + dc[q] : acc[a][q])) + dc[q] - dp[q]);
             if (LAST) {
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) {
@@ -1359,6 +1367,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4(DevSystem s, Panel
         for (int bb = b0; bb < b1; ++bb) {
             const int J = Jn;
             if (bb + 1 < b1) Jn = __ldg(s.bcol + bb + 1);
+            if (s.unit_diag && J == I) continue;   // S_II = 1: d_I is added in the update
             const float2* xb = cur + (size_t)(4 * J) * P + 2 * t0;
             const float4* St = reinterpret_cast<const float4*>(s.S32T + 16 * (size_t)bb);
 #pragma unroll
@@ -1394,7 +1403,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4(DevSystem s, Panel
                 const float dp[4] = {p4.x, p4.y, p4.z, p4.w}, y[4] = {y0.x, y0.y, y1.x, y1.y};
                 float dn[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - y[q]) + dc[q] - dp[q]);
+                for (int q = 0; q < 4; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - (s.unit_diag ? y[q] + dc[q] : y[q])) + dc[q] - dp[q]);
                 if (LAST) {
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
@@ -1452,6 +1461,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4r(DevSystem s, Pane
             if (bb + 1 < b1) mn = __ldg(s.bmeta + bb + 1);
             const int J = m.x;
             const int nj = (m.y < 0) ? 1 : 4;
+            if (s.unit_diag && J == I) continue;   // S_II = 1: d_I is added in the update
             const float2* xb = cur + (size_t)(4 * J) * P + 2 * t0;
             const float4* Sr = reinterpret_cast<const float4*>(s.S32r) + (m.y & 0x7fffffff);
             if (ni == 4) {
@@ -1507,7 +1517,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4r(DevSystem s, Pane
                 const float dp[4] = {p4.x, p4.y, p4.z, p4.w}, y[4] = {y0.x, y0.y, y1.x, y1.y};
                 float dn[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - y[q]) + dc[q] - dp[q]);
+                for (int q = 0; q < 4; ++q) dn[q] = dp[q] + omega * (gamma * (f[q] - (s.unit_diag ? y[q] + dc[q] : y[q])) + dc[q] - dp[q]);
                 if (LAST) {
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {

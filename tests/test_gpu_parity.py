@@ -186,6 +186,30 @@ def test_explicit_H_same_as_ased(P, c1, h1):
     assert np.abs(x1.cpu().numpy() - x2.cpu().numpy()).max() <= 1e-12 * np.abs(x1.cpu().numpy()).max()
 
 
+def test_non_identity_diagonal_blocks(P, c1, prec):
+    """Orbitals rescaled by a seeded diagonal D (S' = D S D, H' = D H D):
+    the diagonal blocks of S' are no longer the identity, so every product
+    keeps them (the path that skips identity diagonal blocks is not taken);
+    the solutions meet the same true-residual bar and the populations the
+    same 1e-6 e bar against the dense definitions of the rescaled system."""
+    s, H, S, z, w, cols = c1
+    d = np.random.default_rng(11).uniform(0.8, 1.25, S.shape[0])
+    S2, H2 = S * np.outer(d, d), H * np.outer(d, d)
+    oo, bo = s.orb_offset(), s.block_offsets()
+    sv, hv = np.zeros_like(s.S_vals), np.zeros_like(s.S_vals)
+    for i in range(s.n_atoms):
+        for b in range(s.brow_ptr[i], s.brow_ptr[i + 1]):
+            j = s.bcol[b]
+            sv[bo[b]:bo[b + 1]] = S2[oo[i]:oo[i] + 4, oo[j]:oo[j] + 4].ravel()
+            hv[bo[b]:bo[b + 1]] = H2[oo[i]:oo[i] + 4, oo[j]:oo[j] + 4].ravel()
+    h = P.tb_create(s.orb_per_atom, s.brow_ptr, s.bcol, sv, hv, None, s.K)
+    zz = z[::4]
+    x, _ = P.tb_shifted_cocg(h, zz, cols[:4], opts=P.tb_default_opts(**_pm(prec)))
+    assert _true_rel_res(H2, S2, zz, x.cpu().numpy(), cols[:4]).max() <= 1e-8
+    q, _ = P.tb_mulliken_orbital(h, z, w, cols, 2.0, opts=P.tb_default_opts(**_pm(prec)))
+    assert np.abs(q.cpu().numpy() - dense.mulliken_orbital(H2, S2, z, w, 2.0)[cols]).max() <= 1e-6
+
+
 def test_panel_split_with_ragged_tail(P, c1, c1_ref, h1, prec):
     s, H, S, z, w, cols = c1
     cols13 = choose_columns(256, 13, seed=7)
