@@ -107,6 +107,8 @@ struct InnerState {
     int32_t conv;
     int32_t skip;        // refinement: this real column needs no further correction
     double scale;        // refinement: FP32 right-hand side = FP64 residual * scale
+    double unscale;      // refinement: 1 / scale (the residual norm; 0 when skipped), the
+                         // factor of the correction, so no kernel divides per element
 };
 
 struct PanelDev {

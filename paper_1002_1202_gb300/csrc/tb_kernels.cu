@@ -594,7 +594,8 @@ __global__ void __launch_bounds__(THREADS) k_refine_start(PanelDev p, const doub
                 p.inner[2 * t + part].bnorm2 = b2;
                 InnerState st = p.inner32[2 * t + part];
                 st.skip = (!cact || b2 == 0.0) ? 1 : 0;
-                st.scale = st.skip ? 0.0 : 1.0 / sqrt(b2);
+                st.unscale = st.skip ? 0.0 : sqrt(b2);
+                st.scale = st.skip ? 0.0 : 1.0 / st.unscale;
                 p.inner32[2 * t + part] = st;
                 nact += st.skip ? 0 : 1;
             }
@@ -691,7 +692,8 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
                     } else if (!cact || r2 <= p.inner_tol * p.inner_tol * b2 || r2 == 0.0) {
                         st.skip = 1;
                     }
-                    st.scale = st.skip ? 0.0 : 1.0 / sqrt(r2);
+                    st.unscale = st.skip ? 0.0 : sqrt(r2);
+                    st.scale = st.skip ? 0.0 : 1.0 / st.unscale;
                 }
                 nact += st.skip ? 0 : 1;
                 p.inner32[2 * t + part] = st;
@@ -746,7 +748,7 @@ __global__ void k_refine_add(PanelDev p) {
     const InnerState i0 = p.inner32[2 * c], i1 = p.inner32[2 * c + 1];
     const bool u0 = !i0.skip, u1 = !i1.skip;
     if (!u0 && !u1) return;
-    const double f0 = u0 ? 1.0 / i0.scale : 0.0, f1 = u1 ? 1.0 / i1.scale : 0.0;
+    const double f0 = u0 ? i0.unscale : 0.0, f1 = u1 ? i1.unscale : 0.0;
     const long long items = (long long)p.npad * P;
     for (long long idx = blockIdx.x * (long long)THREADS + threadIdx.x; idx < items;
          idx += (long long)gridDim.x * THREADS) {
@@ -1307,8 +1309,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_inner32_cheb(DevSystem s, PanelD
                     const InnerState i0 = p.inner32[2 * (c0 + j)], i1 = p.inner32[2 * (c0 + j) + 1];
                     const bool ca = p.col[c0 + j].active != 0;
                     double2 x = p.Rp[e + j];
-                    if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] / i0.scale;
-                    if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] / i1.scale;
+                    if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] * i0.unscale;
+                    if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] * i1.unscale;
                     p.Rp[e + j] = x;
                     p.RpS[e + j] = df_split(x);
                 }
@@ -1410,8 +1412,8 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4(DevSystem s, Panel
                         const InnerState i0 = p.inner32[2 * (c + j)], i1 = p.inner32[2 * (c + j) + 1];
                         const bool ca = p.col[c + j].active != 0;
                         double2 x = p.Rp[e + j];
-                        if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] / i0.scale;
-                        if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] / i1.scale;
+                        if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] * i0.unscale;
+                        if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] * i1.unscale;
                         p.Rp[e + j] = x;
                         p.RpS[e + j] = df_split(x);
                     }
@@ -1524,8 +1526,8 @@ __global__ void __launch_bounds__(THREADS, 3) k_inner32_cheb4r(DevSystem s, Pane
                         const InnerState i0 = p.inner32[2 * (c + j)], i1 = p.inner32[2 * (c + j) + 1];
                         const bool ca = p.col[c + j].active != 0;
                         double2 x = p.Rp[e + j];
-                        if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] / i0.scale;
-                        if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] / i1.scale;
+                        if (ca && !i0.skip && isfinite(dn[2 * j])) x.x += (double)dn[2 * j] * i0.unscale;
+                        if (ca && !i1.skip && isfinite(dn[2 * j + 1])) x.y += (double)dn[2 * j + 1] * i1.unscale;
                         p.Rp[e + j] = x;
                         p.RpS[e + j] = df_split(x);
                     }
