@@ -1621,8 +1621,8 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
                 for (int a = ni; a < 4; ++a) Sp[16 * b + 5 * a] = 1.0;   // padded slot: S = 1, H = 0
         }
     }
-    // identity diagonal blocks of S (padded slots included); TB_UNIT_DIAG=0
-    // keeps the diagonal blocks in the FP32 products
+    // identity diagonal blocks of S; TB_UNIT_DIAG=0 keeps the diagonal
+    // blocks in the FP32 Chebyshev steps
     const char* ud_env = std::getenv("TB_UNIT_DIAG");
     bool unit_diag = !(ud_env && std::atoi(ud_env) == 0);
     for (int i = 0; i < n && unit_diag; ++i) {
@@ -1659,7 +1659,11 @@ tb_status tb_create(tb_handle** out, const tb_system_desc* d, void* stream) {
     h->ds.n_atoms = n;
     h->ds.nb = nb;
     h->ds.npad = 4 * n;
-    h->ds.unit_diag = unit_diag ? 1 : 0;
+    // systems with s-only atoms keep the diagonal block in the product: on
+    // water the changed FP32 rounding of the corrections made more of them
+    // fall short of inner_lo_tol (7 % more Chebyshev steps, measured)
+    const bool s_only = std::any_of(d->orb_per_atom, d->orb_per_atom + n, [](int32_t o) { return o == 1; });
+    h->ds.unit_diag = (unit_diag && !s_only) ? 1 : 0;
     cudaGetDevice(&h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [&](cudaError_t e) {

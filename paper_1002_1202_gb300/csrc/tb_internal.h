@@ -53,10 +53,10 @@ struct DevSystem {
     // column S[0..3][0], 1x4 as the row S[0][0..3], 1x1 as S[0][0] and three
     // zeros.
     int rag = 0;
-    // 1 when every block row holds its diagonal block once and that block
-    // of S is exactly the identity (orthonormal orbitals on one atom, as an
-    // STO basis gives): the FP32 products with S then skip the diagonal
-    // block and add the vector's own rows instead.
+    // 1 when every block row holds its diagonal block once, that block of S
+    // is exactly the identity (orthonormal orbitals on one atom, as an STO
+    // basis gives) and no atom has a single orbital: the FP32 Chebyshev
+    // steps then skip the diagonal block and add the vector's own rows.
     int unit_diag = 0;
     unsigned char* norb = nullptr;   // [n_atoms] 1 or 4
     int* row_order = nullptr;        // [n_atoms] atom of each block-row slot (indices of this view)

@@ -251,10 +251,9 @@ __global__ void k_panel_init(PanelDev p) {
 __device__ __forceinline__ void df_row_ragged(const DevSystem& s, const float* __restrict__ Mh,
                                               const float* __restrict__ Ml, int I, int ni,
                                               const float4* __restrict__ RpS, int P, int c, float2 (&hi)[4],
-                                              float2 (&lo)[4], int skip_atom = -1) {
+                                              float2 (&lo)[4]) {
     for (int bb = s.brow[I]; bb < s.brow[I + 1]; ++bb) {
         const int2 m = __ldg(s.bmeta + bb);
-        if (m.x == skip_atom) continue;
         const float4* xr = RpS + (size_t)4 * m.x * P + c;
         if (m.y >= 0) {
             const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
@@ -623,12 +622,9 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
                 float2 ah[4], al[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) ah[a] = al[a] = make_float2(0.f, 0.f);
-                // an identity diagonal block is left out: its product is x_I,
-                // taken exactly from the FP64 solution below
-                if (RAG) df_row_ragged(s, s.S32, s.S32lo, I, s.norb[I], p.RpS, P, c, ah, al, s.unit_diag ? I : -1);
+                if (RAG) df_row_ragged(s, s.S32, s.S32lo, I, s.norb[I], p.RpS, P, c, ah, al);
                 for (int bb = RAG ? s.brow[I + 1] : s.brow[I]; bb < s.brow[I + 1]; ++bb) {
                     const int J = s.bcol[bb];
-                    if (s.unit_diag && J == I) continue;
                     const float4* xr = p.RpS + (size_t)4 * J * P + c;
                     const float4 x[4] = {xr[0], xr[P], xr[2 * P], xr[3 * P]};
                     const float4* Sh = reinterpret_cast<const float4*>(s.S32 + 16 * (size_t)bb);
@@ -665,7 +661,7 @@ __global__ void __launch_bounds__(THREADS) k_refine_residual(DevSystem s, PanelD
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const size_t e = (size_t)(4 * I + a) * P + c;
-                const double2 r = (DF && s.unit_diag) ? csub(csub(b[e], p.Rp[e]), acc[a]) : csub(b[e], acc[a]);
+                const double2 r = csub(b[e], acc[a]);
                 p.Rin[e] = r;
                 v[0] += r.x * r.x;
                 v[1] += r.y * r.y;
