@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--large", action="store_true",
                     help="instead of the benchmark step: the 100 000-atom Si system (25x25x20 cells), Chebyshev-step "
                          "time and HBM fraction per panel width, mixed vs FP64 calls and their populations")
+    ap.add_argument("--water-order", choices=["placement", "morton"], default="placement",
+                    help="--batch-full: molecules in their placement order or sorted by the Morton key of the O position")
     ap.add_argument("--adjoint-full", action="store_true",
                     help="measure the band-energy adjoint and forces on the cracked 7680-atom Si slab instead")
     ap.add_argument("--adjoint-cells", type=int, default=10,
@@ -935,8 +937,8 @@ def run_large(args):
 
 def _water_box(args):
     from tbinputs import water_system
-    n, seed = args
-    return water_system(n, seed=seed)
+    n, seed, order = args
+    return water_system(n, seed=seed, order=order)
 
 
 def run_batch_full(args):
@@ -953,7 +955,7 @@ def run_batch_full(args):
     sizes = [int(n) for n in np.random.default_rng(4).integers(512, 1537, size=64)]
     t0 = time.time()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        boxes = pool.map(_water_box, [(n, 1000 + i) for i, n in enumerate(sizes)])
+        boxes = pool.map(_water_box, [(n, 1000 + i, args.water_order) for i, n in enumerate(sizes)])
     build_s = time.time() - t0
     import torch
     from tbinputs import gauss_legendre_grid
@@ -987,8 +989,8 @@ def run_batch_full(args):
     print(json.dumps({
         "metric": "batch_full", "unit": UNIT,
         "workload": "64 water boxes of %d-%d molecules (+H3O+), %d orbitals in all, 64 columns per box, 128 "
-                    "Gauss-Legendre shifts on [-20,5] eV + 0.01i eV, %d outer iterations per call, mixed precision"
-                    % (min(sizes), max(sizes), int(hb.n_orb), iters),
+                    "Gauss-Legendre shifts on [-20,5] eV + 0.01i eV, %d outer iterations per call, mixed precision; "
+                    "molecules in %s order" % (min(sizes), max(sizes), int(hb.n_orb), iters, args.water_order),
         "build_s": build_s, "batched_s": t_b, "value": units / t_b,
         "per_box_first8_s": t_s, "per_box_first8_value": 128 * 64 * 8 * iters / t_s,
         "sizes": sizes}))

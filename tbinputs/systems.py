@@ -134,12 +134,28 @@ def si_diamond(cells=(2, 2, 2), a=5.431, sigma=0.05, seed=1) -> tuple:
     return [SI] * len(pos), pos, box, (True, True, True)
 
 
+def _morton_keys(p, L, bits=10):
+    """Morton (Z-order) keys of positions in [0, L)^3: the cell indices on a
+    2^bits grid with their bits interleaved."""
+    q = np.clip((np.asarray(p) / L * (1 << bits)).astype(np.int64), 0, (1 << bits) - 1)
+    key = np.zeros(len(q), dtype=np.int64)
+    for b in range(bits):
+        for a in range(3):
+            key |= ((q[:, a] >> b) & 1) << (3 * b + a)
+    return key
+
+
 def water_box(n_mol: int, density=1.0, seed=4, excess_proton=True,
-              r_oh=0.96, angle_deg=104.5, d_oo_min=2.5) -> tuple:
+              r_oh=0.96, angle_deg=104.5, d_oo_min=2.5, order="placement") -> tuple:
     """Liquid-water-like box: O sites by random sequential placement with an
     O-O distance of at least ``d_oo_min``, random molecular orientations,
     rigid O-H = ``r_oh`` and H-O-H = ``angle_deg``.  With ``excess_proton``
-    one molecule gets a third H (H3O+)."""
+    one molecule gets a third H (H3O+).  ``order``: molecules listed in
+    their placement order, or ("morton") sorted by the Morton key of their
+    O position, the spatial order a cell-list code keeps; the molecules and
+    their geometry are the same either way."""
+    if order not in ("placement", "morton"):
+        raise ValueError(order)
     L = (n_mol * 18.015 / (0.60221408 * density)) ** (1.0 / 3.0)
     rng = np.random.default_rng(seed)
     ncell = max(1, int(L // d_oo_min))
@@ -176,8 +192,9 @@ def water_box(n_mol: int, density=1.0, seed=4, excess_proton=True,
     half = math.radians(angle_deg) / 2.0
     local_h = np.array([[math.sin(half), 0.0, math.cos(half)],
                         [-math.sin(half), 0.0, math.cos(half)]]) * r_oh
-    species, pos = [], []
+    species, pos, first = [], [], []
     for m, p in enumerate(o_pos):
+        first.append(len(species))
         q = rng.normal(size=4)
         q /= np.linalg.norm(q)
         w, x, y, z = q
@@ -197,6 +214,12 @@ def water_box(n_mol: int, density=1.0, seed=4, excess_proton=True,
             species.append(H)
             pos.append(p + r_oh * v / np.linalg.norm(v))
     pos = np.mod(np.array(pos), L)
+    if order == "morton":
+        first.append(len(species))
+        perm = np.argsort(_morton_keys(np.mod(np.array(o_pos), L), L), kind="stable")
+        idx = np.concatenate([np.arange(first[m], first[m + 1]) for m in perm])
+        species = [species[i] for i in idx]
+        pos = pos[idx]
     return species, pos, np.array([L, L, L]), (True, True, True)
 
 
@@ -396,7 +419,7 @@ def si_slab_system(cells=(10, 10, 10), sigma=0.1, seed=7, cutoff=4.0, K=1.75, **
                               "cutoff": cutoff, "tip": tip.tolist()})
 
 
-def water_system(n_mol=64, seed=4, cutoff=4.5, K=1.75, excess_proton=True) -> TBSystem:
-    sp, pos, box, pbc = water_box(n_mol, seed=seed, excess_proton=excess_proton)
+def water_system(n_mol=64, seed=4, cutoff=4.5, K=1.75, excess_proton=True, order="placement") -> TBSystem:
+    sp, pos, box, pbc = water_box(n_mol, seed=seed, excess_proton=excess_proton, order=order)
     return build_system(sp, pos, box, pbc, cutoff, K,
-                        meta={"kind": "water", "n_mol": n_mol, "seed": seed, "cutoff": cutoff})
+                        meta={"kind": "water", "n_mol": n_mol, "seed": seed, "cutoff": cutoff, "order": order})
