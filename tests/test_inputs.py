@@ -92,6 +92,41 @@ def test_water_counts():
     assert sy.n_atoms == 3 * 64 + 1 and sy.n_orb == 6 * 64 + 1
 
 
+def test_water_morton_order_is_a_permutation_of_molecules():
+    """The Morton order lists the same molecules (each O followed by its own
+    H atoms, the H3O+ kept whole) in a new order: the same atoms, the same
+    overlap spectrum, and consecutive block rows that share more of their
+    neighbour atoms."""
+    a = water_system(100, seed=9)
+    b = water_system(100, seed=9, order="morton")
+    assert a.n_atoms == b.n_atoms and a.n_orb == b.n_orb
+    key = lambda s: sorted((sp.name, *np.round(p, 10)) for sp, p in zip(s.species, s.positions))
+    assert key(a) == key(b)
+    # every H sits within O-H of the O that precedes it in the list
+    for s in (a, b):
+        o = None
+        for sp, p in zip(s.species, s.positions):
+            if sp.name == "O":
+                o = p
+            else:
+                d = p - o
+                d -= s.box * np.round(d / s.box)
+                assert abs(np.linalg.norm(d) - 0.96) < 1e-9
+    ea = np.linalg.eigvalsh(a.dense_S())
+    eb = np.linalg.eigvalsh(b.dense_S())
+    assert np.abs(ea - eb).max() <= 1e-12
+
+    def distinct_ratio(s, G=16):
+        d = r = 0
+        for g0 in range(0, s.n_atoms, G):
+            refs = s.bcol[s.brow_ptr[g0]:s.brow_ptr[min(s.n_atoms, g0 + G)]]
+            d += len(set(refs.tolist()))
+            r += len(refs)
+        return d / r
+
+    assert distinct_ratio(b) < distinct_ratio(a)
+
+
 def test_cracked_slab_geometry():
     """The wedge-cracked Si slab: no atom centre (before displacement) inside
     the wedge, the gap 2 A wide at the tip and opening by 10 degrees, open
